@@ -1,0 +1,184 @@
+/*
+ * fdsc.h -- C ABI of libfdsc, the GB300 (sm_103a) implementation of the
+ * frequency-domain secure convolution (FDSC) of ENSEI (Bian, Wang, Hiromoto,
+ * Shi, Sato, CVPR 2020).
+ *
+ * One convolution layer, Fig. 2 of the paper, runs as:
+ *   Alice  fdsc_ntt2d(x_A) -> fdsc_encrypt                         (lines 1-2)
+ *   Bob    fdsc_ntt2d(x_B) -> fdsc_homrec      (between layers, lines 9-11)
+ *   Bob    fdsc_homconv (Hadamard product summed over input channels,
+ *          fused with HomShare)                                    (lines 3-4)
+ *   Alice  fdsc_decrypt -> fdsc_intt2d;  Bob fdsc_intt2d(s_B-hat)  (lines 5-6)
+ * with setup (no user input): fdsc_params_create, fdsc_keygen,
+ * fdsc_filter_prepare, fdsc_mask_prepare.
+ *
+ * Conventions
+ *  - Every call returns an int status: FDSC_OK (0) or a negative FDSC_ERR_*.
+ *    fdsc_last_error() returns a message for the calling thread's last
+ *    failure.  No C++ exception crosses this boundary.
+ *  - Tensor arguments are DEVICE pointers owned by the caller (allocated on
+ *    the device that was current when the params object was created); the
+ *    library never frees them and keeps no reference after the call.  The
+ *    only library-owned memory is the params object's constant tables.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All compute calls are asynchronous on that stream; argument
+ *    errors are reported before anything is enqueued, launch errors after.
+ *  - Element types: Z_p data uint32 in [0, p); Z_q data uint64 in [0, q);
+ *    weights int8.  All arrays are dense, row-major, with the shapes given.
+ *  - Z_q arrays must be 16-byte aligned and Z_p arrays 16-byte aligned
+ *    (the kernels use 128-bit loads); FDSC_ERR_ARG otherwise.
+ *  - Transform orders: NTT2D / INTT2D spectra are in natural order
+ *    (k1, k2), f = k1 W + k2.  Ciphertext words index j holds the evaluation
+ *    of the ring element at psi_q^(2 brv_n(j) + 1); slot i of a slot set is
+ *    the plaintext evaluated at psi_p^(2 brv_S(i) + 1).
+ */
+#ifndef FDSC_H
+#define FDSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FDSC_OK = 0,
+    FDSC_ERR_ARG = -1,         /* invalid argument, shape or alignment            */
+    FDSC_ERR_NOISE = -2,       /* the decryption noise bound fails (q too small)  */
+    FDSC_ERR_OOM = -3,         /* device or host allocation failed                */
+    FDSC_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed     */
+    FDSC_ERR_UNSUPPORTED = -5  /* valid but outside what this build implements    */
+};
+
+/* Message for the calling thread's most recent failure ("" if none). */
+const char* fdsc_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Parameters (Sec. 3.1 BFV triple (n, p_E, q); Sec. 5.2 moduli; Sec. 6.4) */
+/* ---------------------------------------------------------------------- */
+/* One prime p serves as NTT, sharing and plaintext modulus.  q is the
+ * largest prime below 2^60 with q = 1 mod 8192 p, Delta = floor(q / p).
+ * S = min(n, 2^(v2(p-1)-1)) slots per slot set, d = n / S slot sets per
+ * ciphertext (d > 1 when x^n + 1 does not split into linear factors mod p). */
+typedef struct {
+    uint32_t n, logn, p, S, logS, d;
+    uint32_t g_p, psi_p;        /* smallest primitive root mod p; 2S-th root  */
+    uint64_t q, g_q, psi_q;     /* modulus; smallest primitive root; 2n-th root */
+    uint64_t delta, r_q;        /* floor(q/p), q mod p                          */
+} fdsc_params_info;
+
+typedef struct fdsc_params fdsc_params; /* opaque */
+
+/* Host-only derivation of the parameters for ring degree n (power of two,
+ * 16 <= n <= 4096) and prime p (< 2^20, p = 1 mod 4).  Touches no device.
+ * FDSC_ERR_ARG for unsupported (n, p). */
+int fdsc_params_query(uint32_t n, uint32_t p, fdsc_params_info* out);
+
+/* Creates the params object on the CURRENT device: derives the parameters
+ * and uploads the twiddle tables (about 40 n bytes).  max_T is the largest
+ * number of input ciphertexts a HomConv output will sum; the worst-case
+ * decryption noise
+ *   T n (19 + r_q) floor(p/2) + r_q ceil(T n (p-1) floor(p/2) / p) + r_q
+ * must keep p |noise| + r_q (p-1) < q/2, else FDSC_ERR_NOISE. */
+int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_params** out);
+int fdsc_params_destroy(fdsc_params* P);
+int fdsc_params_get_info(const fdsc_params* P, fdsc_params_info* out);
+
+/* The Gaussian sampler's cumulative table (sigma = 3.2, |e| <= 19; 2^63
+ * scaled), for cross-checking; 19 entries. */
+int fdsc_gauss_table(uint64_t* out19);
+
+/* ---------------------------------------------------------------------- */
+/* Layer shape and ciphertext packing                                      */
+/* ---------------------------------------------------------------------- */
+/* B images of Ci channels on an H x W plane (powers of two, H W <= 4096,
+ * H and W dividing p-1), Co filters.  When H W <= S, one slot set holds
+ * g_c x g_b blocks of H W slots (g_c channels of g_b images;
+ * g_c g_b H W <= S); when H W > S, one channel spectrum spans
+ * beta = H W / S ciphertexts ("halves") and g_c = g_b = 1. */
+typedef struct {
+    uint32_t B, Ci, Co, H, W, g_c, g_b;
+} fdsc_layer;
+
+typedef struct {
+    uint32_t HW, T, GB, beta;   /* T = ceil(Ci/g_c) (or Ci); GB = ceil(B/(d g_b)) */
+    uint32_t n_in, n_out;       /* input ciphertexts GB T beta; outputs GB Co beta */
+    uint64_t ct_in_words;       /* n_in  * 2 * n   (uint64)                       */
+    uint64_t ct_out_words;      /* n_out * 2 * n                                  */
+    uint64_t filter_words;      /* Co * T * beta * n                              */
+    uint64_t mask_words;        /* n_out * n                                      */
+    uint64_t in_spectra_words;  /* B * Ci * H W    (uint32)                       */
+    uint64_t out_spectra_words; /* B * Co * H W                                   */
+} fdsc_layout;
+
+int fdsc_layout_query(uint32_t n, uint32_t p, const fdsc_layer* L, fdsc_layout* out);
+
+/* ---------------------------------------------------------------------- */
+/* Transforms                                                              */
+/* ---------------------------------------------------------------------- */
+/* Eq. 12 in two dimensions (the cyclic NTT over the padded H x W plane,
+ * Fig. 2 lines 1 and 9): X[k1][k2] = sum_{i,j} x[i][j] w_H^(i k1) w_W^(j k2)
+ * mod p, w_L = g_p^((p-1)/L).  x, X: uint32 [planes][H][W]; x may equal X. */
+int fdsc_ntt2d(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_t* x, uint32_t* X,
+               uint64_t planes, void* stream);
+/* Fig. 2 line 6: the inverse, x = (HW)^-1 sum X w^-(...). */
+int fdsc_intt2d(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_t* X, uint32_t* x,
+                uint64_t planes, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Setup                                                                   */
+/* ---------------------------------------------------------------------- */
+/* Secret key of Eq. 1: ternary t (uniform on {-1,0,1}, drawn from `seed`),
+ * written as t_hat = NTT_q(t): uint64 [n]. */
+int fdsc_keygen(const fdsc_params* P, uint64_t seed, uint64_t* t_hat, void* stream);
+
+/* Fig. 2 line 3 (Bob): w_hat = flatten(NTT2D(W)) packed into plaintext
+ * polynomials and lifted to NTT_q.  w: int8 [Co][Ci][fh][fw] (taps at the
+ * top-left of the padded plane, fh <= H, fw <= W); P_hat: uint64
+ * [Co][T][beta][n] -- plaintext (co, k, h) holds the spectra of channels
+ * k g_c .. k g_c + g_c - 1 in its blocks, centred-lifted, at x^(d i). */
+int fdsc_filter_prepare(const fdsc_params* P, const fdsc_layer* L, const int8_t* w, uint32_t fh,
+                        uint32_t fw, uint64_t* P_hat, void* stream);
+
+/* Eq. 2 (HomShare) randomness, drawn from `seed`: Bob's share
+ * sB_hat: uint32 [B][Co][H W], uniform mod p, and the encrypted-domain mask
+ * M_hat: uint64 [GB][Co][beta][n] = NTT_q(Delta * encode(mask slots)), the
+ * mask split over the g_c channel blocks so that the decrypt-side fold
+ * gives y_hat - sB_hat for every packing. */
+int fdsc_mask_prepare(const fdsc_params* P, const fdsc_layer* L, uint64_t seed, uint64_t* M_hat,
+                      uint32_t* sB_hat, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Online path                                                             */
+/* ---------------------------------------------------------------------- */
+/* Eq. 1 in the NTT_q domain (Sec. 5.1): X: uint32 [B][Ci][H W] spectra
+ * (NTT2D of Alice's share); ct: uint64 [GB][T][beta][2][n] with
+ * c0_hat = -a_hat, c1_hat = a_hat o t_hat + NTT_q(Delta m + e); a_hat
+ * uniform mod q and e ~ D_{3.2}, |e| <= 19, both drawn from `seed`. */
+int fdsc_encrypt(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, const uint32_t* X,
+                 uint64_t seed, uint64_t* ct, void* stream);
+
+/* Eq. 3 (HomRec): ct (in place) += the plaintext encoding of XB, Bob's share
+ * spectra uint32 [B][Ci][H W] packed like the ciphertext. */
+int fdsc_homrec(const fdsc_params* P, const fdsc_layer* L, const uint32_t* XB, uint64_t* ct,
+                void* stream);
+
+/* Fig. 2 lines 3-4: ct_out[bb][co][h][c][j] = sum_k ct_in[bb][k][h][c][j]
+ * P_hat[co][k][h][j] mod q, then c1 -= M_hat[bb][co][h] (HomShare; skipped
+ * when M_hat is NULL).  ct_out: uint64 [GB][Co][beta][2][n]; must not alias
+ * ct_in.  Exact: the sum is formed in 128 bits and reduced once per 256
+ * terms. */
+int fdsc_homconv(const fdsc_params* P, const fdsc_layer* L, const uint64_t* ct_in,
+                 const uint64_t* P_hat, const uint64_t* M_hat, uint64_t* ct_out, void* stream);
+
+/* Fig. 2 line 5 (Alice): v = INTT_q(c0_hat o t_hat + c1_hat),
+ * m = floor((2 p v + q) / (2 q)) mod p, slots = decode(m), and the g_c
+ * channel blocks of each image folded: SA_hat: uint32 [B][Co][H W]. */
+int fdsc_decrypt(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat,
+                 const uint64_t* ct, uint32_t* SA_hat, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDSC_H */

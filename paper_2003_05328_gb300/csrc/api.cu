@@ -1,0 +1,137 @@
+// api.cu -- the compute entry points of the libfdsc C ABI: argument checks,
+// then one kernel launch each on the caller's stream.
+#include "fdsc_internal.h"
+
+namespace {
+
+int check_params(const fdsc_params* P) {
+    if (!P) return fdsc_set_error(FDSC_ERR_ARG, "params is NULL");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fdsc_set_error(FDSC_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev != P->device)
+        return fdsc_set_error(FDSC_ERR_ARG, "params were created on device %d but device %d is current", P->device,
+                              dev);
+    return FDSC_OK;
+}
+
+int check_ptr(const void* p, const char* name, bool align16 = true) {
+    if (!p) return fdsc_set_error(FDSC_ERR_ARG, "%s is NULL", name);
+    if (align16 && (reinterpret_cast<uintptr_t>(p) & 15))
+        return fdsc_set_error(FDSC_ERR_ARG, "%s is not 16-byte aligned", name);
+    return FDSC_OK;
+}
+
+int launched(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return FDSC_OK;
+    return fdsc_set_error(FDSC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool overlap(const void* a, u64 abytes, const void* b, u64 bbytes) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + bbytes && y < x + abytes;
+}
+
+int ntt2d_common(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_t* x, uint32_t* X, uint64_t planes,
+                 void* stream, bool inverse) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (H < 2 || W < 2 || (H & (H - 1)) || (W & (W - 1)))
+        return fdsc_set_error(FDSC_ERR_ARG, "H = %u, W = %u: powers of two >= 2 required", H, W);
+    if (H > P->dev.lmax || W > P->dev.lmax || (u64)H * W > FDSC_MAX_HW)
+        return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "plane %ux%u exceeds H, W <= %u, HW <= %u", H, W, P->dev.lmax,
+                              FDSC_MAX_HW);
+    if (planes == 0) return FDSC_OK;
+    if ((rc = check_ptr(x, "x")) || (rc = check_ptr(X, "X"))) return rc;
+    return launched(launch_ntt2d(P->dev, H, W, x, X, planes, inverse, (cudaStream_t)stream),
+                    inverse ? "intt2d" : "ntt2d");
+}
+
+}  // namespace
+
+extern "C" int fdsc_ntt2d(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_t* x, uint32_t* X,
+                          uint64_t planes, void* stream) {
+    return ntt2d_common(P, H, W, x, X, planes, stream, false);
+}
+
+extern "C" int fdsc_intt2d(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_t* X, uint32_t* x,
+                           uint64_t planes, void* stream) {
+    return ntt2d_common(P, H, W, X, x, planes, stream, true);
+}
+
+extern "C" int fdsc_keygen(const fdsc_params* P, uint64_t seed, uint64_t* t_hat, void* stream) {
+    int rc = check_params(P);
+    if (rc || (rc = check_ptr(t_hat, "t_hat"))) return rc;
+    return launched(launch_keygen(P->dev, seed, t_hat, (cudaStream_t)stream), "keygen");
+}
+
+extern "C" int fdsc_encrypt(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, const uint32_t* X,
+                            uint64_t seed, uint64_t* ct, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_ptr(t_hat, "t_hat")) || (rc = check_ptr(X, "X")) || (rc = check_ptr(ct, "ct"))) return rc;
+    return launched(launch_encrypt(P->dev, D, t_hat, X, seed, ct, (cudaStream_t)stream), "encrypt");
+}
+
+extern "C" int fdsc_homrec(const fdsc_params* P, const fdsc_layer* L, const uint32_t* XB, uint64_t* ct,
+                           void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_ptr(XB, "XB")) || (rc = check_ptr(ct, "ct"))) return rc;
+    return launched(launch_homrec(P->dev, D, XB, ct, (cudaStream_t)stream), "homrec");
+}
+
+extern "C" int fdsc_filter_prepare(const fdsc_params* P, const fdsc_layer* L, const int8_t* w, uint32_t fh,
+                                   uint32_t fw, uint64_t* P_hat, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if (fh == 0 || fw == 0 || fh > D.H || fw > D.W)
+        return fdsc_set_error(FDSC_ERR_ARG, "filter %ux%u must fit the %ux%u plane", fh, fw, D.H, D.W);
+    if ((rc = check_ptr(w, "w", false)) || (rc = check_ptr(P_hat, "P_hat"))) return rc;
+    return launched(launch_filter_prepare(P->dev, D, w, fh, fw, P_hat, (cudaStream_t)stream), "filter_prepare");
+}
+
+extern "C" int fdsc_mask_prepare(const fdsc_params* P, const fdsc_layer* L, uint64_t seed, uint64_t* M_hat,
+                                 uint32_t* sB_hat, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_ptr(M_hat, "M_hat")) || (rc = check_ptr(sB_hat, "sB_hat"))) return rc;
+    return launched(launch_mask_prepare(P->dev, D, seed, M_hat, sB_hat, (cudaStream_t)stream), "mask_prepare");
+}
+
+extern "C" int fdsc_homconv(const fdsc_params* P, const fdsc_layer* L, const uint64_t* ct_in, const uint64_t* P_hat,
+                            const uint64_t* M_hat, uint64_t* ct_out, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    fdsc_layout lay;
+    if ((rc = fdsc_make_layer(P->info, L, &D, &lay))) return rc;
+    if (D.T > P->max_T)
+        return fdsc_set_error(FDSC_ERR_NOISE, "T = %u input ciphertexts exceed the params' noise budget (max_T = %u)",
+                              D.T, P->max_T);
+    if ((rc = check_ptr(ct_in, "ct_in")) || (rc = check_ptr(P_hat, "P_hat")) || (rc = check_ptr(ct_out, "ct_out")))
+        return rc;
+    if (M_hat && (rc = check_ptr(M_hat, "M_hat"))) return rc;
+    if (overlap(ct_in, lay.ct_in_words * 8, ct_out, lay.ct_out_words * 8))
+        return fdsc_set_error(FDSC_ERR_ARG, "ct_out overlaps ct_in");
+    return launched(launch_homconv(P->dev, D, ct_in, P_hat, M_hat, ct_out, (cudaStream_t)stream), "homconv");
+}
+
+extern "C" int fdsc_decrypt(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, const uint64_t* ct,
+                            uint32_t* SA_hat, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_ptr(t_hat, "t_hat")) || (rc = check_ptr(ct, "ct")) || (rc = check_ptr(SA_hat, "SA_hat")))
+        return rc;
+    return launched(launch_decrypt(P->dev, D, t_hat, ct, SA_hat, (cudaStream_t)stream), "decrypt");
+}

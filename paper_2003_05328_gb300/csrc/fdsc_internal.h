@@ -1,0 +1,78 @@
+// fdsc_internal.h -- shared host/device definitions of libfdsc.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fdsc.h"
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+// Largest cyclic transform length the NTT2D tables cover (H, W <= LMAX).
+#define FDSC_LMAX 4096u
+// Largest padded plane a CTA transforms in shared memory.
+#define FDSC_MAX_HW 4096u
+
+// Everything a kernel needs about (n, p, q): passed by value.
+struct DevParams {
+    u32 n, logn, p, S, logS, d;
+    u32 Sinv, Sinv_s;      // S^-1 mod p and its 32-bit Shoup companion
+    u32 lmax, loglmax;     // NTT2D twiddle table covers w_lmax^k, k < lmax/2
+    u64 q, twoq, delta;
+    u64 r64, r64_s;        // 2^64 mod q, floor(r64 2^64 / q)
+    u64 one_s;             // floor(2^64 / q): Shoup companion of 1
+    u64 round_k;           // floor(p 2^64 / q)
+    u64 ninv, ninv_s;      // n^-1 mod q and companion
+    const u64* qfw;        // psi_q^brv_n(k), k < n
+    const u64* qfw_s;
+    const u64* qinv;       // psi_q^-brv_n(k)
+    const u64* qinv_s;
+    const u32* pfw;        // psi_p^brv_S(k), k < S
+    const u32* pfw_s;
+    const u32* pinv;
+    const u32* pinv_s;
+    const u32* w2d;        // w_lmax^k, k < lmax/2
+    const u32* w2d_s;
+    const u32* w2di;       // w_lmax^-k
+    const u32* w2di_s;
+    const u64* cdt;        // [19] Gaussian cumulative table
+};
+
+// A layer with its packing, derived (all counts fit in 32 bits).
+struct DevLayer {
+    u32 B, Ci, Co, H, W, HW, logH, logW;
+    u32 g_c, g_b, T, GB, beta, n_in, n_out;
+};
+
+struct fdsc_params {
+    fdsc_params_info info;
+    DevParams dev;
+    u32 max_T;
+    int device;
+    void* table_mem;  // one device allocation holding every table
+};
+
+// ---- host helpers (params.cu) ----
+int fdsc_set_error(int code, const char* fmt, ...);
+int fdsc_derive(u32 n, u32 p, fdsc_params_info* out);
+int fdsc_make_layer(const fdsc_params_info& I, const fdsc_layer* L, DevLayer* out, fdsc_layout* lay);
+void fdsc_host_cdt(u64* cdt19);
+bool fdsc_noise_ok(const fdsc_params_info& I, u32 T);
+u32 fdsc_shoup32(u32 w, u32 p);
+u32 fdsc_powmod32(u32 b, u64 e, u32 p);
+
+// ---- kernel launchers (return cudaError_t of the launch) ----
+cudaError_t launch_ntt2d(const DevParams& P, u32 H, u32 W, const u32* x, u32* X, u64 planes, bool inverse,
+                         cudaStream_t s);
+cudaError_t launch_keygen(const DevParams& P, u64 seed, u64* t_hat, cudaStream_t s);
+cudaError_t launch_encrypt(const DevParams& P, const DevLayer& L, const u64* t_hat, const u32* X, u64 seed,
+                           u64* ct, cudaStream_t s);
+cudaError_t launch_homrec(const DevParams& P, const DevLayer& L, const u32* XB, u64* ct, cudaStream_t s);
+cudaError_t launch_filter_prepare(const DevParams& P, const DevLayer& L, const int8_t* w, u32 fh, u32 fw,
+                                  u64* Phat, cudaStream_t s);
+cudaError_t launch_mask_prepare(const DevParams& P, const DevLayer& L, u64 seed, u64* Mhat, u32* sB,
+                                cudaStream_t s);
+cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* Phat,
+                           const u64* Mhat, u64* ct_out, cudaStream_t s);
+cudaError_t launch_decrypt(const DevParams& P, const DevLayer& L, const u64* t_hat, const u64* ct, u32* SA,
+                           cudaStream_t s);

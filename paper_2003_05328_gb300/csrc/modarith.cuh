@@ -1,0 +1,211 @@
+// modarith.cuh -- device arithmetic of libfdsc: exact modular products mod q
+// (60-bit) and mod p (< 2^20), the counter-based sampler, and the
+// block-cooperative transforms that run on shared memory.
+//
+// Products by a fixed operand w use Shoup's precomputed quotient
+// w' = floor(w 2^k / m): for any a < 2^k, a w - floor(a w' / 2^k) m lies in
+// [0, 2m) and is computed exactly in wrapping k-bit arithmetic (V. Shoup, NTL;
+// D. Harvey, "Faster arithmetic for number-theoretic transforms", 2014).
+// Butterflies keep values lazily in [0, 4m) (Harvey), which needs 4q < 2^64.
+#pragma once
+#include "fdsc_internal.h"
+
+// ------------------------------------------------------------------ mod q
+__device__ __forceinline__ u64 shoup_mul(u64 a, u64 w, u64 ws, u64 q) {
+    return a * w - __umul64hi(a, ws) * q;  // [0, 2q)
+}
+
+// (hi 2^64 + lo) mod q for any hi, lo < 2^64: hi 2^64 = hi (2^64 mod q) and
+// lo = lo * 1, each by a Shoup product, then two conditional subtractions.
+__device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const DevParams& P) {
+    u64 r = shoup_mul(hi, P.r64, P.r64_s, P.q) + (lo - __umul64hi(lo, P.one_s) * P.q);
+    r = r >= P.twoq ? r - P.twoq : r;
+    return r >= P.q ? r - P.q : r;
+}
+
+__device__ __forceinline__ u64 mulmod_q(u64 a, u64 b, const DevParams& P) {
+    return reduce128(__umul64hi(a, b), a * b, P);
+}
+__device__ __forceinline__ u64 addmod_q(u64 a, u64 b, u64 q) {
+    u64 s = a + b;
+    return s >= q ? s - q : s;
+}
+__device__ __forceinline__ u64 submod_q(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// ------------------------------------------------------------------ mod p
+__device__ __forceinline__ u32 shoup_mul32(u32 a, u32 w, u32 ws, u32 p) {
+    return a * w - __umulhi(a, ws) * p;  // [0, 2p)
+}
+__device__ __forceinline__ u32 addmod_p(u32 a, u32 b, u32 p) {
+    u32 s = a + b;
+    return s >= p ? s - p : s;
+}
+__device__ __forceinline__ u32 submod_p(u32 a, u32 b, u32 p) { return a >= b ? a - b : a + p - b; }
+
+// ------------------------------------------------------------------ sampler
+// SplitMix64 output function (Steele, Lea & Flood 2014) used as a counter
+// generator: stream key = out(seed + domain gamma); value idx = out(key +
+// (idx + 1) gamma).
+#define FDSC_GAMMA 0x9E3779B97F4A7C15ull
+enum { DOM_T = 1, DOM_A = 2, DOM_E = 3, DOM_MASK = 4, DOM_MASK_SPLIT = 5 };
+
+__device__ __forceinline__ u64 splitmix_out(u64 z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ u64 stream_key(u64 seed, u64 dom) { return splitmix_out(seed + dom * FDSC_GAMMA); }
+__device__ __forceinline__ u64 stream_at(u64 key, u64 idx) { return splitmix_out(key + (idx + 1) * FDSC_GAMMA); }
+
+// floor((r1 2^64 + r2) q / 2^128): the top word of r1 q + hi(r2 q).
+__device__ __forceinline__ u64 uniform_q(u64 r1, u64 r2, u64 q) {
+    u64 lo = r1 * q, hi = __umul64hi(r1, q);
+    u64 s = lo + __umul64hi(r2, q);
+    return hi + (s < lo);
+}
+__device__ __forceinline__ u32 uniform_p(u64 r, u32 p) { return (u32)__umul64hi(r, (u64)p); }
+
+// Discrete Gaussian from one word: sign bit 63, magnitude = number of table
+// entries the low 63 bits reach.
+__device__ __forceinline__ int gauss_sample(u64 r, const u64* cdt) {
+    u64 u = r & 0x7FFFFFFFFFFFFFFFull;
+    int a = 0;
+#pragma unroll
+    for (int k = 0; k < 19; k++) a += (u >= cdt[k]);
+    return (r >> 63) ? -a : a;
+}
+
+// ------------------------------------------------------------------ transforms
+// All run with the whole CTA on a shared-memory array and end synchronised.
+
+// Negacyclic NTT mod q, natural order in, bit-reversed evaluation order out
+// (Cooley-Tukey butterflies with twiddles psi^brv(m+i)).  In: [0, 4q); out [0, q).
+__device__ __forceinline__ void ntt_q_fwd(u64* a, const DevParams& P) {
+    const u32 half = P.n >> 1;
+    u32 logt = P.logn - 1;
+    for (u32 m = 1; m < P.n; m <<= 1, logt--) {
+        const u32 t = 1u << logt;
+        for (u32 b = threadIdx.x; b < half; b += blockDim.x) {
+            const u32 i = b >> logt, j = (i << (logt + 1)) + (b & (t - 1));
+            const u64 w = P.qfw[m + i], ws = P.qfw_s[m + i];
+            u64 x = a[j];
+            x = x >= P.twoq ? x - P.twoq : x;
+            const u64 y = shoup_mul(a[j + t], w, ws, P.q);
+            a[j] = x + y;
+            a[j + t] = x - y + P.twoq;
+        }
+        __syncthreads();
+    }
+    for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) {
+        u64 x = a[j];
+        x = x >= P.twoq ? x - P.twoq : x;
+        a[j] = x >= P.q ? x - P.q : x;
+    }
+    __syncthreads();
+}
+
+// Inverse: bit-reversed in, natural out, Gentleman-Sande butterflies with
+// psi^-brv(h+i), then the factor n^-1.  In: [0, 2q); out [0, q).
+__device__ __forceinline__ void ntt_q_inv(u64* a, const DevParams& P) {
+    const u32 half = P.n >> 1;
+    u32 logt = 0;
+    for (u32 h = half; h >= 1; h >>= 1, logt++) {
+        const u32 t = 1u << logt;
+        for (u32 b = threadIdx.x; b < half; b += blockDim.x) {
+            const u32 i = b >> logt, j = (i << (logt + 1)) + (b & (t - 1));
+            const u64 w = P.qinv[h + i], ws = P.qinv_s[h + i];
+            const u64 x = a[j], y = a[j + t];
+            u64 s = x + y;
+            a[j] = s >= P.twoq ? s - P.twoq : s;
+            a[j + t] = shoup_mul(x - y + P.twoq, w, ws, P.q);
+        }
+        __syncthreads();
+    }
+    for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) {
+        u64 x = shoup_mul(a[j], P.ninv, P.ninv_s, P.q);
+        a[j] = x >= P.q ? x - P.q : x;
+    }
+    __syncthreads();
+}
+
+// Slot decode on `cnt` consecutive length-S sets: negacyclic NTT mod p,
+// natural in, bit-reversed out.  In [0, p); out [0, p).
+__device__ __forceinline__ void ntt_p_fwd(u32* a, u32 cnt, const DevParams& P) {
+    const u32 half = P.S >> 1, p = P.p;
+    u32 logt = P.logS - 1;
+    for (u32 m = 1; m < P.S; m <<= 1, logt--) {
+        const u32 t = 1u << logt;
+        for (u32 g = threadIdx.x; g < half * cnt; g += blockDim.x) {
+            const u32 set = g >> (P.logS - 1), b = g & (half - 1);
+            const u32 i = b >> logt, j = set * P.S + (i << (logt + 1)) + (b & (t - 1));
+            u32 x = a[j], y = shoup_mul32(a[j + t], P.pfw[m + i], P.pfw_s[m + i], p);
+            y = y >= p ? y - p : y;
+            a[j] = addmod_p(x, y, p);
+            a[j + t] = submod_p(x, y, p);
+        }
+        __syncthreads();
+    }
+}
+
+// Slot encode: the inverse (bit-reversed in, natural out, times S^-1).
+__device__ __forceinline__ void ntt_p_inv(u32* a, u32 cnt, const DevParams& P) {
+    const u32 half = P.S >> 1, p = P.p;
+    u32 logt = 0;
+    for (u32 h = half; h >= 1; h >>= 1, logt++) {
+        const u32 t = 1u << logt;
+        for (u32 g = threadIdx.x; g < half * cnt; g += blockDim.x) {
+            const u32 set = g >> (P.logS - 1), b = g & (half - 1);
+            const u32 i = b >> logt, j = set * P.S + (i << (logt + 1)) + (b & (t - 1));
+            const u32 x = a[j], y = a[j + t];
+            a[j] = addmod_p(x, y, p);
+            u32 d = shoup_mul32(submod_p(x, y, p), P.pinv[h + i], P.pinv_s[h + i], p);
+            a[j + t] = d >= p ? d - p : d;
+        }
+        __syncthreads();
+    }
+    for (u32 j = threadIdx.x; j < P.S * cnt; j += blockDim.x) {
+        u32 x = shoup_mul32(a[j], P.Sinv, P.Sinv_s, p);
+        a[j] = x >= p ? x - p : x;
+    }
+    __syncthreads();
+}
+
+// Cyclic 2D NTT of one H x W plane held in shared memory in bit-reversed
+// order along both axes (x[brv(i)][brv(j)]); leaves the natural-order
+// spectrum.  Radix-2 decimation in time along rows, then columns, with
+// twiddles w_L^k = w_lmax^(k lmax / L).  `inverse` selects w^-1 (no scaling).
+__device__ __forceinline__ void ntt2d_plane(u32* x, u32 logH, u32 logW, bool inverse, const DevParams& P) {
+    const u32 p = P.p, H = 1u << logH, W = 1u << logW, nb = (H * W) >> 1;
+    const u32* tw = inverse ? P.w2di : P.w2d;
+    const u32* tws = inverse ? P.w2di_s : P.w2d_s;
+    // rows
+    for (u32 ls = 1; ls <= logW; ls++) {
+        const u32 hl = 1u << (ls - 1), shift = P.loglmax - ls;
+        for (u32 b = threadIdx.x; b < nb; b += blockDim.x) {
+            const u32 row = b >> (logW - 1), k = b & ((W >> 1) - 1);
+            const u32 j = k & (hl - 1), idx = (row << logW) + ((k >> (ls - 1)) << ls) + j;
+            const u32 tk = j << shift;
+            u32 u = x[idx], v = shoup_mul32(x[idx + hl], tw[tk], tws[tk], p);
+            v = v >= p ? v - p : v;
+            x[idx] = addmod_p(u, v, p);
+            x[idx + hl] = submod_p(u, v, p);
+        }
+        __syncthreads();
+    }
+    // columns
+    for (u32 ls = 1; ls <= logH; ls++) {
+        const u32 hl = 1u << (ls - 1), shift = P.loglmax - ls;
+        for (u32 b = threadIdx.x; b < nb; b += blockDim.x) {
+            const u32 col = b & (W - 1), k = b >> logW;
+            const u32 j = k & (hl - 1), r = ((k >> (ls - 1)) << ls) + j;
+            const u32 idx = (r << logW) + col, tk = j << shift;
+            u32 u = x[idx], v = shoup_mul32(x[idx + (hl << logW)], tw[tk], tws[tk], p);
+            v = v >= p ? v - p : v;
+            x[idx] = addmod_p(u, v, p);
+            x[idx + (hl << logW)] = submod_p(u, v, p);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ u32 brv_bits(u32 x, u32 bits) { return bits ? __brev(x) >> (32 - bits) : 0; }

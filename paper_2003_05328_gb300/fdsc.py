@@ -1,0 +1,274 @@
+"""Python binding of libfdsc (argument marshalling only).
+
+Every function here forwards to the entry point of the same name in
+``include/fdsc.h``: it checks shapes and dtypes, allocates outputs with
+PyTorch when the caller gives none, and passes raw device pointers and the
+current CUDA stream.  All arithmetic runs in the CUDA kernels of libfdsc;
+there is no CPU path, and every call raises if the library is missing or
+returns an error.
+
+Dtype mapping: Z_p data (uint32 in the C ABI) travels in torch.int32
+tensors and Z_q data (uint64) in torch.int64 tensors; every value is
+non-negative and below 2^60, so the bit patterns are identical.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfdsc.so")
+
+FDSC_OK = 0
+ERR_NAMES = {-1: "FDSC_ERR_ARG", -2: "FDSC_ERR_NOISE", -3: "FDSC_ERR_OOM", -4: "FDSC_ERR_CUDA",
+             -5: "FDSC_ERR_UNSUPPORTED"}
+
+
+class FdscError(RuntimeError):
+    def __init__(self, code: int, fn: str, msg: str):
+        super().__init__(f"{fn}: {ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ParamsInfo(C.Structure):
+    _fields_ = [(k, C.c_uint32) for k in ("n", "logn", "p", "S", "logS", "d", "g_p", "psi_p")] + \
+               [(k, C.c_uint64) for k in ("q", "g_q", "psi_q", "delta", "r_q")]
+
+
+class Layer(C.Structure):
+    _fields_ = [(k, C.c_uint32) for k in ("B", "Ci", "Co", "H", "W", "g_c", "g_b")]
+
+
+class Layout(C.Structure):
+    _fields_ = [(k, C.c_uint32) for k in ("HW", "T", "GB", "beta", "n_in", "n_out")] + \
+               [(k, C.c_uint64) for k in ("ct_in_words", "ct_out_words", "filter_words", "mask_words",
+                                          "in_spectra_words", "out_spectra_words")]
+
+
+_vp = C.c_void_p
+_PI = C.POINTER(ParamsInfo)
+_PL = C.POINTER(Layer)
+_PO = C.POINTER(Layout)
+_SIGS = {
+    "fdsc_last_error": (C.c_char_p, []),
+    "fdsc_params_query": (C.c_int, [C.c_uint32, C.c_uint32, _PI]),
+    "fdsc_params_create": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(_vp)]),
+    "fdsc_params_destroy": (C.c_int, [_vp]),
+    "fdsc_params_get_info": (C.c_int, [_vp, _PI]),
+    "fdsc_gauss_table": (C.c_int, [_vp]),
+    "fdsc_layout_query": (C.c_int, [C.c_uint32, C.c_uint32, _PL, _PO]),
+    "fdsc_ntt2d": (C.c_int, [_vp, C.c_uint32, C.c_uint32, _vp, _vp, C.c_uint64, _vp]),
+    "fdsc_intt2d": (C.c_int, [_vp, C.c_uint32, C.c_uint32, _vp, _vp, C.c_uint64, _vp]),
+    "fdsc_keygen": (C.c_int, [_vp, C.c_uint64, _vp, _vp]),
+    "fdsc_filter_prepare": (C.c_int, [_vp, _PL, _vp, C.c_uint32, C.c_uint32, _vp, _vp]),
+    "fdsc_mask_prepare": (C.c_int, [_vp, _PL, C.c_uint64, _vp, _vp, _vp]),
+    "fdsc_encrypt": (C.c_int, [_vp, _PL, _vp, _vp, C.c_uint64, _vp, _vp]),
+    "fdsc_homrec": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
+    "fdsc_homconv": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp, _vp]),
+    "fdsc_decrypt": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
+}
+# entry points declared in include/fdsc.h (checked against the library's exports by the tests)
+EXPORTS = tuple(_SIGS)
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libfdsc.so (built by ``paper_2003_05328_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2003_05328_gb300.build.build()")
+        h = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(h, name)
+            f.restype, f.argtypes = res, args
+        _lib = h
+    return _lib
+
+
+def _call(name: str, *args) -> None:
+    rc = getattr(lib(), name)(*args)
+    if rc != FDSC_OK:
+        raise FdscError(rc, name, (lib().fdsc_last_error() or b"").decode())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor, dtype, numel: int, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------- parameters
+def params_query(n: int, p: int) -> ParamsInfo:
+    info = ParamsInfo()
+    _call("fdsc_params_query", n, p, C.byref(info))
+    return info
+
+
+def layout_query(n: int, p: int, layer: "LayerSpec") -> Layout:
+    out = Layout()
+    _call("fdsc_layout_query", n, p, C.byref(layer.c()), C.byref(out))
+    return out
+
+
+def gauss_table():
+    import numpy as np
+
+    out = np.zeros(19, np.uint64)
+    _call("fdsc_gauss_table", out.ctypes.data)
+    return out
+
+
+class Params:
+    """Owner of an ``fdsc_params`` object created on the current device."""
+
+    def __init__(self, n: int, p: int, max_T: int = 256):
+        h = _vp()
+        _call("fdsc_params_create", n, p, max_T, C.byref(h))
+        self.handle = h
+        self.device = torch.cuda.current_device()
+        self.info = ParamsInfo()
+        _call("fdsc_params_get_info", h, C.byref(self.info))
+
+    @property
+    def n(self):
+        return self.info.n
+
+    @property
+    def p(self):
+        return self.info.p
+
+    def close(self):
+        if self.handle:
+            lib().fdsc_params_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass(frozen=True)
+class LayerSpec:
+    B: int
+    Ci: int
+    Co: int
+    H: int
+    W: int
+    g_c: int = 1
+    g_b: int = 1
+
+    def c(self) -> Layer:
+        return Layer(self.B, self.Ci, self.Co, self.H, self.W, self.g_c, self.g_b)
+
+
+def layout(P: Params, L: LayerSpec) -> Layout:
+    return layout_query(P.n, P.p, L)
+
+
+# ---------------------------------------------------------------- transforms
+def _ntt2d(name, P, x, out, stream):
+    H, W = x.shape[-2:]
+    planes = x.numel() // (H * W)
+    if out is None:
+        out = torch.empty_like(x)
+    _call(name, P.handle, H, W, _ptr(x, torch.int32, x.numel(), "x"), _ptr(out, torch.int32, x.numel(), "out"),
+          planes, _stream(stream))
+    return out
+
+
+def ntt2d(P: Params, x: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """Cyclic NTT2D mod p of int32 [..., H, W] planes (Eq. 12, 2-D)."""
+    return _ntt2d("fdsc_ntt2d", P, x, out, stream)
+
+
+def intt2d(P: Params, X: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    return _ntt2d("fdsc_intt2d", P, X, out, stream)
+
+
+# ---------------------------------------------------------------- setup
+def keygen(P: Params, seed: int, out=None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(P.n, dtype=torch.int64, device="cuda")
+    _call("fdsc_keygen", P.handle, seed, _ptr(out, torch.int64, P.n, "t_hat"), _stream(stream))
+    return out
+
+
+def filter_prepare(P: Params, L: LayerSpec, w: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    lay = layout(P, L)
+    Co, Ci, fh, fw = w.shape
+    if (Co, Ci) != (L.Co, L.Ci):
+        raise ValueError("filter shape does not match the layer")
+    if out is None:
+        out = torch.empty(lay.filter_words, dtype=torch.int64, device="cuda")
+    _call("fdsc_filter_prepare", P.handle, C.byref(L.c()), _ptr(w, torch.int8, w.numel(), "w"), fh, fw,
+          _ptr(out, torch.int64, lay.filter_words, "P_hat"), _stream(stream))
+    return out
+
+
+def mask_prepare(P: Params, L: LayerSpec, seed: int, M_hat=None, sB_hat=None, stream=None):
+    lay = layout(P, L)
+    if M_hat is None:
+        M_hat = torch.empty(lay.mask_words, dtype=torch.int64, device="cuda")
+    if sB_hat is None:
+        sB_hat = torch.empty(lay.out_spectra_words, dtype=torch.int32, device="cuda")
+    _call("fdsc_mask_prepare", P.handle, C.byref(L.c()), seed, _ptr(M_hat, torch.int64, lay.mask_words, "M_hat"),
+          _ptr(sB_hat, torch.int32, lay.out_spectra_words, "sB_hat"), _stream(stream))
+    return M_hat, sB_hat
+
+
+# ---------------------------------------------------------------- online
+def encrypt(P: Params, L: LayerSpec, t_hat, X, seed: int, out=None, stream=None) -> torch.Tensor:
+    lay = layout(P, L)
+    if out is None:
+        out = torch.empty(lay.ct_in_words, dtype=torch.int64, device="cuda")
+    _call("fdsc_encrypt", P.handle, C.byref(L.c()), _ptr(t_hat, torch.int64, P.n, "t_hat"),
+          _ptr(X, torch.int32, lay.in_spectra_words, "X"), seed, _ptr(out, torch.int64, lay.ct_in_words, "ct"),
+          _stream(stream))
+    return out
+
+
+def homrec(P: Params, L: LayerSpec, XB, ct, stream=None) -> torch.Tensor:
+    lay = layout(P, L)
+    _call("fdsc_homrec", P.handle, C.byref(L.c()), _ptr(XB, torch.int32, lay.in_spectra_words, "XB"),
+          _ptr(ct, torch.int64, lay.ct_in_words, "ct"), _stream(stream))
+    return ct
+
+
+def homconv(P: Params, L: LayerSpec, ct_in, P_hat, M_hat=None, out=None, stream=None) -> torch.Tensor:
+    lay = layout(P, L)
+    if out is None:
+        out = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
+    m = None if M_hat is None else _ptr(M_hat, torch.int64, lay.mask_words, "M_hat")
+    _call("fdsc_homconv", P.handle, C.byref(L.c()), _ptr(ct_in, torch.int64, lay.ct_in_words, "ct_in"),
+          _ptr(P_hat, torch.int64, lay.filter_words, "P_hat"), m, _ptr(out, torch.int64, lay.ct_out_words, "ct_out"),
+          _stream(stream))
+    return out
+
+
+def decrypt(P: Params, L: LayerSpec, t_hat, ct, out=None, stream=None) -> torch.Tensor:
+    lay = layout(P, L)
+    if out is None:
+        out = torch.empty(lay.out_spectra_words, dtype=torch.int32, device="cuda")
+    _call("fdsc_decrypt", P.handle, C.byref(L.c()), _ptr(t_hat, torch.int64, P.n, "t_hat"),
+          _ptr(ct, torch.int64, lay.ct_out_words, "ct"), _ptr(out, torch.int32, lay.out_spectra_words, "SA_hat"),
+          _stream(stream))
+    return out

@@ -1,0 +1,257 @@
+"""GPU parity: every stage of the CUDA path is bit-identical to the CPU
+oracle on the same seeded inputs (exact integer arithmetic, tolerance zero).
+
+Stage-by-stage checks run at sizes the oracle finishes in seconds (the full
+32x32x64 layer, reduced-batch versions of the other workloads, ragged and
+degenerate shapes); at full batch sizes the composed result is checked with a
+property that holds at any size, s_A + s_B = u * w mod p, on sampled planes
+against the oracle's plain convolution.
+"""
+import numpy as np
+import pytest
+import torch
+
+import fdsc_inputs as FI
+from fdsc_harness import compare_all, dev, gpu_round_trip, u32, u64
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_05328_gb300 import build
+
+    build.build()
+    from paper_2003_05328_gb300 import fdsc
+
+    torch.cuda.set_device(0)
+    return fdsc
+
+
+def _inputs(seed, B, Ci, Co, H, W, fh, fw, p, support=None):
+    g = np.random.default_rng(seed)
+    h, w_ = support or (H, W)
+    xA = np.zeros((B, Ci, H, W), np.uint32)
+    xB = np.zeros((B, Ci, H, W), np.uint32)
+    xA[:, :, :h, :w_] = g.integers(0, p, (B, Ci, h, w_))
+    xB[:, :, :h, :w_] = g.integers(0, p, (B, Ci, h, w_))
+    w = g.integers(-8, 8, (Co, Ci, fh, fw)).astype(np.int8)
+    return xA, xB, w
+
+
+def _check_layer(F, n, p, B, Ci, Co, H, W, fh, fw=None, g_c=None, g_b=1, seed=0, homrec=True, support=None,
+                 xA=None, xB=None, w=None):
+    fw = fw or fh
+    OP = O.params(n, p)
+    OL = O.layer(OP, B, Ci, Co, H, W, g_c, g_b)
+    P = F.Params(n, p, max_T=max(OL.T, 1))
+    L = F.LayerSpec(B, Ci, Co, H, W, OL.g_c, OL.g_b)
+    if xA is None:
+        xA, xB, w = _inputs(seed, B, Ci, Co, H, W, fh, fw, p, support)
+    if not homrec:
+        xB = np.zeros_like(xA)
+    ks, es, ss = 1000 + seed, 2000 + seed, 3000 + seed
+    got = gpu_round_trip(P, L, xA, xB, w, ks, es, ss, homrec=homrec)
+    ref = O.round_trip(OP, OL, xA, xB, w, ks, es, ss, with_homrec=homrec)
+    compare_all(got, ref)
+    y = O.conv_plain(p, (xA.astype(np.int64) + xB) % p, w)
+    assert np.array_equal((got["yA"].reshape(y.shape).astype(np.int64) + got["yB"].reshape(y.shape)) % p, y)
+    P.close()
+    return got, ref
+
+
+# ---------------------------------------------------------------- transforms
+@pytest.mark.parametrize("p", [65537, 12289])
+@pytest.mark.parametrize("H,W,planes", [(2, 2, 3), (4, 64, 5), (64, 4, 2), (8, 8, 7), (16, 16, 64), (32, 32, 64),
+                                        (64, 64, 9), (2, 2048, 2), (32, 32, 2500)])
+def test_ntt2d_intt2d_match_oracle(F, p, H, W, planes):
+    P = F.Params(1024, p)
+    x = np.random.default_rng(H * 131 + W + planes).integers(0, p, (planes, H, W)).astype(np.uint32)
+    X = F.ntt2d(P, dev(x, np.int32))
+    assert np.array_equal(u32(X).reshape(x.shape), O.ntt2d(x, p))
+    back = F.intt2d(P, X)
+    assert np.array_equal(u32(back).reshape(x.shape), x)
+    # in place
+    t = dev(x, np.int32)
+    F.ntt2d(P, t, out=t)
+    assert np.array_equal(u32(t).reshape(x.shape), O.ntt2d(x, p))
+    # a delta transforms to all ones; the inverse of the oracle spectrum is x
+    d = np.zeros((1, H, W), np.uint32)
+    d[0, 0, 0] = 1
+    assert np.all(u32(F.ntt2d(P, dev(d, np.int32))) == 1)
+    assert np.array_equal(u32(F.intt2d(P, dev(O.ntt2d(x, p), np.int32))).reshape(x.shape), x)
+    P.close()
+
+
+def test_ntt2d_empty_batch_is_noop(F):
+    P = F.Params(1024, 65537)
+    x = torch.empty((0, 16, 16), dtype=torch.int32, device="cuda")
+    out = F.ntt2d(P, x)
+    assert out.numel() == 0
+    P.close()
+
+
+@pytest.mark.parametrize("n,p", [(1024, 65537), (2048, 65537), (4096, 65537), (4096, 12289), (16, 65537)])
+def test_keygen_matches_oracle(F, n, p):
+    P = F.Params(n, p)
+    t_hat = F.keygen(P, 424242)
+    _, ref = O.keygen(O.params(n, p), 424242)
+    assert np.array_equal(u64(t_hat), ref)
+    P.close()
+
+
+# ---------------------------------------------------------------- whole layer, every stage
+@pytest.mark.parametrize("cfg", ["cfg0", "cfg1"])
+def test_config_layer_bit_exact(F, cfg):
+    c = FI.CONFIGS[cfg]
+    ls = c.layers[0]
+    S = O.params(ls.n, ls.p).S
+    g_c, g_b = FI.default_pack(ls, S)
+    xA, xB = FI.shares(ls, c.cid)
+    w = FI.weights(ls, c.cid)
+    _check_layer(F, ls.n, ls.p, ls.B, ls.Ci, ls.Co, ls.H, ls.W, ls.fh, ls.fw, g_c, g_b, seed=c.cid, xA=xA, xB=xB,
+                 w=w)
+
+
+@pytest.mark.parametrize("args", [
+    dict(n=256, p=65537, B=3, Ci=5, Co=3, H=8, W=8, fh=3, g_c=2, g_b=2),          # ragged Ci and B
+    dict(n=256, p=65537, B=2, Ci=3, Co=2, H=32, W=16, fh=3),                     # halves (HW > S)
+    dict(n=512, p=12289, B=3, Ci=3, Co=2, H=8, W=8, fh=3, g_c=2, g_b=2),          # p = 12289
+    dict(n=4096, p=12289, B=3, Ci=2, Co=3, H=64, W=64, fh=3),                    # d = 2 slot sets, halves
+    dict(n=4096, p=12289, B=5, Ci=3, Co=2, H=16, W=16, fh=3, g_c=2, g_b=3),       # d = 2 with blocks
+    dict(n=2048, p=65537, B=1, Ci=1, Co=16, H=32, W=32, fh=5, support=(28, 28)), # MNIST-shaped layer
+    dict(n=1024, p=65537, B=2, Ci=7, Co=5, H=16, W=16, fh=3, g_c=3, g_b=1),       # g_c not a power of two
+    dict(n=64, p=65537, B=1, Ci=1, Co=1, H=2, W=2, fh=2),                        # smallest plane, full filter
+    dict(n=1024, p=65537, B=1, Ci=3, Co=2, H=32, W=32, fh=1),                    # 1x1 filter
+    dict(n=1024, p=65537, B=1, Ci=2, Co=2, H=4, W=256, fh=3, fw=5),              # wide plane, fh != fw
+    dict(n=2048, p=65537, B=2, Ci=64, Co=8, H=32, W=32, fh=3, homrec=False),     # first round, no HomRec
+])
+def test_layer_variants_bit_exact(F, args):
+    _check_layer(F, **args)
+
+
+@pytest.mark.parametrize("layer", [0, 1, 2])
+def test_batched_stack_layers_reduced_batch_bit_exact(F, layer):
+    ls = FI.CONFIGS["cfg2"].layers[layer]
+    S = O.params(ls.n, ls.p).S
+    g_c, g_b = FI.default_pack(ls, S)
+    _check_layer(F, ls.n, ls.p, 2, ls.Ci, ls.Co, ls.H, ls.W, ls.fh, ls.fw, g_c, g_b, seed=20 + layer)
+
+
+def test_binarized_layer_reduced_channels_bit_exact(F):
+    ls = FI.CONFIGS["cfg4"].layers[0]
+    g = np.random.default_rng(44)
+    B, Ci, Co = 2, 8, 8
+    xA, xB, _ = _inputs(44, B, Ci, Co, ls.H, ls.W, 3, 3, ls.p)
+    w = (g.integers(0, 2, (Co, Ci, 3, 3)) * 2 - 1).astype(np.int8)
+    _check_layer(F, ls.n, ls.p, B, Ci, Co, ls.H, ls.W, 3, 3, 1, 1, xA=xA, xB=xB, w=w)
+
+
+def test_degenerate_values(F):
+    n, p, B, Ci, Co, H, W = 1024, 65537, 1, 4, 3, 16, 16
+    zeros = np.zeros((B, Ci, H, W), np.uint32)
+    top = np.full((B, Ci, H, W), p - 1, np.uint32)
+    w = np.full((Co, Ci, 3, 3), -8, np.int8)
+    _check_layer(F, n, p, B, Ci, Co, H, W, 3, g_c=4, xA=zeros, xB=zeros.copy(), w=w)
+    _check_layer(F, n, p, B, Ci, Co, H, W, 3, g_c=4, xA=top, xB=top.copy(), w=w)
+    _check_layer(F, n, p, B, Ci, Co, H, W, 3, g_c=4, xA=top, xB=zeros.copy(), w=np.zeros_like(w))
+
+
+def test_homconv_without_mask_and_determinism(F):
+    n, p, B, Ci, Co, H, W = 2048, 65537, 1, 64, 64, 32, 32
+    OP = O.params(n, p)
+    OL = O.layer(OP, B, Ci, Co, H, W, 2, 1)
+    P = F.Params(n, p)
+    L = F.LayerSpec(B, Ci, Co, H, W, 2, 1)
+    g = np.random.default_rng(5)
+    ct = np.array(g.integers(0, OP.q, (OL.n_in, 2, n), dtype=np.uint64))
+    Ph = np.array(g.integers(0, OP.q, (Co * OL.T, n), dtype=np.uint64))
+    ct[0, 0, :8] = OP.q - 1  # extremes
+    Ph[0, :8] = OP.q - 1
+    ref = O.homconv(OP, OL, ct, Ph, None)
+    a = F.homconv(P, L, dev(ct.view(np.int64), np.int64), dev(Ph.view(np.int64), np.int64))
+    b = F.homconv(P, L, dev(ct.view(np.int64), np.int64), dev(Ph.view(np.int64), np.int64))
+    assert np.array_equal(u64(a).reshape(ref.shape), ref)
+    assert torch.equal(a, b)
+    P.close()
+
+
+def test_homconv_many_terms_folds_accumulator(F):
+    # T = 300 > 256: the 128-bit accumulator must be reduced part way.
+    n, p, B, Ci, Co, H, W = 64, 65537, 1, 300, 2, 8, 8
+    OP = O.params(n, p)
+    OL = O.layer(OP, B, Ci, Co, H, W, 1, 1)
+    P = F.Params(n, p, max_T=300)
+    L = F.LayerSpec(B, Ci, Co, H, W, 1, 1)
+    ct = np.full((OL.n_in, 2, n), OP.q - 1, np.uint64)
+    Ph = np.full((Co * OL.T, n), OP.q - 1, np.uint64)
+    ref = O.homconv(OP, OL, ct, Ph, None)
+    got = F.homconv(P, L, dev(ct.view(np.int64), np.int64), dev(Ph.view(np.int64), np.int64))
+    assert np.array_equal(u64(got).reshape(ref.shape), ref)
+    P.close()
+
+
+# ---------------------------------------------------------------- full sizes (property checks)
+def _full_size_property(F, ls, cid, g_c, g_b, sample_planes):
+    P = F.Params(ls.n, ls.p, max_T=256)
+    L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
+    xA, xB = FI.shares(ls, cid)
+    w = FI.weights(ls, cid)
+    ks, es, ss = FI.seeds(cid)
+    got = gpu_round_trip(P, L, xA, xB, w, ks, es, ss)
+    y = (got["yA"].reshape(ls.B, ls.Co, ls.H, ls.W).astype(np.int64) +
+         got["yB"].reshape(ls.B, ls.Co, ls.H, ls.W)) % ls.p
+    x = (xA.astype(np.int64) + xB) % ls.p
+    rng = np.random.default_rng(cid)
+    for _ in range(sample_planes):
+        b, co = int(rng.integers(ls.B)), int(rng.integers(ls.Co))
+        ref = O.conv_plain(ls.p, x[b:b + 1], w[co:co + 1])
+        assert np.array_equal(y[b, co], ref[0, 0]), (b, co)
+    # Bob's mask is uniform and Alice's share alone is not the result
+    assert not np.array_equal(got["yA"].reshape(y.shape), y)
+    P.close()
+
+
+@pytest.mark.parametrize("layer", [0, 1, 2])
+def test_batched_stack_full_batch_property(F, layer):
+    ls = FI.CONFIGS["cfg2"].layers[layer]
+    g_c, g_b = FI.default_pack(ls, O.params(ls.n, ls.p).S)
+    _full_size_property(F, ls, 2, g_c, g_b, 6)
+
+
+def test_binarized_layer_full_size_property(F):
+    ls = FI.CONFIGS["cfg4"].layers[0]
+    _full_size_property(F, ls, 4, 1, 1, 4)
+
+
+# ---------------------------------------------------------------- errors
+def test_argument_errors_are_reported(F):
+    P = F.Params(2048, 65537, max_T=16)
+    L = F.LayerSpec(1, 64, 64, 32, 32, 2, 1)  # T = 32 > max_T
+    lay = F.layout(P, L)
+    ct = torch.zeros(lay.ct_in_words, dtype=torch.int64, device="cuda")
+    Ph = torch.zeros(lay.filter_words, dtype=torch.int64, device="cuda")
+    with pytest.raises(F.FdscError) as e:
+        F.homconv(P, L, ct, Ph)
+    assert e.value.code == -2
+    L2 = F.LayerSpec(1, 32, 64, 32, 32, 2, 1)
+    lay2 = F.layout(P, L2)
+    big = torch.zeros(lay2.ct_in_words + lay2.ct_out_words, dtype=torch.int64, device="cuda")
+    with pytest.raises(F.FdscError) as e:  # output overlapping the input
+        F._call("fdsc_homconv", P.handle, F.C.byref(L2.c()), big.data_ptr(), Ph.data_ptr(), None,
+                     big.data_ptr() + 8 * 16, 0)
+    assert e.value.code == -1
+    x = torch.zeros(2 * 16 * 16 + 1, dtype=torch.int32, device="cuda")
+    with pytest.raises(F.FdscError) as e:  # misaligned
+        F._call("fdsc_ntt2d", P.handle, 16, 16, x.data_ptr() + 4, x.data_ptr(), 2, 0)
+    assert e.value.code == -1
+    with pytest.raises(F.FdscError) as e:  # bad plane
+        F._call("fdsc_ntt2d", P.handle, 12, 16, x.data_ptr(), x.data_ptr(), 1, 0)
+    assert e.value.code == -1
+    with pytest.raises(F.FdscError) as e:  # noise bound at creation
+        F.Params(4096, 65537, max_T=100000)
+    assert e.value.code == -2
+    P.close()
