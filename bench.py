@@ -1,0 +1,398 @@
+"""Benchmark of the FDSC hot path on GB300.
+
+One step = one image through one convolution layer, every online stage of
+Fig. 2 plus HomRec: NTT2D(x_A) -> encrypt -> NTT2D(x_B) -> HomRec ->
+HomConv + HomShare -> decrypt -> INTT2D(s_A) -> INTT2D(s_B), on the
+32x32x64 -> 64 CIFAR-shaped layer (batch 1, 3x3 filters, n = 2048,
+p = 65537, 60-bit q).  Keys, filter spectra and HomShare masks are prepared
+before timing (the paper's t_setup); the step is the paper's t_online.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+The device number (`value`) replays the step as a CUDA graph with inputs
+resident in HBM; L2 is flushed (a write larger than L2) before every timed
+step, outside its events.  `e2e` runs the same step through the Python
+binding of the C ABI from pinned host buffers, copies in and out included.
+`--impl reference` times the CPU oracle (single thread) on a bounded sample.
+Under torchrun every rank runs an independent replica on its own GPU (the
+path has no exchange step) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fdsc_inputs as FI  # noqa: E402
+
+METRIC = "HomConv layers/s & mod-q MAC/s at 32×32×64; p50/p99 served latency"
+WORKLOAD = "cfg1"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "homconv_traffic.json")
+KERNEL_SOURCES = ["paper_2003_05328_gb300/csrc/homconv.cu", "paper_2003_05328_gb300/csrc/modarith.cuh",
+                  "paper_2003_05328_gb300/csrc/fdsc_internal.h"]
+
+
+def kernel_digest() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def aggregate(local_seconds: float, local_units: float, world: int):
+    """Whole-job figures: total units over the slowest rank's time."""
+    if world == 1:
+        return local_seconds, local_units
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([local_units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def layer_counts(ls, T, beta, GB, n):
+    """Algorithmic bytes and modular products of one HomConv launch (filter
+    read once, per image group the input, output and mask words)."""
+    filt = 8 * ls.Co * T * beta * n
+    per_group = 8 * (2 * T * beta * n + 2 * ls.Co * beta * n + ls.Co * beta * n)
+    macs = 2 * ls.Co * T * beta * n * GB
+    return filt + GB * per_group, macs
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu, self.proc, self.path = gpu_index, None, None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline leg only)
+def oracle_online_sample(budget_s: float, co_sample: int = 8):
+    """Time the oracle's online stages on the bench layer: the input side
+    (NTT2D x2, encrypt, HomRec) once per round and the output side (HomConv,
+    decrypt, INTT2D x2) for `co_sample` of the Co output channels, repeated
+    until `budget_s` is spent.  The output side is independent per output
+    channel, so one layer costs t_in + t_out * Co / co_sample."""
+    from oracle import oracle as O
+
+    c = FI.CONFIGS[WORKLOAD]
+    ls = c.layers[0]
+    P = O.params(ls.n, ls.p)
+    g_c, g_b = FI.default_pack(ls, P.S)
+    L = O.layer(P, ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
+    Ls = O.layer(P, ls.B, ls.Ci, co_sample, ls.H, ls.W, g_c, g_b)
+    xA, xB = FI.shares(ls, c.cid)
+    w = FI.weights(ls, c.cid)
+    ks, es, ss = FI.seeds(c.cid)
+    _, t_hat = O.keygen(P, ks)
+    Phat = O.filter_prepare(P, Ls, w[:co_sample])
+    Mhat, sB = O.mask_prepare(P, Ls, ss)
+    t_in, t_out, rounds = 0.0, 0.0, 0
+    t0 = time.perf_counter()
+    while rounds < 1 or time.perf_counter() - t0 < budget_s:
+        a = time.perf_counter()
+        XA = O.ntt2d(xA, ls.p).reshape(ls.B, ls.Ci, -1)
+        ct = O.encrypt(P, L, t_hat, XA, es)
+        XB = O.ntt2d(xB, ls.p).reshape(ls.B, ls.Ci, -1)
+        ct = O.homrec(P, L, ct, XB)
+        b = time.perf_counter()
+        out = O.homconv(P, Ls, ct, Phat, Mhat)
+        SA, _ = O.decrypt(P, Ls, t_hat, out)
+        O.ntt2d(SA.reshape(ls.B, co_sample, ls.H, ls.W), ls.p, inverse=True)
+        O.ntt2d(sB.reshape(ls.B, co_sample, ls.H, ls.W), ls.p, inverse=True)
+        e = time.perf_counter()
+        t_in += b - a
+        t_out += e - b
+        rounds += 1
+    per_layer = (t_in + t_out * ls.Co / co_sample) / rounds
+    sample = (f"{rounds} round(s) of the {WORKLOAD} layer's online stages: input side in full, output side "
+              f"(HomConv+HomShare, decrypt, INTT2D x2) for {co_sample}/{ls.Co} output channels, scaled to the "
+              f"full layer; single thread")
+    return per_layer, sample
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    budget = max(0.05, min(1.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_online_sample(0.0)
+    per = []
+    for _ in range(args.steps):
+        t, sample = oracle_online_sample(budget)
+        per.append(t)
+    sec = float(np.mean(per))
+    ls = FI.CONFIGS[WORKLOAD].layers[0]
+    value = 1.0 / sec
+    line = {"metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "layer": "32x32x64->64 3x3", "batch": ls.B, "n": ls.n, "p": ls.p,
+                       "q_bits": 60, "l2": "cpu"},
+            "mac_per_s": value * 2 * ls.Co * ls.Ci * ls.H * ls.W,
+            "cpu_baseline": {"value": value, "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, local_rank, world):
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    from paper_2003_05328_gb300 import build as B
+
+    B.build()
+    from paper_2003_05328_gb300 import fdsc as F
+
+    c = FI.CONFIGS[WORKLOAD]
+    ls = c.layers[0]
+    info = F.params_query(ls.n, ls.p)
+    g_c, g_b = FI.default_pack(ls, info.S)
+    L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
+    P = F.Params(ls.n, ls.p, max_T=64)
+    lay = F.layout(P, L)
+    xA_h, xB_h = FI.shares(ls, c.cid)
+    w_h = FI.weights(ls, c.cid)
+    ks, es, ss = FI.seeds(c.cid)
+    dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
+
+    # setup (t_setup)
+    t_hat = F.keygen(P, ks)
+    Phat = F.filter_prepare(P, L, dev(w_h, np.int8))
+    Mhat, sB = F.mask_prepare(P, L, ss)
+    xA, xB = dev(xA_h, np.int32), dev(xB_h, np.int32)
+    XA, XB = torch.empty_like(xA), torch.empty_like(xB)
+    ct = torch.empty(lay.ct_in_words, dtype=torch.int64, device="cuda")
+    ct_out = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
+    SA = torch.empty(lay.out_spectra_words, dtype=torch.int32, device="cuda")
+    yA = torch.empty((ls.B, ls.Co, ls.H, ls.W), dtype=torch.int32, device="cuda")
+    yB = torch.empty_like(yA)
+    sB4 = sB.view(ls.B, ls.Co, ls.H, ls.W)
+    LAUNCHES_PER_STEP = 8
+
+    def step():
+        F.ntt2d(P, xA, out=XA)
+        F.encrypt(P, L, t_hat, XA, es, out=ct)
+        F.ntt2d(P, xB, out=XB)
+        F.homrec(P, L, XB, ct)
+        F.homconv(P, L, ct, Phat, Mhat, out=ct_out)
+        F.decrypt(P, L, t_hat, ct_out, out=SA)
+        F.intt2d(P, SA.view(ls.B, ls.Co, ls.H, ls.W), out=yA)
+        F.intt2d(P, sB4, out=yB)
+
+    l2 = torch.cuda.get_device_properties(local_rank).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.int32, device="cuda")
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            step()
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        g.replay()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record()
+        g.replay()
+        ends[i].record()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+    # HomConv launches alone, same launch configuration, L2 flushed before each
+    hc_steps = max(20, min(args.steps, 2000))
+    hs = [torch.cuda.Event(enable_timing=True) for _ in range(hc_steps)]
+    he = [torch.cuda.Event(enable_timing=True) for _ in range(hc_steps)]
+    for i in range(hc_steps):
+        flush.fill_(i & 0xFF)
+        hs[i].record()
+        F.homconv(P, L, ct, Phat, Mhat, out=ct_out)
+        he[i].record()
+    torch.cuda.synchronize()
+    hc_ms = [a.elapsed_time(b) for a, b in zip(hs, he)]
+    clk = clocks.stop()
+
+    # end to end through the public API: pinned host in, host out
+    e2e_steps = max(10, min(args.steps, 500))
+    xA_pin = torch.from_numpy(xA_h.astype(np.int32)).pin_memory()
+    xB_pin = torch.from_numpy(xB_h.astype(np.int32)).pin_memory()
+    yA_pin = torch.empty(yA.shape, dtype=torch.int32).pin_memory()
+    yB_pin = torch.empty(yB.shape, dtype=torch.int32).pin_memory()
+    es_ = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
+    ee_ = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
+    for i in range(e2e_steps):
+        flush.fill_(i & 0xFF)
+        es_[i].record()
+        xA.copy_(xA_pin, non_blocking=True)
+        xB.copy_(xB_pin, non_blocking=True)
+        step()
+        yA_pin.copy_(yA, non_blocking=True)
+        yB_pin.copy_(yB, non_blocking=True)
+        ee_[i].record()
+        ee_[i].synchronize()
+    e2e_ms = [a.elapsed_time(b) for a, b in zip(es_, ee_)]
+    h2d = xA_pin.numel() * 4 + xB_pin.numel() * 4
+    d2h = yA_pin.numel() * 4 + yB_pin.numel() * 4
+
+    local_sec = sum(step_ms) / 1e3
+    tot_sec, tot_units = aggregate(local_sec, float(args.steps * ls.B), world)
+    e2e_sec, e2e_units = aggregate(sum(e2e_ms) / 1e3, float(e2e_steps * ls.B), world)
+    if rank != 0:
+        return
+    value = tot_units / tot_sec
+    hc_avg = float(np.mean(hc_ms))
+    alg_bytes, macs = layer_counts(ls, lay.T, lay.beta, lay.GB, ls.n)
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = alg_bytes / (hc_avg * 1e-3) / 1e9
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        tr = json.load(open(TRAFFIC_FILE))
+        if tr.get("kernel_digest") == kernel_digest() and tr.get("workload") == WORKLOAD:
+            traffic = tr.get("dram_bytes_per_launch")
+    useful_macs = 2 * ls.Co * ls.Ci * ls.H * ls.W * ls.B
+    cpu = None
+    if not args.no_cpu_baseline:
+        per_layer, sample = oracle_online_sample(args.cpu_seconds)
+        cpu = {"value": 1.0 / per_layer, "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "layer": "32x32x64->64 3x3", "batch": ls.B, "n": ls.n, "p": ls.p,
+                   "q_bits": 60, "packing": {"g_c": g_c, "g_b": g_b, "T": lay.T},
+                   "l2": "flushed before every timed step (write of %d MiB)" % (flush.numel() * 4 >> 20),
+                   "step": "ntt2d,encrypt,ntt2d,homrec,homconv+homshare,decrypt,intt2d,intt2d (CUDA graph)"},
+        "mac_per_s": value * 2 * ls.Co * ls.Ci * ls.H * ls.W,
+        "homconv_layers_per_s": ls.B / (hc_avg * 1e-3),
+        "homconv_mac_per_s": macs / (hc_avg * 1e-3),
+        "useful_macs_per_layer": useful_macs // ls.B,
+        "step_ms_p50": float(np.percentile(step_ms, 50)), "step_ms_p99": float(np.percentile(step_ms, 99)),
+        "roofline": {"kernel": "homconv_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_source": peak_src + " (hbm_gbs, burst copy)", "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "alg_bytes_per_launch": alg_bytes, "launch_us": hc_avg * 1e3},
+        "e2e": {"value": e2e_units / e2e_sec, "unit": "layers/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms),
+                "path": "python binding of the C ABI, eager launches, pinned host buffers"},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps + hc_steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    P.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="fdsc", choices=["fdsc", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "fdsc" else "gloo"
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gpu(args, rank, local_rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

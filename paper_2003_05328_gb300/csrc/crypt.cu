@@ -9,6 +9,10 @@
 //   K7 filter_prepare  Fig. 2 line 3: w_hat packed, lifted, NTT_q
 //   K8 mask_prepare    Eq. 2 (HomShare) randomness and its NTT_q image
 //   K5 decrypt         Sec. 3.1 decryption, slot decode, channel-block fold
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "modarith.cuh"
 
 namespace {
@@ -251,10 +255,21 @@ __global__ void __launch_bounds__(kThreads) decrypt_kernel(DevParams P, DevLayer
     }
 }
 
+// Opt a kernel in to more than the default 48 KiB of dynamic shared memory
+// (leaving room for its static shared arrays); done once per kernel and size.
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (bytes + 1024 <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = done[{reinterpret_cast<const void*>(kernel), dev}];
+    if (have >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
 }
 
 }  // namespace
