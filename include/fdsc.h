@@ -178,6 +178,16 @@ int fdsc_homconv(const fdsc_params* P, const fdsc_layer* L, const uint64_t* ct_i
 int fdsc_decrypt(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat,
                  const uint64_t* ct, uint32_t* SA_hat, void* stream);
 
+/* ---------------------------------------------------------------------- */
+/* Tuning                                                                  */
+/* ---------------------------------------------------------------------- */
+/* Selects the HomConv kernel variant for later fdsc_homconv calls in this
+ * process (all variants give identical results): 0 automatic (default),
+ * 1 limb-column accumulation with one image group per thread, 2 the same
+ * with two image groups per thread, 3 carry-chained 128-bit accumulation.
+ * FDSC_ERR_ARG for other values.  Not synchronised with concurrent calls. */
+int fdsc_set_homconv_variant(int variant);
+
 #ifdef __cplusplus
 }
 #endif

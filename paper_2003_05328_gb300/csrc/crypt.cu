@@ -17,7 +17,14 @@
 
 namespace {
 
-constexpr u32 kThreads = 256;
+constexpr u32 kMaxThreads = 512;
+
+// One CTA per ring element: n/8 threads (8 coefficients each in the radix-8
+// passes), at least one warp.
+inline u32 threads_for(u32 n, u32 hw = 0) {
+    u32 t = n / 8 > hw / 8 ? n / 8 : hw / 8;
+    return t < 32 ? 32 : t;
+}
 
 // Packed input slot: slot s of slot set r of input ciphertext (bb, k, h).
 // HW <= S: block s / HW holds image (bb d + r) g_b + blk / g_c and channel
@@ -46,7 +53,7 @@ __device__ __forceinline__ u64 add_signed_mod_q(u64 v, int e, u64 q) {
 }
 
 // ---------------------------------------------------------------- keygen
-__global__ void __launch_bounds__(kThreads) keygen_kernel(DevParams P, u64 seed, u64* t_hat) {
+__global__ void __launch_bounds__(kMaxThreads) keygen_kernel(DevParams P, u64 seed, u64* t_hat) {
     extern __shared__ u64 c[];
     const u64 key = stream_key(seed, DOM_T);
     for (u32 i = threadIdx.x; i < P.n; i += blockDim.x) {
@@ -54,14 +61,14 @@ __global__ void __launch_bounds__(kThreads) keygen_kernel(DevParams P, u64 seed,
         c[i] = t3 == 0 ? P.q - 1 : (u64)(t3 - 1);
     }
     __syncthreads();
-    ntt_q_fwd(c, P);
+    ntt_q_fwd8(c, P);
     for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) t_hat[j] = c[j];
 }
 
 // ---------------------------------------------------------------- encrypt / homrec
 // mode 0: encrypt X into ct; mode 1: HomRec, add the encoding of X to c1.
 template <int kMode>
-__global__ void __launch_bounds__(kThreads) encode_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
+__global__ void __launch_bounds__(kMaxThreads) encode_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
                                                           const u32* __restrict__ X, u64 seed, u64* ct) {
     extern __shared__ u64 smem[];
     u64* c = smem;                                       // [n]
@@ -73,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) encode_kernel(DevParams P, DevLayer 
     for (u32 sg = threadIdx.x; sg < P.n; sg += blockDim.x)
         slots[sg] = input_slot(P, L, X, bb, k, h, sg >> P.logS, sg & (P.S - 1));
     __syncthreads();
-    ntt_p_inv(slots, P.d, P);  // slot encode, per slot set
+    ntt_p_inv8(slots, P.d, P);  // slot encode, per slot set
     const u64 keyE = stream_key(seed, DOM_E);
     for (u32 sg = threadIdx.x; sg < P.n; sg += blockDim.x) {
         const u32 r = sg >> P.logS, i = sg & (P.S - 1), coef = r + P.d * i;
@@ -82,7 +89,7 @@ __global__ void __launch_bounds__(kThreads) encode_kernel(DevParams P, DevLayer 
         c[coef] = v;
     }
     __syncthreads();
-    ntt_q_fwd(c, P);
+    ntt_q_fwd8(c, P);
     u64* c0 = ct + (u64)u * 2 * P.n;
     u64* c1 = c0 + P.n;
     if (kMode == 0) {
@@ -101,7 +108,7 @@ __global__ void __launch_bounds__(kThreads) encode_kernel(DevParams P, DevLayer 
 // ---------------------------------------------------------------- filter prepare
 // One CTA per filter plaintext (co, k, h).  The channel spectra it needs are
 // computed here with the shared NTT2D plane routine.
-__global__ void __launch_bounds__(kThreads) filter_kernel(DevParams P, DevLayer L, const int8_t* __restrict__ w,
+__global__ void __launch_bounds__(kMaxThreads) filter_kernel(DevParams P, DevLayer L, const int8_t* __restrict__ w,
                                                           u32 fh, u32 fw, u64* __restrict__ Phat) {
     extern __shared__ u64 smem[];
     const u32 cbytes = P.n * 8, pbytes = L.HW * 4;
@@ -118,25 +125,33 @@ __global__ void __launch_bounds__(kThreads) filter_kernel(DevParams P, DevLayer 
         __syncthreads();
         for (u32 e = threadIdx.x; e < L.HW; e += blockDim.x) plane[e] = 0;
         __syncthreads();
+        // DIF (natural in, both axes bit-reversed out) when the plane allows
+        // radix-8 lines; otherwise bit-reversed in, natural out.
+        const bool dif = L.logH >= 3 && L.logW >= 3;
         const int8_t* wf = w + ((u64)co * L.Ci + ci) * fh * fw;
         for (u32 e = threadIdx.x; e < fh * fw; e += blockDim.x) {
             const u32 a = e / fw, b = e % fw;
             const int wv = wf[e];
-            plane[(brv_bits(a, L.logH) << L.logW) + brv_bits(b, L.logW)] = (u32)(wv < 0 ? (int)P.p + wv : wv);
+            const u32 pos = dif ? (a << L.logW) + b : (brv_bits(a, L.logH) << L.logW) + brv_bits(b, L.logW);
+            plane[pos] = (u32)(wv < 0 ? (int)P.p + wv : wv);
         }
         __syncthreads();
-        ntt2d_plane(plane, L.logH, L.logW, false, P);
+        if (dif) ntt2d_plane_dif(plane, L.logH, L.logW, false, P);
+        else ntt2d_plane(plane, L.logH, L.logW, false, P);
+        auto at = [&](u32 f) {
+            return dif ? plane[(brv_bits(f >> L.logW, L.logH) << L.logW) + brv_bits(f & (L.W - 1), L.logW)] : plane[f];
+        };
         if (L.beta == 1) {
             for (u32 e = threadIdx.x; e < L.g_b * L.HW; e += blockDim.x) {
                 const u32 ib = e >> (L.logH + L.logW), f = e & (L.HW - 1);
-                slots[(ib * L.g_c + ic) * L.HW + f] = plane[f];
+                slots[(ib * L.g_c + ic) * L.HW + f] = at(f);
             }
         } else {
-            for (u32 s = threadIdx.x; s < P.S; s += blockDim.x) slots[s] = plane[h * P.S + s];
+            for (u32 s = threadIdx.x; s < P.S; s += blockDim.x) slots[s] = at(h * P.S + s);
         }
     }
     __syncthreads();
-    ntt_p_inv(slots, 1, P);
+    ntt_p_inv8(slots, 1, P);
     for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) c[j] = 0;
     __syncthreads();
     for (u32 i = threadIdx.x; i < P.S; i += blockDim.x) {
@@ -144,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) filter_kernel(DevParams P, DevLayer 
         c[(u64)P.d * i] = m <= (P.p - 1) / 2 ? (u64)m : P.q - (P.p - m);  // centred lift
     }
     __syncthreads();
-    ntt_q_fwd(c, P);
+    ntt_q_fwd8(c, P);
     u64* out = Phat + (u64)v * P.n;
     for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) out[j] = c[j];
 }
@@ -160,7 +175,7 @@ __device__ __forceinline__ u32 mask_value(const DevParams& P, const DevLayer& L,
     return v;
 }
 
-__global__ void __launch_bounds__(kThreads) mask_kernel(DevParams P, DevLayer L, u64 seed, u64* __restrict__ Mhat,
+__global__ void __launch_bounds__(kMaxThreads) mask_kernel(DevParams P, DevLayer L, u64 seed, u64* __restrict__ Mhat,
                                                         u32* __restrict__ sB) {
     extern __shared__ u64 smem[];
     u64* c = smem;
@@ -193,13 +208,13 @@ __global__ void __launch_bounds__(kThreads) mask_kernel(DevParams P, DevLayer L,
         slots[sg] = val;
     }
     __syncthreads();
-    ntt_p_inv(slots, P.d, P);
+    ntt_p_inv8(slots, P.d, P);
     for (u32 sg = threadIdx.x; sg < P.n; sg += blockDim.x) {
         const u32 r = sg >> P.logS, i = sg & (P.S - 1);
         c[r + P.d * i] = P.delta * slots[sg];
     }
     __syncthreads();
-    ntt_q_fwd(c, P);
+    ntt_q_fwd8(c, P);
     u64* out = Mhat + (u64)v * P.n;
     for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) out[j] = c[j];
 }
@@ -218,7 +233,7 @@ __device__ __forceinline__ u32 round_pq(u64 v, const DevParams& P) {
     return (u32)(z >= P.p ? z - P.p : z);
 }
 
-__global__ void __launch_bounds__(kThreads) decrypt_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
+__global__ void __launch_bounds__(kMaxThreads) decrypt_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
                                                            const u64* __restrict__ ct, u32* __restrict__ SA) {
     extern __shared__ u64 smem[];
     u64* c = smem;
@@ -229,13 +244,13 @@ __global__ void __launch_bounds__(kThreads) decrypt_kernel(DevParams P, DevLayer
     const u64* c1 = c0 + P.n;
     for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) c[j] = addmod_q(mulmod_q(c0[j], t_hat[j], P), c1[j], P.q);
     __syncthreads();
-    ntt_q_inv(c, P);
+    ntt_q_inv8(c, P);
     for (u32 coef = threadIdx.x; coef < P.n; coef += blockDim.x) {
         const u32 r = coef & (P.d - 1), i = coef / P.d;
         slots[r * P.S + i] = round_pq(c[coef], P);
     }
     __syncthreads();
-    ntt_p_fwd(slots, P.d, P);  // slot decode
+    ntt_p_fwd8(slots, P.d, P);  // slot decode
     if (L.beta == 1) {
         const u32 per_set = L.g_b * L.HW;
         for (u32 e = threadIdx.x; e < P.d * per_set; e += blockDim.x) {
@@ -278,7 +293,7 @@ cudaError_t launch_keygen(const DevParams& P, u64 seed, u64* t_hat, cudaStream_t
     const size_t sm = (size_t)P.n * 8;
     cudaError_t e = set_smem(keygen_kernel, sm);
     if (e != cudaSuccess) return e;
-    keygen_kernel<<<1, kThreads, sm, s>>>(P, seed, t_hat);
+    keygen_kernel<<<1, threads_for(P.n), sm, s>>>(P, seed, t_hat);
     return cudaGetLastError();
 }
 
@@ -287,7 +302,7 @@ cudaError_t launch_encrypt(const DevParams& P, const DevLayer& L, const u64* t_h
     const size_t sm = (size_t)P.n * 12;
     cudaError_t e = set_smem(encode_kernel<0>, sm);
     if (e != cudaSuccess) return e;
-    encode_kernel<0><<<L.n_in, kThreads, sm, s>>>(P, L, t_hat, X, seed, ct);
+    encode_kernel<0><<<L.n_in, threads_for(P.n), sm, s>>>(P, L, t_hat, X, seed, ct);
     return cudaGetLastError();
 }
 
@@ -295,7 +310,7 @@ cudaError_t launch_homrec(const DevParams& P, const DevLayer& L, const u32* XB, 
     const size_t sm = (size_t)P.n * 12;
     cudaError_t e = set_smem(encode_kernel<1>, sm);
     if (e != cudaSuccess) return e;
-    encode_kernel<1><<<L.n_in, kThreads, sm, s>>>(P, L, nullptr, XB, 0, ct);
+    encode_kernel<1><<<L.n_in, threads_for(P.n), sm, s>>>(P, L, nullptr, XB, 0, ct);
     return cudaGetLastError();
 }
 
@@ -306,7 +321,7 @@ cudaError_t launch_filter_prepare(const DevParams& P, const DevLayer& L, const i
     cudaError_t e = set_smem(filter_kernel, sm);
     if (e != cudaSuccess) return e;
     const u32 grid = L.Co * L.T * L.beta;
-    filter_kernel<<<grid, kThreads, sm, s>>>(P, L, w, fh, fw, Phat);
+    filter_kernel<<<grid, threads_for(P.n, L.HW), sm, s>>>(P, L, w, fh, fw, Phat);
     return cudaGetLastError();
 }
 
@@ -315,7 +330,7 @@ cudaError_t launch_mask_prepare(const DevParams& P, const DevLayer& L, u64 seed,
     const size_t sm = (size_t)P.n * 12;
     cudaError_t e = set_smem(mask_kernel, sm);
     if (e != cudaSuccess) return e;
-    mask_kernel<<<L.n_out, kThreads, sm, s>>>(P, L, seed, Mhat, sB);
+    mask_kernel<<<L.n_out, threads_for(P.n), sm, s>>>(P, L, seed, Mhat, sB);
     return cudaGetLastError();
 }
 
@@ -324,6 +339,6 @@ cudaError_t launch_decrypt(const DevParams& P, const DevLayer& L, const u64* t_h
     const size_t sm = (size_t)P.n * 12;
     cudaError_t e = set_smem(decrypt_kernel, sm);
     if (e != cudaSuccess) return e;
-    decrypt_kernel<<<L.n_out, kThreads, sm, s>>>(P, L, t_hat, ct, SA);
+    decrypt_kernel<<<L.n_out, threads_for(P.n), sm, s>>>(P, L, t_hat, ct, SA);
     return cudaGetLastError();
 }

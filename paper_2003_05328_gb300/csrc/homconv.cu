@@ -7,18 +7,38 @@
 //   out[bb][co][h][c][j] = sum_k in[bb][k][h][c][j] * P[co][k][h][j]  (mod q)
 // followed by the HomShare mask subtraction on c = 1.
 //
-// Each thread owns one index J = (h, j) and a chunk of output channels; the
-// 60-bit x 60-bit products are accumulated exactly in 128 bits with
-// carry-chained 32-bit multiply-adds and reduced once per output (and every
-// 256 terms, so that T (q-1)^2 < 2^128 always holds).  A warp reads 32
-// consecutive uint64 of every operand row: fully coalesced.
+// Work split: a CTA has 4 warps, one output channel per warp, and covers 64
+// consecutive evaluation indices (2 per lane, so every operand row is read
+// with 16-byte loads, fully coalesced).  Each thread also serves NB image
+// groups, reusing every filter word from registers NB times.  The k loop is
+// unrolled so that each thread keeps several 16-byte loads in flight; the
+// input words are shared by the 4 warps through L1.
+//
+// Exact accumulation (both variants keep the true integer sum, reduced to
+// [0, q) only at the end and every 256 terms, since 256 (q-1)^2 < 2^128):
+//  - kWide:  operands split into 30-bit limbs (q < 2^60), the four limb
+//            products accumulated with 32x32+64-bit multiply-adds into 64-bit
+//            columns that are carried forward every 8 terms;
+//  - !kWide: a 128-bit accumulator updated with carry-chained 32-bit
+//            multiply-adds (10 per product).
+#include <type_traits>
+
 #include "modarith.cuh"
 
 namespace {
 
-// acc += a * b as 128-bit integers.  With a = a1 2^32 + a0 and b likewise:
-// a0 b0 + a1 b1 2^64 in one carry chain, then a0 b1 2^32 and a1 b0 2^32.
-__device__ __forceinline__ void mac128(u32 (&acc)[4], u64 a, u64 b) {
+constexpr u32 kWarps = 4;           // output channels per CTA
+constexpr u32 kJT = 64;             // evaluation indices per CTA
+constexpr u32 kThreads = 32 * kWarps;
+constexpr u32 kUnroll = 4;          // k terms per load batch
+constexpr u64 kM30 = (1ull << 30) - 1;
+
+// ---- 128-bit carry-chain accumulator
+struct Acc128 {
+    u32 w[4];
+};
+__device__ __forceinline__ void acc_zero(Acc128& a) { a.w[0] = a.w[1] = a.w[2] = a.w[3] = 0; }
+__device__ __forceinline__ void acc_mac(Acc128& acc, u64 a, u64 b) {
     const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
     asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
         "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
@@ -30,90 +50,197 @@ __device__ __forceinline__ void mac128(u32 (&acc)[4], u64 a, u64 b) {
         "mad.lo.cc.u32  %1, %5, %6, %1;\n\t"
         "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
         "addc.u32       %3, %3, 0;"
-        : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3])
+        : "+r"(acc.w[0]), "+r"(acc.w[1]), "+r"(acc.w[2]), "+r"(acc.w[3])
         : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
 }
+__device__ __forceinline__ u64 acc_reduce(const Acc128& a, const DevParams& P) {
+    return reduce128(((u64)a.w[3] << 32) | a.w[2], ((u64)a.w[1] << 32) | a.w[0], P);
+}
+__device__ __forceinline__ void acc_set(Acc128& a, u64 r) {
+    a.w[0] = (u32)r;
+    a.w[1] = (u32)(r >> 32);
+    a.w[2] = a.w[3] = 0;
+}
 
-__device__ __forceinline__ u64 reduce_acc(const u32 (&acc)[4], const DevParams& P) {
-    const u64 lo = ((u64)acc[1] << 32) | acc[0], hi = ((u64)acc[3] << 32) | acc[2];
+// ---- 30-bit limb columns: value = c0 + c1 2^30 + c2 2^60 + c3 2^92
+struct AccLimb {
+    u64 c0, c1, c2, c3;
+};
+__device__ __forceinline__ void acc_zero(AccLimb& a) { a.c0 = a.c1 = a.c2 = a.c3 = 0; }
+__device__ __forceinline__ void acc_mac_limbs(AccLimb& A, u32 x0, u32 x1, u32 w0, u32 w1) {
+    A.c0 += (u64)x0 * w0;
+    A.c1 += (u64)x0 * w1;
+    A.c1 += (u64)x1 * w0;
+    A.c2 += (u64)x1 * w1;
+}
+// Carry the columns forward: afterwards c0, c1 < 2^30, c2 < 2^32.  With at
+// most 8 products per column between calls no column overflows 64 bits.
+__device__ __forceinline__ void acc_normalize(AccLimb& A) {
+    A.c1 += A.c0 >> 30;
+    A.c0 &= kM30;
+    A.c2 += A.c1 >> 30;
+    A.c1 &= kM30;
+    A.c3 += A.c2 >> 32;
+    A.c2 &= 0xFFFFFFFFull;
+}
+__device__ __forceinline__ u64 acc_reduce(AccLimb A, const DevParams& P) {
+    acc_normalize(A);
+    const u64 t = A.c0 + (A.c1 << 30);
+    const u64 lo = t + (A.c2 << 60);
+    const u64 hi = (A.c2 >> 4) + (A.c3 << 28) + (lo < t ? 1 : 0);
     return reduce128(hi, lo, P);
 }
-
-__device__ __forceinline__ void set_acc(u32 (&acc)[4], u64 v) {
-    acc[0] = (u32)v;
-    acc[1] = (u32)(v >> 32);
-    acc[2] = 0;
-    acc[3] = 0;
+__device__ __forceinline__ void acc_set(AccLimb& a, u64 r) {
+    a.c0 = r & kM30;
+    a.c1 = r >> 30;
+    a.c2 = a.c3 = 0;
 }
 
-constexpr u32 kThreads = 128;
+__device__ __forceinline__ ulonglong2 ldg2(const u64* p) { return __ldg(reinterpret_cast<const ulonglong2*>(p)); }
 
-template <int CB>
+template <int NB, bool kWide>
 __global__ void __launch_bounds__(kThreads) homconv_kernel(DevParams P, DevLayer L, const u64* __restrict__ ct_in,
                                                            const u64* __restrict__ Phat,
                                                            const u64* __restrict__ Mhat, u64* __restrict__ ct_out,
-                                                           u32 jblocks, u32 cchunks) {
-    const u32 nJ = L.beta * P.n;
+                                                           u32 btiles, u32 jtiles) {
+    using Acc = typename std::conditional<kWide, AccLimb, Acc128>::type;
     u32 blk = blockIdx.x;
-    const u32 jb = blk % jblocks;
-    blk /= jblocks;
-    const u32 cc = blk % cchunks, bb = blk / cchunks;
-    const u32 J = jb * kThreads + threadIdx.x;
-    if (J >= nJ) return;
+    const u32 bt = blk % btiles;
+    blk /= btiles;
+    const u32 jt = blk % jtiles, ct = blk / jtiles;
+    const u32 co = ct * kWarps + (threadIdx.x >> 5);
+    const u32 J = jt * kJT + 2 * (threadIdx.x & 31);
+    const u32 nJ = L.beta * P.n;
+    if (co >= L.Co || J >= nJ) return;
     const u32 h = J >> P.logn, j = J & (P.n - 1);
-    const u32 co0 = cc * CB;
     const u64 n = P.n, beta = L.beta, T = L.T;
+    const u32 bb0 = bt * NB;
+    const u32 nbv = L.GB - bb0 < (u32)NB ? L.GB - bb0 : (u32)NB;
 
-    u32 acc[CB][2][4];
+    Acc acc[NB][2][2];  // [image group][j offset][component]
 #pragma unroll
-    for (int cb = 0; cb < CB; cb++)
+    for (int b = 0; b < NB; b++)
 #pragma unroll
-        for (int c = 0; c < 2; c++) set_acc(acc[cb][c], 0);
+        for (int e = 0; e < 2; e++) {
+            acc_zero(acc[b][e][0]);
+            acc_zero(acc[b][e][1]);
+        }
 
-    const u64* in_p = ct_in + ((u64)bb * T * beta + h) * 2 * n + j;  // + k beta 2n + c n
-    const u64* w_p = Phat + ((u64)co0 * T * beta + h) * n + j;       // + (cb T + k) beta n
-    const u64 in_step = beta * 2 * n, w_step = beta * n, w_cb = T * beta * n;
-    const u32 cb_valid = L.Co - co0 < (u32)CB ? L.Co - co0 : (u32)CB;
-
-    for (u32 k = 0; k < L.T; k++) {
-        const u64 x0 = in_p[k * in_step], x1 = in_p[k * in_step + n];
+    const u64 w_step = beta * n, x_step = beta * 2 * n;
+    const u64* wp = Phat + ((u64)co * T * beta + h) * n + j;
+    const u64* xp[NB];
 #pragma unroll
-        for (int cb = 0; cb < CB; cb++) {
-            if ((u32)cb < cb_valid) {
-                const u64 w = w_p[cb * w_cb + k * w_step];
-                mac128(acc[cb][0], x0, w);
-                mac128(acc[cb][1], x1, w);
+    for (int b = 0; b < NB; b++) xp[b] = ct_in + ((u64)(bb0 + (b < (int)nbv ? b : 0)) * T * beta + h) * 2 * n + j;
+
+    for (u32 k0 = 0; k0 < L.T; k0 += kUnroll) {
+        ulonglong2 wv[kUnroll], xv[NB][kUnroll][2];
+#pragma unroll
+        for (int u = 0; u < (int)kUnroll; u++) {
+            if (k0 + u < L.T) {
+                wv[u] = ldg2(wp + (k0 + u) * w_step);
+#pragma unroll
+                for (int b = 0; b < NB; b++) {
+                    xv[b][u][0] = ldg2(xp[b] + (k0 + u) * x_step);
+                    xv[b][u][1] = ldg2(xp[b] + (k0 + u) * x_step + n);
+                }
             }
         }
-        if ((k & 255u) == 255u) {
 #pragma unroll
-            for (int cb = 0; cb < CB; cb++)
+        for (int u = 0; u < (int)kUnroll; u++) {
+            if (k0 + u >= L.T) break;
+            const u64 w2[2] = {wv[u].x, wv[u].y};
 #pragma unroll
-                for (int c = 0; c < 2; c++) set_acc(acc[cb][c], reduce_acc(acc[cb][c], P));
+            for (int e = 0; e < 2; e++) {
+                if constexpr (kWide) {
+                    const u32 w0 = (u32)(w2[e] & kM30), w1 = (u32)(w2[e] >> 30);
+#pragma unroll
+                    for (int b = 0; b < NB; b++) {
+#pragma unroll
+                        for (int c = 0; c < 2; c++) {
+                            const u64 x = e ? xv[b][u][c].y : xv[b][u][c].x;
+                            acc_mac_limbs(acc[b][e][c], (u32)(x & kM30), (u32)(x >> 30), w0, w1);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < NB; b++)
+#pragma unroll
+                        for (int c = 0; c < 2; c++)
+                            acc_mac(acc[b][e][c], e ? xv[b][u][c].y : xv[b][u][c].x, w2[e]);
+                }
+            }
+        }
+        if constexpr (kWide) {
+            if (((k0 / kUnroll) & 1) || k0 + kUnroll >= L.T) {  // every 8 terms
+#pragma unroll
+                for (int b = 0; b < NB; b++)
+#pragma unroll
+                    for (int e = 0; e < 2; e++) {
+                        acc_normalize(acc[b][e][0]);
+                        acc_normalize(acc[b][e][1]);
+                    }
+            }
+        }
+        if (((k0 + kUnroll) & 255u) == 0 && k0 + kUnroll < L.T) {  // keep 256 (q-1)^2 < 2^128 headroom
+#pragma unroll
+            for (int b = 0; b < NB; b++)
+#pragma unroll
+                for (int e = 0; e < 2; e++)
+#pragma unroll
+                    for (int c = 0; c < 2; c++) acc_set(acc[b][e][c], acc_reduce(acc[b][e][c], P));
         }
     }
+
 #pragma unroll
-    for (int cb = 0; cb < CB; cb++) {
-        if ((u32)cb >= cb_valid) continue;
-        const u32 co = co0 + cb;
-        const u64 v = ((u64)bb * L.Co + co) * beta + h;
-        u64 r0 = reduce_acc(acc[cb][0], P), r1 = reduce_acc(acc[cb][1], P);
-        if (Mhat) r1 = submod_q(r1, Mhat[v * n + j], P.q);
-        ct_out[v * 2 * n + j] = r0;
-        ct_out[v * 2 * n + n + j] = r1;
+    for (int b = 0; b < NB; b++) {
+        if (b >= (int)nbv) break;
+        const u64 v = ((u64)(bb0 + b) * L.Co + co) * beta + h;
+        ulonglong2 r0, r1;
+        r0.x = acc_reduce(acc[b][0][0], P);
+        r0.y = acc_reduce(acc[b][1][0], P);
+        r1.x = acc_reduce(acc[b][0][1], P);
+        r1.y = acc_reduce(acc[b][1][1], P);
+        if (Mhat) {
+            const ulonglong2 m = ldg2(Mhat + v * n + j);
+            r1.x = submod_q(r1.x, m.x, P.q);
+            r1.y = submod_q(r1.y, m.y, P.q);
+        }
+        *reinterpret_cast<ulonglong2*>(ct_out + v * 2 * n + j) = r0;
+        *reinterpret_cast<ulonglong2*>(ct_out + v * 2 * n + n + j) = r1;
     }
+}
+
+template <int NB, bool W>
+cudaError_t launch_variant(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* Phat, const u64* Mhat,
+                           u64* ct_out, cudaStream_t s) {
+    const u32 nJ = L.beta * P.n;
+    const u32 jtiles = (nJ + kJT - 1) / kJT;
+    const u32 ctiles = (L.Co + kWarps - 1) / kWarps;
+    const u32 btiles = (L.GB + NB - 1) / NB;
+    const u64 grid = (u64)jtiles * ctiles * btiles;
+    if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
+    homconv_kernel<NB, W><<<(u32)grid, kThreads, 0, s>>>(P, L, ct_in, Phat, Mhat, ct_out, btiles, jtiles);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
+// Variant selection: 0 = automatic, 1 = limb columns NB=1, 2 = limb columns
+// NB=2, 3 = carry chain NB=1.
+static int g_homconv_variant = 0;
+extern "C" int fdsc_set_homconv_variant(int v) {
+    if (v < 0 || v > 3) return FDSC_ERR_ARG;
+    g_homconv_variant = v;
+    return FDSC_OK;
+}
+
 cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* Phat, const u64* Mhat,
                            u64* ct_out, cudaStream_t s) {
-    constexpr int CB = 4;
-    const u32 nJ = L.beta * P.n;
-    const u32 jblocks = (nJ + kThreads - 1) / kThreads;
-    const u32 cchunks = (L.Co + CB - 1) / CB;
-    const u64 grid = (u64)jblocks * cchunks * L.GB;
-    if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
-    homconv_kernel<CB><<<(u32)grid, kThreads, 0, s>>>(P, L, ct_in, Phat, Mhat, ct_out, jblocks, cchunks);
-    return cudaGetLastError();
+    int v = g_homconv_variant;
+    if (v == 0) v = L.GB >= 2 ? 2 : 1;
+    switch (v) {
+        case 2: return launch_variant<2, true>(P, L, ct_in, Phat, Mhat, ct_out, s);
+        case 3: return launch_variant<1, false>(P, L, ct_in, Phat, Mhat, ct_out, s);
+        default: return launch_variant<1, true>(P, L, ct_in, Phat, Mhat, ct_out, s);
+    }
 }

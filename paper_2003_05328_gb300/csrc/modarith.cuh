@@ -209,3 +209,207 @@ __device__ __forceinline__ void ntt2d_plane(u32* x, u32 logH, u32 logW, bool inv
 }
 
 __device__ __forceinline__ u32 brv_bits(u32 x, u32 bits) { return bits ? __brev(x) >> (32 - bits) : 0; }
+
+// ------------------------------------------------------------------ radix-8 register passes
+// A length-L transform (L = 2^logL >= 8) is run as passes of up to three
+// butterfly stages: in each pass a thread holds 8 elements whose indices
+// differ in one 3-bit window [wlo, wlo+3), does the stages of that window in
+// registers, and exchanges through shared memory (one barrier per pass
+// instead of one per stage).  Thread tl of a vector owns the elements
+// win_index(tl, r, wlo), r < 8; L/8 threads serve one vector.
+__device__ __forceinline__ u32 win_index(u32 tl, u32 r, u32 wlo) {
+    return ((tl >> wlo) << (wlo + 3)) | (r << wlo) | (tl & ((1u << wlo) - 1u));
+}
+
+// Harvey butterflies mod q.  CT: x in [0,4q), y < 2^64 -> both in [0,4q).
+__device__ __forceinline__ void bfly_ct_q(u64& x, u64& y, u64 w, u64 ws, const DevParams& P) {
+    const u64 a = x >= P.twoq ? x - P.twoq : x;
+    const u64 t = shoup_mul(y, w, ws, P.q);
+    x = a + t;
+    y = a - t + P.twoq;
+}
+// GS: x, y in [0,2q) -> both in [0,2q).
+__device__ __forceinline__ void bfly_gs_q(u64& x, u64& y, u64 w, u64 ws, const DevParams& P) {
+    const u64 s = x + y;
+    const u64 d = shoup_mul(x - y + P.twoq, w, ws, P.q);
+    x = s >= P.twoq ? s - P.twoq : s;
+    y = d;
+}
+__device__ __forceinline__ void bfly_ct_p(u32& x, u32& y, u32 w, u32 ws, u32 p) {
+    u32 t = shoup_mul32(y, w, ws, p);
+    t = t >= p ? t - p : t;
+    const u32 a = x;
+    x = addmod_p(a, t, p);
+    y = submod_p(a, t, p);
+}
+__device__ __forceinline__ void bfly_gs_p(u32& x, u32& y, u32 w, u32 ws, u32 p) {
+    const u32 a = x, b = y;
+    x = addmod_p(a, b, p);
+    u32 d = shoup_mul32(submod_p(a, b, p), w, ws, p);
+    y = d >= p ? d - p : d;
+}
+
+// Stage with bit b = wlo + RB on the 8 registers; twiddle of the pair whose
+// lower index is i: table[(L + i) >> (b + 1)] (psi^brv for CT, psi^-brv for GS).
+template <int RB, bool CT, typename T>
+__device__ __forceinline__ void r8_stage(T (&x)[8], u32 tl, u32 wlo, u32 L, const T* tw, const T* tws,
+                                         const DevParams& P) {
+    const u32 b = wlo + RB;
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        if (r & (1 << RB)) continue;
+        const u32 k = (L + win_index(tl, r, wlo)) >> (b + 1);
+        const T w = __ldg(tw + k), ws = __ldg(tws + k);
+        if constexpr (sizeof(T) == 8) {
+            if (CT) bfly_ct_q(x[r], x[r | (1 << RB)], w, ws, P);
+            else bfly_gs_q(x[r], x[r | (1 << RB)], w, ws, P);
+        } else {
+            if (CT) bfly_ct_p(x[r], x[r | (1 << RB)], w, ws, P.p);
+            else bfly_gs_p(x[r], x[r | (1 << RB)], w, ws, P.p);
+        }
+    }
+}
+
+// Forward negacyclic transform of `cnt` contiguous length-L vectors in a:
+// natural order in, bit-reversed evaluation order out.  mod q: in [0,4q),
+// out [0,q).  mod p: in and out [0,p).  Every thread of the CTA must call it.
+template <typename T>
+__device__ __forceinline__ void ntt_fwd_r8(T* a, u32 logL, u32 cnt, const T* tw, const T* tws, const DevParams& P) {
+    const u32 L = 1u << logL, lper = logL - 3;
+    const bool active = threadIdx.x < (cnt << lper);
+    const u32 vec = threadIdx.x >> lper, tl = threadIdx.x & ((1u << lper) - 1u);
+    T* v = a + (u64)vec * L;
+    for (int hi = (int)logL - 1; hi >= 0; hi -= 3) {
+        const u32 wlo = hi >= 2 ? (u32)hi - 2 : 0u;
+        const int lo = hi - 2 > 0 ? hi - 2 : 0;  // lowest stage bit of this pass
+        if (active) {
+            T x[8];
+#pragma unroll
+            for (int r = 0; r < 8; r++) x[r] = v[win_index(tl, r, wlo)];
+            if ((int)wlo + 2 <= hi && (int)wlo + 2 >= lo) r8_stage<2, true>(x, tl, wlo, L, tw, tws, P);
+            if ((int)wlo + 1 <= hi && (int)wlo + 1 >= lo) r8_stage<1, true>(x, tl, wlo, L, tw, tws, P);
+            if ((int)wlo <= hi && (int)wlo >= lo) r8_stage<0, true>(x, tl, wlo, L, tw, tws, P);
+            if (hi < 3) {  // last pass: canonical residues
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    if constexpr (sizeof(T) == 8) {
+                        T y = x[r] >= P.twoq ? x[r] - P.twoq : x[r];
+                        x[r] = y >= P.q ? y - P.q : y;
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 8; r++) v[win_index(tl, r, wlo)] = x[r];
+        }
+        __syncthreads();
+    }
+}
+
+// Inverse: bit-reversed in, natural out, times L^-1 (inv, inv_s).
+template <typename T>
+__device__ __forceinline__ void ntt_inv_r8(T* a, u32 logL, u32 cnt, const T* tw, const T* tws, T inv, T inv_s,
+                                           const DevParams& P) {
+    const u32 L = 1u << logL, lper = logL - 3;
+    const bool active = threadIdx.x < (cnt << lper);
+    const u32 vec = threadIdx.x >> lper, tl = threadIdx.x & ((1u << lper) - 1u);
+    T* v = a + (u64)vec * L;
+    for (u32 lo = 0; lo < logL; lo += 3) {
+        const u32 top = lo + 3 < logL ? lo + 3 : logL;  // stage bits [lo, top)
+        const u32 wlo = lo + 3 <= logL ? lo : logL - 3;
+        if (active) {
+            T x[8];
+#pragma unroll
+            for (int r = 0; r < 8; r++) x[r] = v[win_index(tl, r, wlo)];
+            if (wlo >= lo && wlo < top) r8_stage<0, false>(x, tl, wlo, L, tw, tws, P);
+            if (wlo + 1 >= lo && wlo + 1 < top) r8_stage<1, false>(x, tl, wlo, L, tw, tws, P);
+            if (wlo + 2 >= lo && wlo + 2 < top) r8_stage<2, false>(x, tl, wlo, L, tw, tws, P);
+            if (top == logL) {
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    if constexpr (sizeof(T) == 8) {
+                        T y = shoup_mul(x[r], inv, inv_s, P.q);
+                        x[r] = y >= P.q ? y - P.q : y;
+                    } else {
+                        T y = shoup_mul32(x[r], inv, inv_s, P.p);
+                        x[r] = y >= P.p ? y - P.p : y;
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 8; r++) v[win_index(tl, r, wlo)] = x[r];
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void ntt_q_fwd8(u64* a, const DevParams& P) { ntt_fwd_r8<u64>(a, P.logn, 1, P.qfw, P.qfw_s, P); }
+__device__ __forceinline__ void ntt_q_inv8(u64* a, const DevParams& P) {
+    ntt_inv_r8<u64>(a, P.logn, 1, P.qinv, P.qinv_s, P.ninv, P.ninv_s, P);
+}
+__device__ __forceinline__ void ntt_p_fwd8(u32* a, u32 cnt, const DevParams& P) {
+    ntt_fwd_r8<u32>(a, P.logS, cnt, P.pfw, P.pfw_s, P);
+}
+__device__ __forceinline__ void ntt_p_inv8(u32* a, u32 cnt, const DevParams& P) {
+    ntt_inv_r8<u32>(a, P.logS, cnt, P.pinv, P.pinv_s, P.Sinv, P.Sinv_s, P);
+}
+
+// Cyclic decimation-in-frequency transform mod p of the lines of an H x W
+// plane in shared memory (rows: lines H, length W, stride 1; columns: lines
+// W, length H, stride W): natural order in, bit-reversed order out; twiddle
+// of stage t = 2^b at in-line index i: w_lmax^((i mod t) lmax / (2t)).
+// Needs L >= 8 and HW / 8 threads.
+__device__ __forceinline__ void dif_lines_r8(u32* pl, u32 logL, u32 lines_log, bool rows, u32 logW, const u32* tw,
+                                             const u32* tws, const DevParams& P) {
+    const u32 lper = logL - 3;
+    const bool active = threadIdx.x < (1u << (lines_log + lper));
+    u32 line, tl;
+    if (rows) {
+        line = threadIdx.x >> lper;
+        tl = threadIdx.x & ((1u << lper) - 1u);
+    } else {  // consecutive threads on consecutive columns
+        line = threadIdx.x & ((1u << lines_log) - 1u);
+        tl = threadIdx.x >> lines_log;
+    }
+    const u32 p = P.p;
+    for (int hi = (int)logL - 1; hi >= 0; hi -= 3) {
+        const u32 wlo = hi >= 2 ? (u32)hi - 2 : 0u;
+        const int lo = hi - 2 > 0 ? hi - 2 : 0;
+        if (active) {
+            u32 off[8], x[8];
+#pragma unroll
+            for (int r = 0; r < 8; r++) {
+                const u32 i = win_index(tl, r, wlo);
+                off[r] = rows ? (line << logW) + i : (i << logW) + line;
+                x[r] = pl[off[r]];
+            }
+#pragma unroll
+            for (int RB = 2; RB >= 0; RB--) {
+                const int b = (int)wlo + RB;
+                if (b > hi || b < lo) continue;
+                const u32 t = 1u << b, shift = P.loglmax - 1 - b;
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    if (r & (1 << RB)) continue;
+                    const u32 i = win_index(tl, r, wlo);
+                    const u32 k = (i & (t - 1)) << shift;
+                    const u32 u = x[r], v = x[r | (1 << RB)];
+                    x[r] = addmod_p(u, v, p);
+                    u32 d = shoup_mul32(submod_p(u, v, p), __ldg(tw + k), __ldg(tws + k), p);
+                    x[r | (1 << RB)] = d >= p ? d - p : d;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 8; r++) pl[off[r]] = x[r];
+        }
+        __syncthreads();
+    }
+}
+
+// NTT2D (or its unscaled inverse) of a natural-order plane in shared memory,
+// leaving X[k1][k2] at pl[brv(k1) W + brv(k2)].  H, W >= 8; HW/8 threads.
+__device__ __forceinline__ void ntt2d_plane_dif(u32* pl, u32 logH, u32 logW, bool inverse, const DevParams& P) {
+    const u32* tw = inverse ? P.w2di : P.w2d;
+    const u32* tws = inverse ? P.w2di_s : P.w2d_s;
+    dif_lines_r8(pl, logW, logH, true, logW, tw, tws, P);
+    dif_lines_r8(pl, logH, logW, false, logW, tw, tws, P);
+}

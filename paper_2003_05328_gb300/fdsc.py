@@ -69,6 +69,7 @@ _SIGS = {
     "fdsc_homrec": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
     "fdsc_homconv": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp, _vp]),
     "fdsc_decrypt": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
+    "fdsc_set_homconv_variant": (C.c_int, [C.c_int]),
 }
 # entry points declared in include/fdsc.h (checked against the library's exports by the tests)
 EXPORTS = tuple(_SIGS)
@@ -233,6 +234,11 @@ def mask_prepare(P: Params, L: LayerSpec, seed: int, M_hat=None, sB_hat=None, st
     _call("fdsc_mask_prepare", P.handle, C.byref(L.c()), seed, _ptr(M_hat, torch.int64, lay.mask_words, "M_hat"),
           _ptr(sB_hat, torch.int32, lay.out_spectra_words, "sB_hat"), _stream(stream))
     return M_hat, sB_hat
+
+
+def set_homconv_variant(v: int) -> None:
+    """Kernel variant for HomConv (0 automatic; results are identical)."""
+    _call("fdsc_set_homconv_variant", v)
 
 
 # ---------------------------------------------------------------- online
