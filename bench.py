@@ -70,11 +70,12 @@ def aggregate(local_seconds: float, local_units: float, world: int):
     return float(t.item()), float(u.item())
 
 
-def layer_counts(ls, T, beta, GB, n):
+def layer_counts(ls, T, beta, GB, n, addends=2):
     """Algorithmic bytes and modular products of one HomConv launch (filter
-    read once, per image group the input, output and mask words)."""
+    read once; per image group the input ciphertexts, the c1 addends, the
+    output ciphertexts and the mask words)."""
     filt = 8 * ls.Co * T * beta * n
-    per_group = 8 * (2 * T * beta * n + 2 * ls.Co * beta * n + ls.Co * beta * n)
+    per_group = 8 * ((2 + addends) * T * beta * n + 2 * ls.Co * beta * n + ls.Co * beta * n)
     macs = 2 * ls.Co * T * beta * n * GB
     return filt + GB * per_group, macs
 
@@ -218,7 +219,7 @@ def run_gpu(args, rank, local_rank, world):
     ks, es, ss = FI.seeds(c.cid)
     dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
 
-    # setup (t_setup)
+    # setup (t_setup): key, filter spectra, HomShare masks
     t_hat = F.keygen(P, ks)
     Phat = F.filter_prepare(P, L, dev(w_h, np.int8))
     Mhat, sB = F.mask_prepare(P, L, ss)
@@ -230,9 +231,34 @@ def run_gpu(args, rank, local_rank, world):
     yA = torch.empty((ls.B, ls.Co, ls.H, ls.W), dtype=torch.int32, device="cuda")
     yB = torch.empty_like(yA)
     sB4 = sB.view(ls.B, ls.Co, ls.H, ls.W)
-    LAUNCHES_PER_STEP = 8
+    A_msg = torch.empty(lay.n_in * ls.n, dtype=torch.int64, device="cuda")
+    A_rec = torch.empty_like(A_msg)
+    LAUNCHES_PER_STEP = 6
+    side = [torch.cuda.Stream() for _ in range(3)]
 
     def step():
+        """One online layer.  Four independent producers run concurrently:
+        Alice's encryption constants (Enc(0)), Alice's share encoding, Bob's
+        HomRec plaintext from his share, and Bob's INTT2D of his mask share;
+        then HomConv (+ HomRec addends + HomShare) and Alice's fused
+        decryption + INTT2D."""
+        main = torch.cuda.current_stream()
+        for st in side:
+            st.wait_stream(main)
+        F.encrypt_constants(P, L, t_hat, es, out=ct)
+        with torch.cuda.stream(side[0]):
+            F.encode_share(P, L, xA, out=A_msg)
+        with torch.cuda.stream(side[1]):
+            F.encode_share(P, L, xB, out=A_rec)
+        with torch.cuda.stream(side[2]):
+            F.intt2d(P, sB4, out=yB)
+        for st in side:
+            main.wait_stream(st)
+        F.homconv_sum(P, L, ct, A_msg, A_rec, Phat, Mhat, out=ct_out)
+        F.decrypt_share(P, L, t_hat, ct_out, out=yA)
+
+    def step_unfused():
+        """The same layer through the step-by-step entry points, one stream."""
         F.ntt2d(P, xA, out=XA)
         F.encrypt(P, L, t_hat, XA, es, out=ct)
         F.ntt2d(P, xB, out=XB)
@@ -247,22 +273,29 @@ def run_gpu(args, rank, local_rank, world):
 
     for _ in range(max(1, args.warmup)):
         step()
+        step_unfused()
     torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
-    s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
-        step()
-        torch.cuda.synchronize()
-        with torch.cuda.graph(g, stream=s):
-            step()
-    torch.cuda.current_stream().wait_stream(s)
+
+    def capture(fn):
+        gr = torch.cuda.CUDAGraph()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            fn()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(gr, stream=s):
+                fn()
+        torch.cuda.current_stream().wait_stream(s)
+        return gr
+
+    g = capture(step)
+    g_unfused = capture(step_unfused)
     # HomConv alone, same launch configuration, for the roofline figure
     g_hc = torch.cuda.CUDAGraph()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
         with torch.cuda.graph(g_hc, stream=s):
-            F.homconv(P, L, ct, Phat, Mhat, out=ct_out)
+            F.homconv_sum(P, L, ct, A_msg, A_rec, Phat, Mhat, out=ct_out)
     torch.cuda.current_stream().wait_stream(s)
     for _ in range(args.warmup):
         flush.fill_(1)
@@ -294,6 +327,17 @@ def run_gpu(args, rank, local_rank, world):
         ends[i].record()
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+    # the step-by-step path, for comparison
+    us = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(min(args.steps, 500))]
+    torch.cuda._sleep(sleep_cycles)
+    for i, (a, b) in enumerate(us):
+        flush.fill_(i & 0xFF)
+        a.record()
+        g_unfused.replay()
+        b.record()
+    torch.cuda.synchronize()
+    unfused_ms = [a.elapsed_time(b) for a, b in us]
 
     # HomConv launches alone (graph of the same launch), L2 flushed before each
     hc_steps = max(20, min(args.steps, 2000))
@@ -361,18 +405,20 @@ def run_gpu(args, rank, local_rank, world):
         "config": {"workload": WORKLOAD, "layer": "32x32x64->64 3x3", "batch": ls.B, "n": ls.n, "p": ls.p,
                    "q_bits": 60, "packing": {"g_c": g_c, "g_b": g_b, "T": lay.T},
                    "l2": "flushed before every timed step (write of %d MiB)" % (flush.numel() * 4 >> 20),
-                   "step": "ntt2d,encrypt,ntt2d,homrec,homconv+homshare,decrypt,intt2d,intt2d (CUDA graph)"},
+                   "step": "[encrypt_constants | encode_share(x_A) | encode_share(x_B) | intt2d(s_B)] -> "
+                           "homconv_sum (HomRec + HomConv + HomShare) -> decrypt_share (CUDA graph, 4 streams)"},
         "mac_per_s": value * 2 * ls.Co * ls.Ci * ls.H * ls.W,
         "homconv_layers_per_s": ls.B / (hc_avg * 1e-3),
         "homconv_mac_per_s": macs / (hc_avg * 1e-3),
         "useful_macs_per_layer": useful_macs // ls.B,
         "step_ms_p50": float(np.percentile(step_ms, 50)), "step_ms_p99": float(np.percentile(step_ms, 99)),
-        "roofline": {"kernel": "homconv_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+        "step_by_step_ms": float(np.mean(unfused_ms)),
+        "roofline": {"kernel": "homconv_kernel (homconv_sum: HomRec addends + HomConv + HomShare)", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src + " (hbm_gbs, burst copy)", "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "alg_bytes_per_launch": alg_bytes, "launch_us": hc_avg * 1e3},
         "e2e": {"value": e2e_units / e2e_sec, "unit": "layers/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms),
-                "path": "python binding of the C ABI, eager launches, pinned host buffers"},
+                "path": "python binding of the C ABI, eager launches on 4 streams, pinned host buffers"},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps + hc_steps,
         "homconv_variant": args.homconv_variant,
         "clocks": clk,

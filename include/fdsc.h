@@ -179,6 +179,42 @@ int fdsc_decrypt(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_ha
                  const uint64_t* ct, uint32_t* SA_hat, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Fused online path: the same words as the step-by-step calls, in fewer   */
+/* kernels, with the input-independent work separable from the rest.      */
+/* ---------------------------------------------------------------------- */
+/* Eq. 1 with a zero message, in the NTT_q domain: for every input
+ * ciphertext u, ct[u] = (-a_hat, a_hat o t_hat + NTT_q(e)), a_hat and e
+ * drawn from `seed` exactly as fdsc_encrypt draws them.  These are the RLWE
+ * constants of Sec. 5.1 (no user input).  Because NTT_q is linear,
+ *   fdsc_encrypt(X = NTT2D(x), seed) = this + (0, fdsc_encode_share(x)). */
+int fdsc_encrypt_constants(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, uint64_t seed,
+                           uint64_t* ct, void* stream);
+
+/* The message part of Fig. 2 lines 1-2 (and 9-10) from a SPATIAL share
+ * x: uint32 [B][Ci][H][W] -> NTT2D -> flatten and pack -> slot encode ->
+ * times Delta -> NTT_q, written to A: uint64 [n_in][n].  Needs H W <= S and
+ * H, W >= 8 (FDSC_ERR_UNSUPPORTED otherwise; use fdsc_ntt2d + fdsc_encrypt). */
+int fdsc_encode_share(const fdsc_params* P, const fdsc_layer* L, const uint32_t* x, uint64_t* A, void* stream);
+
+/* Eq. 3 (HomRec) from Bob's SPATIAL share: ct.c1 += fdsc_encode_share(xB).
+ * Same restrictions as fdsc_encode_share. */
+int fdsc_homrec_share(const fdsc_params* P, const fdsc_layer* L, const uint32_t* xB, uint64_t* ct, void* stream);
+
+/* fdsc_homconv applied to the ciphertexts (c0, c1 + A1 + A2): the message and
+ * HomRec plaintexts of fdsc_encode_share are added to c1 as it is read.  A1,
+ * A2: uint64 [n_in][n] or NULL.  ct_out must not overlap any input. */
+int fdsc_homconv_sum(const fdsc_params* P, const fdsc_layer* L, const uint64_t* ct_in, const uint64_t* A1,
+                     const uint64_t* A2, const uint64_t* P_hat, const uint64_t* M_hat, uint64_t* ct_out,
+                     void* stream);
+
+/* Fig. 2 lines 5-6 (Alice) in one kernel: decrypt, decode, fold the channel
+ * blocks and INTT2D, giving her SPATIAL share y: uint32 [B][Co][H][W]
+ * (= fdsc_intt2d(fdsc_decrypt(...))).  Same restrictions as
+ * fdsc_encode_share. */
+int fdsc_decrypt_share(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, const uint64_t* ct,
+                       uint32_t* y, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Tuning                                                                  */
 /* ---------------------------------------------------------------------- */
 /* Selects the HomConv kernel variant for later fdsc_homconv calls in this

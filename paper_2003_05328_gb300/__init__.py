@@ -6,5 +6,6 @@ in ``include/fdsc.h``); :mod:`paper_2003_05328_gb300.fdsc` is its Python
 binding and :mod:`paper_2003_05328_gb300.build` compiles it.
 """
 from . import fdsc  # noqa: F401
-from .fdsc import (FdscError, LayerSpec, Params, decrypt, encrypt, filter_prepare, homconv,  # noqa: F401
-                   homrec, intt2d, keygen, layout, mask_prepare, ntt2d, params_query)
+from .fdsc import (FdscError, LayerSpec, Params, decrypt, decrypt_share, encode_share, encrypt,  # noqa: F401
+                   encrypt_constants, filter_prepare, homconv, homconv_sum, homrec, homrec_share, intt2d, keygen,
+                   layout, mask_prepare, ntt2d, params_query)

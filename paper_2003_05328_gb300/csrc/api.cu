@@ -122,7 +122,8 @@ extern "C" int fdsc_homconv(const fdsc_params* P, const fdsc_layer* L, const uin
     if (M_hat && (rc = check_ptr(M_hat, "M_hat"))) return rc;
     if (overlap(ct_in, lay.ct_in_words * 8, ct_out, lay.ct_out_words * 8))
         return fdsc_set_error(FDSC_ERR_ARG, "ct_out overlaps ct_in");
-    return launched(launch_homconv(P->dev, D, ct_in, P_hat, M_hat, ct_out, (cudaStream_t)stream), "homconv");
+    return launched(launch_homconv(P->dev, D, ct_in, nullptr, nullptr, P_hat, M_hat, ct_out, (cudaStream_t)stream),
+                    "homconv");
 }
 
 extern "C" int fdsc_decrypt(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, const uint64_t* ct,
@@ -134,4 +135,91 @@ extern "C" int fdsc_decrypt(const fdsc_params* P, const fdsc_layer* L, const uin
     if ((rc = check_ptr(t_hat, "t_hat")) || (rc = check_ptr(ct, "ct")) || (rc = check_ptr(SA_hat, "SA_hat")))
         return rc;
     return launched(launch_decrypt(P->dev, D, t_hat, ct, SA_hat, (cudaStream_t)stream), "decrypt");
+}
+
+// ---------------------------------------------------------------- fused online path
+namespace {
+
+// The fused spatial-domain kernels need whole spectra inside one ciphertext
+// (H W <= S), radix-8 lines (H, W >= 8) and their shared memory to fit.
+int check_fused(const fdsc_params* P, const DevLayer& D, size_t smem, const char* what) {
+    if (D.beta != 1 || D.logH < 3 || D.logW < 3)
+        return fdsc_set_error(FDSC_ERR_UNSUPPORTED,
+                              "%s needs H, W >= 8 and H W <= S; use fdsc_ntt2d/fdsc_encrypt/fdsc_decrypt", what);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem + 1024 > (size_t)optin)
+        return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "%s needs %zu bytes of shared memory", what, smem);
+    (void)P;
+    return FDSC_OK;
+}
+
+}  // namespace
+
+extern "C" int fdsc_encrypt_constants(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, uint64_t seed,
+                                      uint64_t* ct, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_ptr(t_hat, "t_hat")) || (rc = check_ptr(ct, "ct"))) return rc;
+    return launched(launch_constants(P->dev, D, t_hat, seed, ct, (cudaStream_t)stream), "encrypt_constants");
+}
+
+extern "C" int fdsc_encode_share(const fdsc_params* P, const fdsc_layer* L, const uint32_t* x, uint64_t* A,
+                                 void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_fused(P, D, share_smem_bytes(P->dev, D), "encode_share"))) return rc;
+    if ((rc = check_ptr(x, "x")) || (rc = check_ptr(A, "A"))) return rc;
+    return launched(launch_share(P->dev, D, x, A, false, (cudaStream_t)stream), "encode_share");
+}
+
+extern "C" int fdsc_homrec_share(const fdsc_params* P, const fdsc_layer* L, const uint32_t* xB, uint64_t* ct,
+                                 void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_fused(P, D, share_smem_bytes(P->dev, D), "homrec_share"))) return rc;
+    if ((rc = check_ptr(xB, "xB")) || (rc = check_ptr(ct, "ct"))) return rc;
+    return launched(launch_share(P->dev, D, xB, ct, true, (cudaStream_t)stream), "homrec_share");
+}
+
+extern "C" int fdsc_homconv_sum(const fdsc_params* P, const fdsc_layer* L, const uint64_t* ct_in, const uint64_t* A1,
+                                const uint64_t* A2, const uint64_t* P_hat, const uint64_t* M_hat, uint64_t* ct_out,
+                                void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    fdsc_layout lay;
+    if ((rc = fdsc_make_layer(P->info, L, &D, &lay))) return rc;
+    if (D.T > P->max_T)
+        return fdsc_set_error(FDSC_ERR_NOISE, "T = %u input ciphertexts exceed the params' noise budget (max_T = %u)",
+                              D.T, P->max_T);
+    if ((rc = check_ptr(ct_in, "ct_in")) || (rc = check_ptr(P_hat, "P_hat")) || (rc = check_ptr(ct_out, "ct_out")))
+        return rc;
+    if ((A1 && (rc = check_ptr(A1, "A1"))) || (A2 && (rc = check_ptr(A2, "A2"))) ||
+        (M_hat && (rc = check_ptr(M_hat, "M_hat"))))
+        return rc;
+    const u64 ob = lay.ct_out_words * 8, ab = (u64)D.n_in * P->info.n * 8;
+    if (overlap(ct_in, lay.ct_in_words * 8, ct_out, ob) || (A1 && overlap(A1, ab, ct_out, ob)) ||
+        (A2 && overlap(A2, ab, ct_out, ob)))
+        return fdsc_set_error(FDSC_ERR_ARG, "ct_out overlaps an input");
+    return launched(launch_homconv(P->dev, D, ct_in, A1, A2, P_hat, M_hat, ct_out, (cudaStream_t)stream),
+                    "homconv_sum");
+}
+
+extern "C" int fdsc_decrypt_share(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat,
+                                  const uint64_t* ct, uint32_t* y, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_fused(P, D, decrypt_share_smem_bytes(P->dev, D), "decrypt_share"))) return rc;
+    if ((rc = check_ptr(t_hat, "t_hat")) || (rc = check_ptr(ct, "ct")) || (rc = check_ptr(y, "y"))) return rc;
+    return launched(launch_decrypt_share(P->dev, D, t_hat, ct, y, (cudaStream_t)stream), "decrypt_share");
 }

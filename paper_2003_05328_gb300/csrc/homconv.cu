@@ -98,8 +98,12 @@ __device__ __forceinline__ void acc_set(AccLimb& a, u64 r) {
 
 __device__ __forceinline__ ulonglong2 ldg2(const u64* p) { return __ldg(reinterpret_cast<const ulonglong2*>(p)); }
 
-template <int NB, bool kWide>
+// kAdd extra c1 addends A1, A2 ([n_in][n] words) are added to every input
+// ciphertext's c1 as it is loaded (HomRec of Bob's encoded share, and the
+// message part of an encryption whose constants were drawn separately).
+template <int NB, bool kWide, int kAdd>
 __global__ void __launch_bounds__(kThreads) homconv_kernel(DevParams P, DevLayer L, const u64* __restrict__ ct_in,
+                                                           const u64* __restrict__ A1, const u64* __restrict__ A2,
                                                            const u64* __restrict__ Phat,
                                                            const u64* __restrict__ Mhat, u64* __restrict__ ct_out,
                                                            u32 btiles, u32 jtiles) {
@@ -129,8 +133,13 @@ __global__ void __launch_bounds__(kThreads) homconv_kernel(DevParams P, DevLayer
     const u64 w_step = beta * n, x_step = beta * 2 * n;
     const u64* wp = Phat + ((u64)co * T * beta + h) * n + j;
     const u64* xp[NB];
+    u64 ap[NB];
 #pragma unroll
-    for (int b = 0; b < NB; b++) xp[b] = ct_in + ((u64)(bb0 + (b < (int)nbv ? b : 0)) * T * beta + h) * 2 * n + j;
+    for (int b = 0; b < NB; b++) {
+        const u64 u0 = (u64)(bb0 + (b < (int)nbv ? b : 0)) * T * beta + h;
+        xp[b] = ct_in + u0 * 2 * n + j;
+        ap[b] = u0 * n + j;
+    }
 
     for (u32 k0 = 0; k0 < L.T; k0 += kUnroll) {
         ulonglong2 wv[kUnroll], xv[NB][kUnroll][2];
@@ -142,6 +151,17 @@ __global__ void __launch_bounds__(kThreads) homconv_kernel(DevParams P, DevLayer
                 for (int b = 0; b < NB; b++) {
                     xv[b][u][0] = ldg2(xp[b] + (k0 + u) * x_step);
                     xv[b][u][1] = ldg2(xp[b] + (k0 + u) * x_step + n);
+                    if constexpr (kAdd >= 1) {
+                        const u64 off = (u64)ap[b] + (k0 + u) * w_step;
+                        const ulonglong2 a1 = ldg2(A1 + off);
+                        xv[b][u][1].x = addmod_q(xv[b][u][1].x, a1.x, P.q);
+                        xv[b][u][1].y = addmod_q(xv[b][u][1].y, a1.y, P.q);
+                        if constexpr (kAdd >= 2) {
+                            const ulonglong2 a2 = ldg2(A2 + off);
+                            xv[b][u][1].x = addmod_q(xv[b][u][1].x, a2.x, P.q);
+                            xv[b][u][1].y = addmod_q(xv[b][u][1].y, a2.y, P.q);
+                        }
+                    }
                 }
             }
         }
@@ -210,16 +230,17 @@ __global__ void __launch_bounds__(kThreads) homconv_kernel(DevParams P, DevLayer
     }
 }
 
-template <int NB, bool W>
-cudaError_t launch_variant(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* Phat, const u64* Mhat,
-                           u64* ct_out, cudaStream_t s) {
+template <int NB, bool W, int kAdd>
+cudaError_t launch_variant(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                           const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
     const u32 nJ = L.beta * P.n;
     const u32 jtiles = (nJ + kJT - 1) / kJT;
     const u32 ctiles = (L.Co + kWarps - 1) / kWarps;
     const u32 btiles = (L.GB + NB - 1) / NB;
     const u64 grid = (u64)jtiles * ctiles * btiles;
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
-    homconv_kernel<NB, W><<<(u32)grid, kThreads, 0, s>>>(P, L, ct_in, Phat, Mhat, ct_out, btiles, jtiles);
+    homconv_kernel<NB, W, kAdd><<<(u32)grid, kThreads, 0, s>>>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, btiles,
+                                                               jtiles);
     return cudaGetLastError();
 }
 
@@ -234,13 +255,25 @@ extern "C" int fdsc_set_homconv_variant(int v) {
     return FDSC_OK;
 }
 
-cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* Phat, const u64* Mhat,
-                           u64* ct_out, cudaStream_t s) {
+template <int NB, bool W>
+cudaError_t launch_adds(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                        const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
+    if (!A1 && A2) {
+        A1 = A2;
+        A2 = nullptr;
+    }
+    if (!A1) return launch_variant<NB, W, 0>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+    if (!A2) return launch_variant<NB, W, 1>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+    return launch_variant<NB, W, 2>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+}
+
+cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                           const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
     int v = g_homconv_variant;
-    if (v == 0) v = L.GB >= 2 ? 2 : 1;
+    if (v == 0) v = 3;
     switch (v) {
-        case 2: return launch_variant<2, true>(P, L, ct_in, Phat, Mhat, ct_out, s);
-        case 3: return launch_variant<1, false>(P, L, ct_in, Phat, Mhat, ct_out, s);
-        default: return launch_variant<1, true>(P, L, ct_in, Phat, Mhat, ct_out, s);
+        case 1: return launch_adds<1, true>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+        case 2: return launch_adds<2, true>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+        default: return launch_adds<1, false>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
     }
 }

@@ -259,7 +259,7 @@ __device__ __forceinline__ void r8_stage(T (&x)[8], u32 tl, u32 wlo, u32 L, cons
     for (int r = 0; r < 8; r++) {
         if (r & (1 << RB)) continue;
         const u32 k = (L + win_index(tl, r, wlo)) >> (b + 1);
-        const T w = __ldg(tw + k), ws = __ldg(tws + k);
+        const T w = tw[k], ws = tws[k];  // generic loads: tables may live in shared or global memory
         if constexpr (sizeof(T) == 8) {
             if (CT) bfly_ct_q(x[r], x[r | (1 << RB)], w, ws, P);
             else bfly_gs_q(x[r], x[r | (1 << RB)], w, ws, P);
@@ -412,4 +412,90 @@ __device__ __forceinline__ void ntt2d_plane_dif(u32* pl, u32 logH, u32 logW, boo
     const u32* tws = inverse ? P.w2di_s : P.w2d_s;
     dif_lines_r8(pl, logW, logH, true, logW, tw, tws, P);
     dif_lines_r8(pl, logH, logW, false, logW, tw, tws, P);
+}
+
+// ------------------------------------------------------------------ staging and multi-plane 2D transforms
+// Asynchronous global -> shared copy of `bytes` (a multiple of 16, both
+// addresses 16-byte aligned) by the whole CTA; stage_wait() completes every
+// copy this thread issued and synchronises the CTA.
+__device__ __forceinline__ void stage_async(void* smem, const void* g, u32 bytes) {
+    const u32 base = (u32)__cvta_generic_to_shared(smem);
+    const char* src = reinterpret_cast<const char*>(g);
+    for (u32 o = threadIdx.x * 16; o < bytes; o += blockDim.x * 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + o), "l"(src + o) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void stage_wait() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+}
+
+// Cyclic radix-8 line transforms over `planes` stacked H x W planes in
+// shared memory (plane stride HW).  Rows: planes*H lines of length W; columns:
+// planes*W lines of length H.  `tw` holds w_T^k (k < T/2) for T = 2^logT >=
+// the line length: stage t = 2^b uses w_{2t}^j = tw[j << (logT - 1 - b)].
+//  dif: natural order in, bit-reversed out (Gentleman-Sande);
+//  dit: bit-reversed in, natural order out (Cooley-Tukey).
+// Needs line length >= 8 and planes * HW / 8 threads.
+template <bool kDif>
+__device__ __forceinline__ void lines_r8(u32* buf, u32 planes, bool rows, u32 logH, u32 logW, const u32* tw,
+                                         const u32* tws, u32 logT, u32 p) {
+    const u32 logL = rows ? logW : logH, lper = logL - 3;
+    const u32 nlines = planes << (rows ? logH : logW);
+    const bool active = threadIdx.x < (nlines << lper);
+    u32 line, tl;
+    if (rows) {
+        line = threadIdx.x >> lper;
+        tl = threadIdx.x & ((1u << lper) - 1u);
+    } else {  // consecutive threads on consecutive columns: conflict-free shared accesses
+        line = threadIdx.x % nlines;
+        tl = threadIdx.x / nlines;
+    }
+    const u32 base = rows ? line << logW : ((line >> logW) << (logH + logW)) + (line & ((1u << logW) - 1u));
+    const u32 stride_log = rows ? 0u : logW;
+    const int npass = ((int)logL + 2) / 3;
+    for (int ps = 0; ps < npass; ps++) {
+        // dif: stage bits descending from logL-1; dit: ascending from 0
+        int hi, lo;
+        if (kDif) {
+            hi = (int)logL - 1 - 3 * ps;
+            lo = hi - 2 > 0 ? hi - 2 : 0;
+        } else {
+            lo = 3 * ps;
+            hi = lo + 2 < (int)logL - 1 ? lo + 2 : (int)logL - 1;
+        }
+        const u32 wlo = kDif ? (hi >= 2 ? (u32)hi - 2 : 0u) : ((u32)lo + 3 <= logL ? (u32)lo : logL - 3);
+        if (active) {
+            u32 x[8];
+#pragma unroll
+            for (int r = 0; r < 8; r++) x[r] = buf[base + (win_index(tl, r, wlo) << stride_log)];
+#pragma unroll
+            for (int s = 0; s < 3; s++) {
+                const int RB = kDif ? 2 - s : s;
+                const int b = (int)wlo + RB;
+                if (b > hi || b < lo) continue;
+                const u32 t = 1u << b, shift = logT - 1 - b;
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    if (r & (1 << RB)) continue;
+                    const u32 k = (win_index(tl, r, wlo) & (t - 1)) << shift;
+                    const u32 w = tw[k], ws = tws[k];
+                    const u32 u = x[r], v = x[r | (1 << RB)];
+                    if (kDif) {
+                        x[r] = addmod_p(u, v, p);
+                        u32 d = shoup_mul32(submod_p(u, v, p), w, ws, p);
+                        x[r | (1 << RB)] = d >= p ? d - p : d;
+                    } else {
+                        u32 m = shoup_mul32(v, w, ws, p);
+                        m = m >= p ? m - p : m;
+                        x[r] = addmod_p(u, m, p);
+                        x[r | (1 << RB)] = submod_p(u, m, p);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 8; r++) buf[base + (win_index(tl, r, wlo) << stride_log)] = x[r];
+        }
+        __syncthreads();
+    }
 }

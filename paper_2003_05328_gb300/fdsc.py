@@ -70,6 +70,11 @@ _SIGS = {
     "fdsc_homconv": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp, _vp]),
     "fdsc_decrypt": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
     "fdsc_set_homconv_variant": (C.c_int, [C.c_int]),
+    "fdsc_encrypt_constants": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp]),
+    "fdsc_encode_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
+    "fdsc_homrec_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
+    "fdsc_homconv_sum": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fdsc_decrypt_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
 }
 # entry points declared in include/fdsc.h (checked against the library's exports by the tests)
 EXPORTS = tuple(_SIGS)
@@ -276,5 +281,58 @@ def decrypt(P: Params, L: LayerSpec, t_hat, ct, out=None, stream=None) -> torch.
         out = torch.empty(lay.out_spectra_words, dtype=torch.int32, device="cuda")
     _call("fdsc_decrypt", P.handle, C.byref(L.c()), _ptr(t_hat, torch.int64, P.n, "t_hat"),
           _ptr(ct, torch.int64, lay.ct_out_words, "ct"), _ptr(out, torch.int32, lay.out_spectra_words, "SA_hat"),
+          _stream(stream))
+    return out
+
+
+# ---------------------------------------------------------------- fused online path
+def encrypt_constants(P: Params, L: LayerSpec, t_hat, seed: int, out=None, stream=None) -> torch.Tensor:
+    """Enc(0) in the NTT_q domain: the RLWE constants of one encryption."""
+    lay = layout(P, L)
+    if out is None:
+        out = torch.empty(lay.ct_in_words, dtype=torch.int64, device="cuda")
+    _call("fdsc_encrypt_constants", P.handle, C.byref(L.c()), _ptr(t_hat, torch.int64, P.n, "t_hat"), seed,
+          _ptr(out, torch.int64, lay.ct_in_words, "ct"), _stream(stream))
+    return out
+
+
+def encode_share(P: Params, L: LayerSpec, x, out=None, stream=None) -> torch.Tensor:
+    """NTT_q(Delta * encode(pack(NTT2D(x)))) for a spatial share x."""
+    lay = layout(P, L)
+    if out is None:
+        out = torch.empty(lay.n_in * P.n, dtype=torch.int64, device="cuda")
+    _call("fdsc_encode_share", P.handle, C.byref(L.c()), _ptr(x, torch.int32, lay.in_spectra_words, "x"),
+          _ptr(out, torch.int64, lay.n_in * P.n, "A"), _stream(stream))
+    return out
+
+
+def homrec_share(P: Params, L: LayerSpec, xB, ct, stream=None) -> torch.Tensor:
+    lay = layout(P, L)
+    _call("fdsc_homrec_share", P.handle, C.byref(L.c()), _ptr(xB, torch.int32, lay.in_spectra_words, "xB"),
+          _ptr(ct, torch.int64, lay.ct_in_words, "ct"), _stream(stream))
+    return ct
+
+
+def homconv_sum(P: Params, L: LayerSpec, ct_in, A1, A2, P_hat, M_hat=None, out=None, stream=None) -> torch.Tensor:
+    lay = layout(P, L)
+    if out is None:
+        out = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
+    na = lay.n_in * P.n
+    a1 = None if A1 is None else _ptr(A1, torch.int64, na, "A1")
+    a2 = None if A2 is None else _ptr(A2, torch.int64, na, "A2")
+    m = None if M_hat is None else _ptr(M_hat, torch.int64, lay.mask_words, "M_hat")
+    _call("fdsc_homconv_sum", P.handle, C.byref(L.c()), _ptr(ct_in, torch.int64, lay.ct_in_words, "ct_in"), a1, a2,
+          _ptr(P_hat, torch.int64, lay.filter_words, "P_hat"), m, _ptr(out, torch.int64, lay.ct_out_words, "ct_out"),
+          _stream(stream))
+    return out
+
+
+def decrypt_share(P: Params, L: LayerSpec, t_hat, ct, out=None, stream=None) -> torch.Tensor:
+    """Decrypt, decode, fold and INTT2D: Alice's spatial share int32 [B][Co][H][W]."""
+    lay = layout(P, L)
+    if out is None:
+        out = torch.empty((L.B, L.Co, L.H, L.W), dtype=torch.int32, device="cuda")
+    _call("fdsc_decrypt_share", P.handle, C.byref(L.c()), _ptr(t_hat, torch.int64, P.n, "t_hat"),
+          _ptr(ct, torch.int64, lay.ct_out_words, "ct"), _ptr(out, torch.int32, lay.out_spectra_words, "y"),
           _stream(stream))
     return out

@@ -1,0 +1,101 @@
+"""GPU parity of the fused online path: encryption constants, spatial share
+encoding, HomRec from a spatial share, HomConv over summed c1 addends and the
+fused decrypt + INTT2D produce exactly the words of the step-by-step oracle
+(Fig. 2; Enc(m) = Enc(0) + (0, NTT_q(Delta m)) by linearity of NTT_q)."""
+import numpy as np
+import pytest
+import torch
+
+import fdsc_inputs as FI
+from fdsc_harness import dev, u32, u64
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_05328_gb300 import build
+
+    build.build()
+    from paper_2003_05328_gb300 import fdsc
+
+    torch.cuda.set_device(0)
+    return fdsc
+
+
+CASES = [
+    dict(n=1024, p=65537, B=1, Ci=4, Co=4, H=16, W=16, fh=3),                      # single small layer
+    dict(n=2048, p=65537, B=1, Ci=64, Co=64, H=32, W=32, fh=3),                    # CIFAR-shaped layer
+    dict(n=2048, p=65537, B=1, Ci=1, Co=16, H=32, W=32, fh=5, support=(28, 28)),   # MNIST-shaped layer
+    dict(n=2048, p=65537, B=2, Ci=128, Co=8, H=16, W=16, fh=3),                    # 16x16, g_c = 8
+    dict(n=4096, p=65537, B=2, Ci=256, Co=4, H=8, W=8, fh=3),                      # 8x8, g_c = 64
+    dict(n=4096, p=65537, B=3, Ci=40, Co=3, H=8, W=8, fh=3, g_c=16, g_b=4),        # image blocks, ragged B
+    dict(n=4096, p=12289, B=5, Ci=3, Co=2, H=16, W=16, fh=3, g_c=2, g_b=3),        # two slot sets (d = 2)
+    dict(n=256, p=65537, B=3, Ci=5, Co=3, H=8, W=8, fh=3, g_c=2, g_b=2),           # small ring, ragged
+    dict(n=1024, p=65537, B=1, Ci=2, Co=2, H=8, W=128, fh=3, fw=5),                # wide plane
+]
+
+
+@pytest.mark.parametrize("args", CASES)
+def test_fused_path_bit_exact(F, args):
+    args = dict(args)
+    n, p, B, Ci, Co, H, W, fh = (args.pop(k) for k in ("n", "p", "B", "Ci", "Co", "H", "W", "fh"))
+    fw = args.pop("fw", fh)
+    g_c, g_b, support = args.pop("g_c", None), args.pop("g_b", 1), args.pop("support", None)
+    OP = O.params(n, p)
+    OL = O.layer(OP, B, Ci, Co, H, W, g_c, g_b)
+    P = F.Params(n, p, max_T=max(OL.T, 1))
+    L = F.LayerSpec(B, Ci, Co, H, W, OL.g_c, OL.g_b)
+    g = np.random.default_rng(n + Ci + 7 * B)
+    h, w_ = support or (H, W)
+    xA = np.zeros((B, Ci, H, W), np.uint32)
+    xB = np.zeros((B, Ci, H, W), np.uint32)
+    xA[:, :, :h, :w_] = g.integers(0, p, (B, Ci, h, w_))
+    xB[:, :, :h, :w_] = g.integers(0, p, (B, Ci, h, w_))
+    w = g.integers(-8, 8, (Co, Ci, fh, fw)).astype(np.int8)
+    ks, es, ss = 71, 72, 73
+    ref = O.round_trip(OP, OL, xA, xB, w, ks, es, ss)
+    q = OP.q
+
+    t_hat = F.keygen(P, ks)
+    Phat = F.filter_prepare(P, L, dev(w, np.int8))
+    Mhat, sB = F.mask_prepare(P, L, ss)
+    C0 = F.encrypt_constants(P, L, t_hat, es)
+    zero = np.zeros((B, Ci, H * W), np.uint32)
+    assert np.array_equal(u64(C0).reshape(OL.n_in, 2, n), O.encrypt(OP, OL, ref["t_hat"], zero, es))
+    dA, dB = dev(xA, np.int32), dev(xB, np.int32)
+    A = F.encode_share(P, L, dA)
+    Bsh = F.encode_share(P, L, dB)
+    # constants + message = encryption; + Bob's plaintext = HomRec
+    got_enc = u64(C0).reshape(OL.n_in, 2, n).astype(object)
+    got_enc[:, 1] = (got_enc[:, 1] + u64(A).reshape(OL.n_in, n).astype(object)) % q
+    assert np.array_equal(got_enc.astype(np.uint64), ref["ct_enc"])
+    ct = F.encrypt_constants(P, L, t_hat, es)
+    F.homrec_share(P, L, dA, ct)
+    F.homrec_share(P, L, dB, ct)
+    assert np.array_equal(u64(ct).reshape(ref["ct_rec"].shape), ref["ct_rec"])
+    out = F.homconv_sum(P, L, C0, A, Bsh, Phat, Mhat)
+    assert np.array_equal(u64(out).reshape(ref["ct_out"].shape), ref["ct_out"])
+    out1 = F.homconv_sum(P, L, ct, None, None, Phat, Mhat)
+    assert torch.equal(out, out1)
+    yA = F.decrypt_share(P, L, t_hat, out)
+    assert np.array_equal(u32(yA).reshape(ref["yA"].shape), ref["yA"])
+    torch.cuda.synchronize()
+    P.close()
+
+
+def test_fused_path_rejects_unsupported_shapes(F):
+    P = F.Params(1024, 65537)
+    L = F.LayerSpec(1, 2, 2, 64, 64, 1, 1)  # H W = 4096 > S = 1024: spectra span several ciphertexts
+    x = torch.zeros(2 * 64 * 64, dtype=torch.int32, device="cuda")
+    with pytest.raises(F.FdscError) as e:
+        F.encode_share(P, L, x)
+    assert e.value.code == -5
+    L2 = F.LayerSpec(1, 2, 2, 4, 64, 1, 1)  # H = 4 < 8
+    with pytest.raises(F.FdscError) as e:
+        F.encode_share(P, L2, torch.zeros(2 * 4 * 64, dtype=torch.int32, device="cuda"))
+    assert e.value.code == -5
+    P.close()
