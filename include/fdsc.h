@@ -220,8 +220,10 @@ int fdsc_decrypt_share(const fdsc_params* P, const fdsc_layer* L, const uint64_t
 /* Selects the HomConv kernel variant for later fdsc_homconv calls in this
  * process (all variants give identical results): 0 automatic (default),
  * 1 limb-column accumulation with one image group per thread, 2 the same
- * with two image groups per thread, 3 carry-chained 128-bit accumulation.
- * FDSC_ERR_ARG for other values.  Not synchronised with concurrent calls. */
+ * with two image groups per thread, 3 carry-chained 128-bit accumulation,
+ * 4 input tile staged in shared memory with carry-chained accumulation,
+ * 5 staged tile with limb columns.  FDSC_ERR_ARG for other values.  Not
+ * synchronised with concurrent calls. */
 int fdsc_set_homconv_variant(int variant);
 
 #ifdef __cplusplus

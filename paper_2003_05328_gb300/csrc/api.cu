@@ -143,9 +143,10 @@ namespace {
 // The fused spatial-domain kernels need whole spectra inside one ciphertext
 // (H W <= S), radix-8 lines (H, W >= 8) and their shared memory to fit.
 int check_fused(const fdsc_params* P, const DevLayer& D, size_t smem, const char* what) {
-    if (D.beta != 1 || D.logH < 3 || D.logW < 3)
+    if (D.beta != 1 || D.logH < 3 || D.logW < 3 || D.logH > 9 || D.logW > 9)
         return fdsc_set_error(FDSC_ERR_UNSUPPORTED,
-                              "%s needs H, W >= 8 and H W <= S; use fdsc_ntt2d/fdsc_encrypt/fdsc_decrypt", what);
+                              "%s needs 8 <= H, W <= 512 and H W <= S; use fdsc_ntt2d/fdsc_encrypt/fdsc_decrypt",
+                              what);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -36,6 +36,11 @@ struct DevParams {
     const u32* w2di;       // w_lmax^-k
     const u32* w2di_s;
     const u64* cdt;        // [19] Gaussian cumulative table
+    // the same twiddles interleaved with their Shoup companions
+    const ulonglong2* qfw2;  // (psi^brv(k), companion), k < n
+    const ulonglong2* qinv2;
+    const uint2* pfw2;       // k < S
+    const uint2* pinv2;
 };
 
 // A layer with its packing, derived (all counts fit in 32 bits).

@@ -244,13 +244,124 @@ cudaError_t launch_variant(const DevParams& P, const DevLayer& L, const u64* ct_
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------- v3: staged input tile
+// A CTA covers kJ3 consecutive evaluation indices (one per lane) and kW3
+// output channels (one per warp).  Its input tile -- every ciphertext k of
+// the image group at those indices, with the c1 addends already summed -- is
+// staged once in shared memory; the warps then stream only filter words from
+// HBM, prefetching the next kPF3 terms while the current ones are multiplied.
+constexpr u32 kJ3 = 32, kW3 = 8, kThreads3 = 32 * kW3, kPF3 = 8;
+
+template <bool kWide>
+__global__ void __launch_bounds__(kThreads3) homconv3_kernel(DevParams P, DevLayer L, const u64* __restrict__ ct_in,
+                                                             const u64* __restrict__ A1, const u64* __restrict__ A2,
+                                                             const u64* __restrict__ Phat,
+                                                             const u64* __restrict__ Mhat, u64* __restrict__ ct_out,
+                                                             u32 jtiles, u32 ctiles) {
+    extern __shared__ __align__(16) u64 xs[];  // [T][2][kJ3] canonical words, or 30-bit limb pairs
+    using Acc = typename std::conditional<kWide, AccLimb, Acc128>::type;
+    u32 blk = blockIdx.x;
+    const u32 jt = blk % jtiles;
+    blk /= jtiles;
+    const u32 ct = blk % ctiles, bb = blk / ctiles;
+    const u32 nJ = L.beta * P.n, T = L.T;
+    const u64 n = P.n, beta = L.beta;
+    // stage the input tile (all threads)
+    for (u32 e = threadIdx.x; e < T * kJ3; e += kThreads3) {
+        const u32 k = e / kJ3, jj = e % kJ3, J = jt * kJ3 + jj;
+        u64 x0 = 0, x1 = 0;
+        if (J < nJ) {
+            const u32 h = J >> P.logn, j = J & (P.n - 1);
+            const u64 u = ((u64)bb * T + k) * beta + h;
+            x0 = __ldg(ct_in + u * 2 * n + j);
+            x1 = __ldg(ct_in + u * 2 * n + n + j);
+            if (A1) x1 = addmod_q(x1, __ldg(A1 + u * n + j), P.q);
+            if (A2) x1 = addmod_q(x1, __ldg(A2 + u * n + j), P.q);
+        }
+        if constexpr (kWide) {
+            x0 = (x0 & kM30) | ((x0 >> 30) << 32);
+            x1 = (x1 & kM30) | ((x1 >> 30) << 32);
+        }
+        xs[(k * 2 + 0) * kJ3 + jj] = x0;
+        xs[(k * 2 + 1) * kJ3 + jj] = x1;
+    }
+    __syncthreads();
+    const u32 lane = threadIdx.x & 31, co = ct * kW3 + (threadIdx.x >> 5), J = jt * kJ3 + lane;
+    if (co >= L.Co || J >= nJ) return;
+    const u32 h = J >> P.logn, j = J & (P.n - 1);
+    const u64* wp = Phat + ((u64)co * T * beta + h) * n + j;
+    const u64 w_step = beta * n;
+
+    Acc acc0, acc1;
+    acc_zero(acc0);
+    acc_zero(acc1);
+    u64 wbuf[kPF3];
+#pragma unroll
+    for (u32 u = 0; u < kPF3; u++) wbuf[u] = u < T ? __ldg(wp + u * w_step) : 0;
+    for (u32 k0 = 0; k0 < T; k0 += kPF3) {
+        u64 wcur[kPF3];
+#pragma unroll
+        for (u32 u = 0; u < kPF3; u++) {
+            wcur[u] = wbuf[u];
+            const u32 kn = k0 + kPF3 + u;
+            if (kn < T) wbuf[u] = __ldg(wp + kn * w_step);
+        }
+#pragma unroll
+        for (u32 u = 0; u < kPF3; u++) {
+            const u32 k = k0 + u;
+            if (k >= T) break;
+            const u64 xa = xs[(k * 2 + 0) * kJ3 + lane], xb = xs[(k * 2 + 1) * kJ3 + lane];
+            if constexpr (kWide) {
+                const u32 w0 = (u32)(wcur[u] & kM30), w1 = (u32)(wcur[u] >> 30);
+                acc_mac_limbs(acc0, (u32)xa, (u32)(xa >> 32), w0, w1);
+                acc_mac_limbs(acc1, (u32)xb, (u32)(xb >> 32), w0, w1);
+            } else {
+                acc_mac(acc0, xa, wcur[u]);
+                acc_mac(acc1, xb, wcur[u]);
+            }
+        }
+        if constexpr (kWide) {
+            acc_normalize(acc0);
+            acc_normalize(acc1);
+        }
+        if (((k0 + kPF3) & 255u) == 0 && k0 + kPF3 < T) {
+            acc_set(acc0, acc_reduce(acc0, P));
+            acc_set(acc1, acc_reduce(acc1, P));
+        }
+    }
+    const u64 v = ((u64)bb * L.Co + co) * beta + h;
+    const u64 r0 = acc_reduce(acc0, P);
+    u64 r1 = acc_reduce(acc1, P);
+    if (Mhat) r1 = submod_q(r1, __ldg(Mhat + v * n + j), P.q);
+    ct_out[v * 2 * n + j] = r0;
+    ct_out[v * 2 * n + n + j] = r1;
+}
+
+template <bool W>
+cudaError_t launch_v3(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                      const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
+    const u32 nJ = L.beta * P.n;
+    const u32 jtiles = (nJ + kJ3 - 1) / kJ3, ctiles = (L.Co + kW3 - 1) / kW3;
+    const u64 grid = (u64)jtiles * ctiles * L.GB;
+    const size_t smem = (size_t)L.T * 2 * kJ3 * 8;
+    if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
+    if (smem + 1024 > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(homconv3_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    homconv3_kernel<W><<<(u32)grid, kThreads3, smem, s>>>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, jtiles, ctiles);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // Variant selection: 0 = automatic, 1 = limb columns NB=1, 2 = limb columns
-// NB=2, 3 = carry chain NB=1.
+// NB=2, 3 = carry chain NB=1, 4 = staged tile with carry chain, 5 = staged
+// tile with limb columns.
 static int g_homconv_variant = 0;
 extern "C" int fdsc_set_homconv_variant(int v) {
-    if (v < 0 || v > 3) return FDSC_ERR_ARG;
+    if (v < 0 || v > 5) return FDSC_ERR_ARG;
     g_homconv_variant = v;
     return FDSC_OK;
 }
@@ -271,7 +382,11 @@ cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_
                            const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
     int v = g_homconv_variant;
     if (v == 0) v = 3;
+    // the staged tile must fit in shared memory (T <= 256 words x 2 x 32 lanes)
+    if ((v == 4 || v == 5) && L.T > 256) v = 3;
     switch (v) {
+        case 4: return launch_v3<false>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+        case 5: return launch_v3<true>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
         case 1: return launch_adds<1, true>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
         case 2: return launch_adds<2, true>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
         default: return launch_adds<1, false>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);

@@ -8,6 +8,8 @@
 // D. Harvey, "Faster arithmetic for number-theoretic transforms", 2014).
 // Butterflies keep values lazily in [0, 4m) (Harvey), which needs 4q < 2^64.
 #pragma once
+#include <utility>
+
 #include "fdsc_internal.h"
 
 // ------------------------------------------------------------------ mod q
@@ -498,4 +500,181 @@ __device__ __forceinline__ void lines_r8(u32* buf, u32 planes, bool rows, u32 lo
         }
         __syncthreads();
     }
+}
+
+// ------------------------------------------------------------------ padded radix-8 passes
+// Shared arrays of the fused kernels hold element i at padx(i): one word of
+// padding every 32 keeps the strided windows of the last passes (stride 4
+// and 1) from piling onto a few banks.
+__device__ __forceinline__ u32 padx(u32 i) { return i + (i >> 5); }
+// Words a padded array of n elements occupies (even, so that what follows
+// stays 8-byte aligned).
+__host__ __device__ inline u32 padded_len(u32 n) { return (n + (n >> 5) + 2) & ~1u; }
+
+template <typename T>
+struct Pair;
+template <>
+struct Pair<u64> {
+    using type = ulonglong2;
+};
+template <>
+struct Pair<u32> {
+    using type = uint2;
+};
+
+template <bool kFwd, typename T>
+__device__ __forceinline__ void bfly_pair(T& x, T& y, typename Pair<T>::type w, const DevParams& P) {
+    if constexpr (sizeof(T) == 8) {
+        if (kFwd) bfly_ct_q(x, y, w.x, w.y, P);
+        else bfly_gs_q(x, y, w.x, w.y, P);
+    } else {
+        if (kFwd) bfly_ct_p(x, y, w.x, w.y, P.p);
+        else bfly_gs_p(x, y, w.x, w.y, P.p);
+    }
+}
+
+// `cnt` consecutive length-2^logL vectors (logL >= 3) in a padded shared
+// array.  kFwd: natural in, bit-reversed evaluation order out (CT); else
+// bit-reversed in, natural out, times L^-1 (GS).  mod q: forward input in
+// [0, 4q), every output canonical.  Twiddles are (value, companion) pairs:
+// stage bit b, pair with lower index i uses tw[(L + i) >> (b + 1)].  The pass
+// loop stays a loop (compact code); per pass each thread computes one base
+// and per stage one twiddle base, the rest are constant offsets.
+template <bool kFwd, typename T>
+__device__ __forceinline__ void ntt_r8p(T* a, u32 logL, u32 cnt, const typename Pair<T>::type* tw, T inv, T inv_s,
+                                        const DevParams& P) {
+    const u32 L = 1u << logL, lper = logL - 3;
+    const bool active = threadIdx.x < (cnt << lper);
+    const u32 tl = threadIdx.x & ((1u << lper) - 1u), voff = (threadIdx.x >> lper) << logL;
+    const int npass = ((int)logL + 2) / 3;
+    for (int ps = 0; ps < npass; ps++) {
+        int hi, lo;
+        u32 wlo;
+        if (kFwd) {
+            hi = (int)logL - 1 - 3 * ps;
+            lo = hi - 2 > 0 ? hi - 2 : 0;
+            wlo = hi >= 2 ? (u32)hi - 2 : 0u;
+        } else {
+            lo = 3 * ps;
+            hi = lo + 2 < (int)logL - 1 ? lo + 2 : (int)logL - 1;
+            wlo = (u32)lo + 3 <= logL ? (u32)lo : logL - 3;
+        }
+        if (active) {
+            const u32 hb = (tl >> wlo) << (wlo + 3);
+            const u32 base = voff + (hb | (tl & ((1u << wlo) - 1u)));
+            T x[8];
+#pragma unroll
+            for (int r = 0; r < 8; r++) x[r] = a[padx(base + ((u32)r << wlo))];
+#pragma unroll
+            for (int s = 0; s < 3; s++) {
+                const int RB = kFwd ? 2 - s : s;
+                const int b = (int)wlo + RB;
+                if (b > hi || b < lo) continue;
+                const u32 tb = (L + hb) >> (b + 1);
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    if (r & (1 << RB)) continue;
+                    bfly_pair<kFwd>(x[r], x[r | (1 << RB)], tw[tb + (r >> (RB + 1))], P);
+                }
+            }
+            if (ps == npass - 1) {
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    if constexpr (sizeof(T) == 8) {
+                        T y = kFwd ? x[r] : shoup_mul(x[r], inv, inv_s, P.q);
+                        if (kFwd) y = y >= P.twoq ? y - P.twoq : y;
+                        x[r] = y >= P.q ? y - P.q : y;
+                    } else if (!kFwd) {
+                        T y = shoup_mul32(x[r], inv, inv_s, P.p);
+                        x[r] = y >= P.p ? y - P.p : y;
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 8; r++) a[padx(base + ((u32)r << wlo))] = x[r];
+        }
+        __syncthreads();
+    }
+}
+
+// Cyclic radix-8 line passes on stacked H x W planes in a padded shared
+// array (rows: planes*H lines of W; columns: planes*W lines of H).  `tw`
+// holds (w_L^k, companion) pairs for k < L/2, L the line length: stage t = 2^b
+// uses tw[(i mod t) << (logL - 1 - b)].  kDif: natural in, bit-reversed out;
+// else bit-reversed in, natural out.  Needs L >= 8 and planes*HW/8 threads.
+template <bool kDif>
+__device__ __forceinline__ void lines_r8p(u32* buf, u32 planes, bool rows, u32 logH, u32 logW, const uint2* tw,
+                                          u32 p) {
+    const u32 logL = rows ? logW : logH, lper = logL - 3;
+    const u32 nlines = planes << (rows ? logH : logW);
+    const bool active = threadIdx.x < (nlines << lper);
+    u32 line, tl;
+    if (rows) {
+        line = threadIdx.x >> lper;
+        tl = threadIdx.x & ((1u << lper) - 1u);
+    } else {
+        line = threadIdx.x % nlines;
+        tl = threadIdx.x / nlines;
+    }
+    const u32 lbase = rows ? line << logW : ((line >> logW) << (logH + logW)) + (line & ((1u << logW) - 1u));
+    const u32 sl = rows ? 0u : logW;
+    const int npass = ((int)logL + 2) / 3;
+    for (int ps = 0; ps < npass; ps++) {
+        int hi, lo;
+        u32 wlo;
+        if (kDif) {
+            hi = (int)logL - 1 - 3 * ps;
+            lo = hi - 2 > 0 ? hi - 2 : 0;
+            wlo = hi >= 2 ? (u32)hi - 2 : 0u;
+        } else {
+            lo = 3 * ps;
+            hi = lo + 2 < (int)logL - 1 ? lo + 2 : (int)logL - 1;
+            wlo = (u32)lo + 3 <= logL ? (u32)lo : logL - 3;
+        }
+        if (active) {
+            const u32 low = tl & ((1u << wlo) - 1u);
+            const u32 ib = ((tl >> wlo) << (wlo + 3)) | low;
+            u32 off[8], x[8];
+#pragma unroll
+            for (int r = 0; r < 8; r++) {
+                off[r] = padx(lbase + ((ib + ((u32)r << wlo)) << sl));
+                x[r] = buf[off[r]];
+            }
+#pragma unroll
+            for (int s = 0; s < 3; s++) {
+                const int RB = kDif ? 2 - s : s;
+                const int b = (int)wlo + RB;
+                if (b > hi || b < lo) continue;
+                const u32 sh = logL - 1 - (u32)b, tlow = low << sh;
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    if (r & (1 << RB)) continue;
+                    const uint2 w = tw[tlow + (((u32)(r & ((1 << RB) - 1)) << wlo) << sh)];
+                    const u32 u = x[r], v = x[r | (1 << RB)];
+                    if (kDif) {
+                        x[r] = addmod_p(u, v, p);
+                        u32 d = shoup_mul32(submod_p(u, v, p), w.x, w.y, p);
+                        x[r | (1 << RB)] = d >= p ? d - p : d;
+                    } else {
+                        u32 m = shoup_mul32(v, w.x, w.y, p);
+                        m = m >= p ? m - p : m;
+                        x[r] = addmod_p(u, m, p);
+                        x[r | (1 << RB)] = submod_p(u, m, p);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 8; r++) buf[off[r]] = x[r];
+        }
+        __syncthreads();
+    }
+}
+
+// Compact (w_L^k, companion) table for k < L/2, gathered from the params'
+// w_lmax table; plain loads by the whole CTA (no barrier).
+__device__ __forceinline__ void load_pairs_for_length(uint2* dst, u32 logL, bool inverse, const DevParams& P) {
+    const u32* g = inverse ? P.w2di : P.w2d;
+    const u32* gs = inverse ? P.w2di_s : P.w2d_s;
+    const u32 half = 1u << (logL - 1), sh = P.loglmax - logL;
+    for (u32 k = threadIdx.x; k < half; k += blockDim.x) dst[k] = make_uint2(__ldg(g + (k << sh)), __ldg(gs + (k << sh)));
 }

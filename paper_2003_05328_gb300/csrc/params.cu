@@ -252,10 +252,24 @@ extern "C" int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_p
     }
     u64 cdt[19];
     fdsc_host_cdt(cdt);
+    std::vector<u64> qfw2(2ull * n), qinv2(2ull * n);
+    for (u32 k = 0; k < n; k++) {
+        qfw2[2 * k] = qfw[k];
+        qfw2[2 * k + 1] = qfw_s[k];
+        qinv2[2 * k] = qinv[k];
+        qinv2[2 * k + 1] = qinv_s[k];
+    }
+    std::vector<u32> pfw2(2ull * S), pinv2(2ull * S);
+    for (u32 k = 0; k < S; k++) {
+        pfw2[2 * k] = pfw[k];
+        pfw2[2 * k + 1] = pfw_s[k];
+        pinv2[2 * k] = pinv[k];
+        pinv2[2 * k + 1] = pinv_s[k];
+    }
 
     // one allocation: [qfw | qfw_s | qinv | qinv_s] [cdt] [pfw .. pinv_s] [w2 .. w2is]
     const size_t bytes_q = 4ull * n * 8, bytes_cdt = 19 * 8 + 8, bytes_p = 4ull * S * 4, bytes_w = 4ull * half * 4;
-    const size_t total = bytes_q + bytes_cdt + bytes_p + bytes_w + 64;
+    const size_t total = 2 * bytes_q + bytes_cdt + 2 * bytes_p + bytes_w + 256;
     fdsc_params* P = new (std::nothrow) fdsc_params();
     if (!P) return fdsc_set_error(FDSC_ERR_OOM, "host allocation failed");
     P->info = I;
@@ -271,7 +285,7 @@ extern "C" int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_p
     unsigned char* h = host.data();
     size_t off = 0;
     auto put = [&](const void* src, size_t b) {
-        memcpy(h + off, src, b);
+        if (off + b <= total) memcpy(h + off, src, b);
         size_t o = off;
         off += (b + 15) & ~size_t(15);
         return o;
@@ -283,6 +297,13 @@ extern "C" int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_p
     size_t o_pinv = put(pinv.data(), 4ull * S), o_pinv_s = put(pinv_s.data(), 4ull * S);
     size_t o_w2 = put(w2.data(), 4ull * half), o_w2s = put(w2s.data(), 4ull * half);
     size_t o_w2i = put(w2i.data(), 4ull * half), o_w2is = put(w2is.data(), 4ull * half);
+    size_t o_qfw2 = put(qfw2.data(), 16ull * n), o_qinv2 = put(qinv2.data(), 16ull * n);
+    size_t o_pfw2 = put(pfw2.data(), 8ull * S), o_pinv2 = put(pinv2.data(), 8ull * S);
+    if (off > total) {  // layout bookkeeping error: never write past the allocation
+        cudaFree(P->table_mem);
+        delete P;
+        return fdsc_set_error(FDSC_ERR_ARG, "internal: table layout %zu > %zu bytes", off, total);
+    }
     e = cudaMemcpy(P->table_mem, h, off, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(P->table_mem);
@@ -310,6 +331,8 @@ extern "C" int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_p
     D.pinv = (const u32*)(dbase + o_pinv); D.pinv_s = (const u32*)(dbase + o_pinv_s);
     D.w2d = (const u32*)(dbase + o_w2); D.w2d_s = (const u32*)(dbase + o_w2s);
     D.w2di = (const u32*)(dbase + o_w2i); D.w2di_s = (const u32*)(dbase + o_w2is);
+    D.qfw2 = (const ulonglong2*)(dbase + o_qfw2); D.qinv2 = (const ulonglong2*)(dbase + o_qinv2);
+    D.pfw2 = (const uint2*)(dbase + o_pfw2); D.pinv2 = (const uint2*)(dbase + o_pinv2);
     *out = P;
     return FDSC_OK;
 }

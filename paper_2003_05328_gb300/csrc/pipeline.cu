@@ -25,39 +25,25 @@ constexpr u32 kMaxThreads = 512;
 
 inline u32 threads_for(u32 n) { return n / 8 < 32 ? 32 : n / 8; }
 
-// Compact table of w_L^k, k < L/2, L = max(H, W) (a strided gather of the
-// params' w_lmax table), loaded with plain loads.
-__device__ __forceinline__ void load_line_table(u32* tw, u32* tws, u32 logT, bool inverse, const DevParams& P) {
-    const u32* g = inverse ? P.w2di : P.w2d;
-    const u32* gs = inverse ? P.w2di_s : P.w2d_s;
-    const u32 half = 1u << (logT - 1), sh = P.loglmax - logT;
-    for (u32 k = threadIdx.x; k < half; k += blockDim.x) {
-        tw[k] = __ldg(g + (k << sh));
-        tws[k] = __ldg(gs + (k << sh));
-    }
-}
-
 // ---------------------------------------------------------------- encryption constants
 __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, const u64* __restrict__ t_hat, u64 seed,
                                                                 u64* __restrict__ ct) {
     extern __shared__ __align__(16) unsigned char sm[];
     const u32 n = P.n;
-    u64* tq = reinterpret_cast<u64*>(sm);  // [n] psi^brv
-    u64* tqs = tq + n;                     // [n]
-    u64* c = tqs + n;                      // [n]
+    ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^brv, companion)
+    u64* c = reinterpret_cast<u64*>(tq + n);             // padded [n]
     __shared__ u64 cdt[19];
-    stage_async(tq, P.qfw, n * 8);
-    stage_async(tqs, P.qfw_s, n * 8);
+    stage_async(tq, P.qfw2, n * 16);
     if (threadIdx.x < 19) cdt[threadIdx.x] = P.cdt[threadIdx.x];
     __syncthreads();
     const u32 u = blockIdx.x;
     const u64 keyE = stream_key(seed, DOM_E);
     for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
         const int e = gauss_sample(stream_at(keyE, (u64)u * n + i), cdt);
-        c[i] = e >= 0 ? (u64)e : P.q - (u64)(-e);
+        c[padx(i)] = e >= 0 ? (u64)e : P.q - (u64)(-e);
     }
     stage_wait();
-    ntt_fwd_r8<u64>(c, P.logn, 1, tq, tqs, P);
+    ntt_r8p<true, u64>(c, P.logn, 1, tq, 0, 0, P);
     const u64 keyA = stream_key(seed, DOM_A);
     u64* c0 = ct + (u64)u * 2 * n;
     u64* c1 = c0 + n;
@@ -65,7 +51,7 @@ __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, con
         const u64 idx = 2 * ((u64)u * n + j);
         const u64 a = uniform_q(stream_at(keyA, idx), stream_at(keyA, idx + 1), P.q);
         c0[j] = a ? P.q - a : 0;
-        c1[j] = addmod_q(mulmod_q(a, __ldg(t_hat + j), P), c[j], P.q);
+        c1[j] = addmod_q(mulmod_q(a, __ldg(t_hat + j), P), c[padx(j)], P.q);
     }
 }
 
@@ -77,20 +63,17 @@ __global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLaye
                                                             u64* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char sm[];
     const u32 n = P.n, S = P.S;
-    u64* tq = reinterpret_cast<u64*>(sm);
-    u64* tqs = tq + n;
-    u64* c = tqs + n;
-    u32* tp = reinterpret_cast<u32*>(c + n);  // [S] psi_p^-brv
-    u32* tps = tp + S;
-    u32* slots = tps + S;                       // [n] = d slot sets
-    u32* t2 = slots + n;                        // [T/2] line twiddles
-    const u32 logT = L.logH > L.logW ? L.logH : L.logW;
-    u32* t2s = t2 + (1u << (logT - 1));
-    stage_async(tq, P.qfw, n * 8);
-    stage_async(tqs, P.qfw_s, n * 8);
-    stage_async(tp, P.pinv, S * 4);
-    stage_async(tps, P.pinv_s, S * 4);
-    load_line_table(t2, t2s, logT, false, P);
+    const u32 np = padded_len(n);                        // padded length (even)
+    ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n]
+    u64* c = reinterpret_cast<u64*>(tq + n);             // padded [n]
+    uint2* tp = reinterpret_cast<uint2*>(c + np);        // [S] (psi_p^-brv, companion)
+    u32* slots = reinterpret_cast<u32*>(tp + S);         // padded [n] = d slot sets
+    uint2* tw_row = reinterpret_cast<uint2*>(slots + np); // [W/2]
+    uint2* tw_col = tw_row + (L.W >> 1);                 // [H/2]
+    stage_async(tq, P.qfw2, n * 16);
+    stage_async(tp, P.pinv2, S * 8);
+    load_pairs_for_length(tw_row, L.logW, false, P);
+    load_pairs_for_length(tw_col, L.logH, false, P);
 
     const u32 u = blockIdx.x, k = u % L.T, bb = u / L.T;
     const u32 HW = L.HW, logHW = L.logH + L.logW, blocks = L.g_c * L.g_b;
@@ -103,26 +86,26 @@ __global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLaye
             if (b < L.B && ci < L.Ci) v = __ldg(x + ((u64)b * L.Ci + ci) * HW + f);
         }
         const u32 pos = (e & ~(HW - 1)) + (brv_bits(f >> L.logW, L.logH) << L.logW) + brv_bits(f & (L.W - 1), L.logW);
-        slots[pos] = v;
+        slots[padx(pos)] = v;
     }
     __syncthreads();
     // NTT2D of every plane (zero planes included): rows, then columns
-    lines_r8<false>(slots, n >> logHW, true, L.logH, L.logW, t2, t2s, logT, P.p);
-    lines_r8<false>(slots, n >> logHW, false, L.logH, L.logW, t2, t2s, logT, P.p);
+    lines_r8p<false>(slots, n >> logHW, true, L.logH, L.logW, tw_row, P.p);
+    lines_r8p<false>(slots, n >> logHW, false, L.logH, L.logW, tw_col, P.p);
     stage_wait();
-    ntt_inv_r8<u32>(slots, P.logS, P.d, tp, tps, P.Sinv, P.Sinv_s, P);  // slot encode
+    ntt_r8p<false, u32>(slots, P.logS, P.d, tp, P.Sinv, P.Sinv_s, P);  // slot encode
     for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
         const u32 r = e >> P.logS, i = e & (S - 1);
-        c[r + P.d * i] = P.delta * slots[e];
+        c[padx(r + P.d * i)] = P.delta * slots[padx(e)];
     }
     __syncthreads();
-    ntt_fwd_r8<u64>(c, P.logn, 1, tq, tqs, P);
+    ntt_r8p<true, u64>(c, P.logn, 1, tq, 0, 0, P);
     if (kMode == 0) {
         u64* A = out + (u64)u * n;
-        for (u32 j = threadIdx.x; j < n; j += blockDim.x) A[j] = c[j];
+        for (u32 j = threadIdx.x; j < n; j += blockDim.x) A[j] = c[padx(j)];
     } else {
         u64* c1 = out + (u64)u * 2 * n + n;
-        for (u32 j = threadIdx.x; j < n; j += blockDim.x) c1[j] = addmod_q(c1[j], c[j], P.q);
+        for (u32 j = threadIdx.x; j < n; j += blockDim.x) c1[j] = addmod_q(c1[j], c[padx(j)], P.q);
     }
 }
 
@@ -142,53 +125,50 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
                                                                     u32 scale, u32 scale_s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const u32 n = P.n, S = P.S;
-    u64* tq = reinterpret_cast<u64*>(sm);
-    u64* tqs = tq + n;
-    u64* c = tqs + n;
-    u32* tp = reinterpret_cast<u32*>(c + n);
-    u32* tps = tp + S;
-    u32* slots = tps + S;
-    u32* planes = slots + n;                    // [d g_b HW]
-    const u32 logT = L.logH > L.logW ? L.logH : L.logW;
+    const u32 np = padded_len(n);
+    ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^-brv, companion)
+    u64* c = reinterpret_cast<u64*>(tq + n);             // padded [n]
+    uint2* tp = reinterpret_cast<uint2*>(c + np);        // [S] (psi_p^brv, companion)
+    u32* slots = reinterpret_cast<u32*>(tp + S);         // padded [n]
     const u32 HW = L.HW, logHW = L.logH + L.logW;
     const u32 nplanes = P.d * L.g_b;
-    u32* t2 = planes + nplanes * HW;
-    u32* t2s = t2 + (1u << (logT - 1));
-    stage_async(tq, P.qinv, n * 8);
-    stage_async(tqs, P.qinv_s, n * 8);
-    stage_async(tp, P.pfw, S * 4);
-    stage_async(tps, P.pfw_s, S * 4);
-    load_line_table(t2, t2s, logT, true, P);
+    u32* planes = slots + np;                            // padded [d g_b HW]
+    uint2* tw_row = reinterpret_cast<uint2*>(planes + padded_len(nplanes * HW));
+    uint2* tw_col = tw_row + (L.W >> 1);
+    stage_async(tq, P.qinv2, n * 16);
+    stage_async(tp, P.pfw2, S * 8);
+    load_pairs_for_length(tw_row, L.logW, true, P);
+    load_pairs_for_length(tw_col, L.logH, true, P);
 
     const u32 v = blockIdx.x, co = v % L.Co, bb = v / L.Co;
     const u64* c0 = ct + (u64)v * 2 * n;
     const u64* c1 = c0 + n;
     for (u32 j = threadIdx.x; j < n; j += blockDim.x)
-        c[j] = addmod_q(mulmod_q(__ldg(c0 + j), __ldg(t_hat + j), P), __ldg(c1 + j), P.q);
+        c[padx(j)] = addmod_q(mulmod_q(__ldg(c0 + j), __ldg(t_hat + j), P), __ldg(c1 + j), P.q);
     stage_wait();
-    ntt_inv_r8<u64>(c, P.logn, 1, tq, tqs, P.ninv, P.ninv_s, P);
+    ntt_r8p<false, u64>(c, P.logn, 1, tq, P.ninv, P.ninv_s, P);
     for (u32 coef = threadIdx.x; coef < n; coef += blockDim.x) {
         const u32 r = coef & (P.d - 1), i = coef / P.d;
-        slots[r * S + i] = round_pq2(c[coef], P);
+        slots[padx(r * S + i)] = round_pq2(c[padx(coef)], P);
     }
     __syncthreads();
-    ntt_fwd_r8<u32>(slots, P.logS, P.d, tp, tps, P);  // slot decode
+    ntt_r8p<true, u32>(slots, P.logS, P.d, tp, 0, 0, P);  // slot decode
     // fold the g_c channel blocks of every image block: plane (r, ib)
     for (u32 e = threadIdx.x; e < nplanes * HW; e += blockDim.x) {
         const u32 pl = e >> logHW, f = e & (HW - 1), r = pl / L.g_b, ib = pl % L.g_b;
-        const u32* src = slots + r * S + ib * L.g_c * HW + f;
+        const u32 src = r * S + ib * L.g_c * HW + f;
         u32 acc = 0;
-        for (u32 ic = 0; ic < L.g_c; ic++) acc = addmod_p(acc, src[ic * HW], P.p);
-        planes[e] = acc;
+        for (u32 ic = 0; ic < L.g_c; ic++) acc = addmod_p(acc, slots[padx(src + ic * HW)], P.p);
+        planes[padx(e)] = acc;
     }
     __syncthreads();
-    lines_r8<true>(planes, nplanes, true, L.logH, L.logW, t2, t2s, logT, P.p);
-    lines_r8<true>(planes, nplanes, false, L.logH, L.logW, t2, t2s, logT, P.p);
+    lines_r8p<true>(planes, nplanes, true, L.logH, L.logW, tw_row, P.p);
+    lines_r8p<true>(planes, nplanes, false, L.logH, L.logW, tw_col, P.p);
     for (u32 e = threadIdx.x; e < nplanes * HW; e += blockDim.x) {
         const u32 pl = e >> logHW, f = e & (HW - 1), r = pl / L.g_b, ib = pl % L.g_b;
         const u32 b = (bb * P.d + r) * L.g_b + ib;
         if (b >= L.B) continue;
-        u32 val = planes[(pl << logHW) + (brv_bits(f >> L.logW, L.logH) << L.logW) + brv_bits(f & (L.W - 1), L.logW)];
+        u32 val = planes[padx((pl << logHW) + (brv_bits(f >> L.logW, L.logH) << L.logW) + brv_bits(f & (L.W - 1), L.logW))];
         val = shoup_mul32(val, scale, scale_s, P.p);
         y[((u64)b * L.Co + co) * HW + f] = val >= P.p ? val - P.p : val;
     }
@@ -200,18 +180,18 @@ cudaError_t opt_in(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-u32 line_log(const DevLayer& L) { return L.logH > L.logW ? L.logH : L.logW; }
 
 }  // namespace
 
 size_t share_smem_bytes(const DevParams& P, const DevLayer& L) {
-    return (size_t)P.n * 8 * 3 + (size_t)P.S * 8 + (size_t)P.n * 4 + (size_t)8 * (1u << (line_log(L) - 1));
+    const size_t np = padded_len(P.n);
+    return (size_t)P.n * 16 + np * 8 + (size_t)P.S * 8 + np * 4 + (size_t)4 * (L.W + L.H);
 }
 size_t decrypt_share_smem_bytes(const DevParams& P, const DevLayer& L) {
-    return (size_t)P.n * 8 * 3 + (size_t)P.S * 8 + (size_t)P.n * 4 + (size_t)P.d * L.g_b * L.HW * 4 +
-           (size_t)8 * (1u << (line_log(L) - 1));
+    const size_t np = padded_len(P.n), npl = padded_len(P.d * L.g_b * L.HW);
+    return (size_t)P.n * 16 + np * 8 + (size_t)P.S * 8 + np * 4 + npl * 4 + (size_t)4 * (L.W + L.H);
 }
-size_t constants_smem_bytes(const DevParams& P) { return (size_t)P.n * 24; }
+size_t constants_smem_bytes(const DevParams& P) { return (size_t)P.n * 16 + (size_t)padded_len(P.n) * 8; }
 
 cudaError_t launch_constants(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 seed, u64* ct,
                              cudaStream_t s) {

@@ -255,3 +255,40 @@ def test_argument_errors_are_reported(F):
         F.Params(4096, 65537, max_T=100000)
     assert e.value.code == -2
     P.close()
+
+
+@pytest.mark.parametrize("shape", [(2048, 1, 64, 64, 32, 32, 2, 1), (4096, 2, 256, 8, 8, 8, 64, 1),
+                                   (1024, 3, 5, 7, 16, 16, 2, 2), (64, 1, 300, 3, 8, 8, 1, 1),
+                                   (256, 2, 3, 5, 32, 16, 1, 1)])
+def test_homconv_variants_identical(F, shape):
+    """Every HomConv kernel variant (accumulation scheme, tiling, fused c1
+    addends) gives the oracle's words."""
+    n, B, Ci, Co, H, W, g_c, g_b = shape
+    OP = O.params(n, 65537)
+    OL = O.layer(OP, B, Ci, Co, H, W, g_c, g_b)
+    P = F.Params(n, 65537, max_T=max(OL.T, 1))
+    L = F.LayerSpec(B, Ci, Co, H, W, g_c, g_b)
+    g = np.random.default_rng(n + Ci)
+    ct = np.array(g.integers(0, OP.q, (OL.n_in, 2, n), dtype=np.uint64))
+    A1 = np.array(g.integers(0, OP.q, (OL.n_in, n), dtype=np.uint64))
+    A2 = np.array(g.integers(0, OP.q, (OL.n_in, n), dtype=np.uint64))
+    Ph = np.array(g.integers(0, OP.q, (Co * OL.T * OL.beta, n), dtype=np.uint64))
+    Mh = np.array(g.integers(0, OP.q, (OL.n_out, n), dtype=np.uint64))
+    ct[:, :, :4] = OP.q - 1
+    Ph[:, :4] = OP.q - 1
+    summed = ct.astype(object)
+    summed[:, 1] = (summed[:, 1] + A1.astype(object) + A2.astype(object)) % OP.q
+    ref = O.homconv(OP, OL, summed.astype(np.uint64), Ph, Mh)
+    d = lambda a: dev(a.view(np.int64), np.int64)
+    try:
+        for v in range(1, 6):
+            F.set_homconv_variant(v)
+            out = F.homconv_sum(P, L, d(ct), d(A1), d(A2), d(Ph), d(Mh))
+            assert np.array_equal(u64(out).reshape(ref.shape), ref), v
+            out = F.homconv_sum(P, L, d(ct), d(A1), None, d(Ph), None)
+            part = ct.astype(object)
+            part[:, 1] = (part[:, 1] + A1.astype(object)) % OP.q
+            assert np.array_equal(u64(out).reshape(ref.shape), O.homconv(OP, OL, part.astype(np.uint64), Ph, None)), v
+    finally:
+        F.set_homconv_variant(0)
+    P.close()
