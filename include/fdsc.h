@@ -48,7 +48,9 @@ enum {
     FDSC_ERR_NOISE = -2,       /* the decryption noise bound fails (q too small)  */
     FDSC_ERR_OOM = -3,         /* device or host allocation failed                */
     FDSC_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed     */
-    FDSC_ERR_UNSUPPORTED = -5  /* valid but outside what this build implements    */
+    FDSC_ERR_UNSUPPORTED = -5, /* valid but outside what this build implements    */
+    FDSC_ERR_TIMEOUT = -6,     /* a bounded wait ran out                          */
+    FDSC_ERR_BUDGET = -7       /* a request can never fit the server's HBM budget */
 };
 
 /* Message for the calling thread's most recent failure ("" if none). */
@@ -213,6 +215,125 @@ int fdsc_homconv_sum(const fdsc_params* P, const fdsc_layer* L, const uint64_t* 
  * fdsc_encode_share. */
 int fdsc_decrypt_share(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, const uint64_t* ct,
                        uint32_t* y, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Several clients in one call                                             */
+/* ---------------------------------------------------------------------- */
+/* The same as fdsc_encrypt_constants, fdsc_mask_prepare and
+ * fdsc_decrypt_share, but image group g (GB groups; one image per group when
+ * d = g_b = 1) uses its own key t_hats + g * key_stride (uint64 words; 0 = one
+ * key for all; even) and its own seed seeds[g] (DEVICE array of GB uint64),
+ * with its randomness indexed from 0 inside the group.  Each group's words are
+ * therefore exactly those of a call with that group alone (B = its images,
+ * that key, that seed), whatever else shares the launch -- what batching
+ * independent requests needs. */
+int fdsc_encrypt_constants_multi(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hats,
+                                 uint64_t key_stride, const uint64_t* seeds, uint64_t* ct, void* stream);
+int fdsc_mask_prepare_multi(const fdsc_params* P, const fdsc_layer* L, const uint64_t* seeds, uint64_t* M_hat,
+                            uint32_t* sB_hat, void* stream);
+int fdsc_decrypt_share_multi(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hats, uint64_t key_stride,
+                             const uint64_t* ct, uint32_t* y, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Batched plan: many layers and images in one graph launch                */
+/* ---------------------------------------------------------------------- */
+/* Not in the paper (a batching runtime around its per-layer protocol).  A
+ * plan holds, for every layer, the filter plaintexts and HomShare masks
+ * (prepared at creation, i.e. setup) and its intermediate ciphertext buffers,
+ * and records the whole online path of every layer (Fig. 2 lines 1-6 with
+ * HomRec) as one CUDA graph in which independent layers and the
+ * input-independent steps run concurrently.  The masks and encryption seeds
+ * are fixed at creation; a protocol run must not reuse them, so a new plan
+ * (or new seeds) is needed per inference. */
+typedef struct {
+    const fdsc_params* params;  /* created for this layer's (n, p), max_T >= T */
+    fdsc_layer layer;           /* g_c = 0: the plan chooses the packing       */
+    uint32_t fh, fw;
+    const int8_t* w;            /* device [Co][Ci][fh][fw]                     */
+    const uint64_t* t_hat;      /* device [n]: the client's key                */
+    uint64_t enc_seed, mask_seed;
+    const uint32_t* xA;         /* device [B][Ci][H][W]: Alice's share         */
+    const uint32_t* xB;         /* device [B][Ci][H][W]: Bob's share (HomRec)  */
+    uint32_t* yA;               /* device [B][Co][H][W]: Alice's output share  */
+    uint32_t* yB;               /* device [B][Co][H][W]: Bob's output share    */
+} fdsc_plan_layer;
+
+typedef struct {
+    uint32_t g_c, g_b;          /* packing used                                */
+    uint32_t homconv_variant;   /* as in fdsc_set_homconv_variant              */
+    uint32_t fused;             /* 1: fused online kernels; 0: step by step    */
+    uint32_t candidates;        /* candidates the tuner timed (0: not tuned)   */
+    uint32_t pad0;
+    double tuned_step_us;       /* the chosen candidate's median step time     */
+} fdsc_plan_layer_info;
+
+enum { FDSC_PLAN_TUNE = 1 };    /* time packings x HomConv variants, keep the fastest */
+
+typedef struct fdsc_plan fdsc_plan;
+
+/* Builds the plan on the current device: allocates its buffers, prepares
+ * filters and masks, runs every layer once and records the graph; with
+ * FDSC_PLAN_TUNE it first times every candidate packing x HomConv variant.
+ * All of this runs on the plan's own streams and has finished on return
+ * (`stream` is reserved).  Layers with H W > S or H, W outside [8, 512] use
+ * the step-by-step kernels. */
+int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, uint32_t flags, void* stream, fdsc_plan** out);
+/* One launch of the recorded graph: every layer's online path. */
+int fdsc_plan_launch(fdsc_plan* plan, void* stream);
+int fdsc_plan_layer_info_get(const fdsc_plan* plan, uint32_t i, fdsc_plan_layer_info* out);
+int fdsc_plan_destroy(fdsc_plan* plan);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of single-image requests                  */
+/* ---------------------------------------------------------------------- */
+/* Not in the paper.  A host thread inside the library admits requests (one
+ * image of one registered layer type, from one client) into batches while
+ * earlier batches are still on the GPU: each lane is a stream with its own
+ * buffers, a batch holds up to max_batch requests of one type, and a batch is
+ * launched only when the bytes of all requests in flight stay within
+ * hbm_budget_bytes.  Every request carries its own key and seeds and is
+ * computed with the multi-client kernels, so its shares are bit-identical
+ * whether it runs alone or batched with others. */
+typedef struct {
+    uint64_t hbm_budget_bytes;  /* device bytes requests in flight may use     */
+    uint32_t max_batch;         /* requests per launch (>= 1)                  */
+    uint32_t lanes;             /* batches in flight at once (>= 1)            */
+} fdsc_server_config;
+
+typedef struct {
+    uint32_t type;              /* from fdsc_server_add_type                   */
+    uint32_t key;               /* index into the type's key pool              */
+    uint64_t enc_seed, mask_seed;
+    const uint32_t* xA;         /* HOST [Ci][H][W]; valid until the request is done */
+    const uint32_t* xB;         /* HOST [Ci][H][W]                              */
+    uint32_t* yA;               /* HOST [Co][H][W], written when done          */
+    uint32_t* yB;               /* HOST [Co][H][W]                              */
+} fdsc_request;
+
+typedef struct {
+    uint64_t submitted, completed, batches;
+    uint64_t peak_inflight_bytes;
+    double mean_batch;
+    double p50_us, p99_us, mean_us, max_us; /* submit-to-completion latency   */
+} fdsc_server_stats;
+
+typedef struct fdsc_server fdsc_server;
+
+int fdsc_server_create(const fdsc_server_config* cfg, fdsc_server** out);
+/* Registers a layer type (B is ignored; fused shapes only: H W <= S,
+ * 8 <= H, W): prepares its filter plaintexts from device weights w and keeps
+ * a pointer to its key pool (device [nkeys][n]). */
+int fdsc_server_add_type(fdsc_server* s, const fdsc_params* P, const fdsc_layer* L, const int8_t* w, uint32_t fh,
+                         uint32_t fw, const uint64_t* keys, uint32_t nkeys, uint32_t* type_id);
+/* Allocates the lanes' buffers and starts the scheduling thread. */
+int fdsc_server_start(fdsc_server* s);
+/* Queues a request (thread-safe); FDSC_ERR_BUDGET if it can never fit. */
+int fdsc_server_submit(fdsc_server* s, const fdsc_request* r, uint64_t* ticket);
+/* Waits at most timeout_ms for a ticket; FDSC_ERR_TIMEOUT if not done. */
+int fdsc_server_wait(fdsc_server* s, uint64_t ticket, uint32_t timeout_ms, double* latency_us);
+int fdsc_server_stats_get(fdsc_server* s, fdsc_server_stats* out);
+/* Stops the thread after the batches in flight finish and frees everything. */
+int fdsc_server_destroy(fdsc_server* s);
 
 /* ---------------------------------------------------------------------- */
 /* Tuning                                                                  */

@@ -104,7 +104,7 @@ extern "C" int fdsc_mask_prepare(const fdsc_params* P, const fdsc_layer* L, uint
     DevLayer D;
     if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
     if ((rc = check_ptr(M_hat, "M_hat")) || (rc = check_ptr(sB_hat, "sB_hat"))) return rc;
-    return launched(launch_mask_prepare(P->dev, D, seed, M_hat, sB_hat, (cudaStream_t)stream), "mask_prepare");
+    return launched(launch_mask_prepare(P->dev, D, seed, nullptr, M_hat, sB_hat, (cudaStream_t)stream), "mask_prepare");
 }
 
 extern "C" int fdsc_homconv(const fdsc_params* P, const fdsc_layer* L, const uint64_t* ct_in, const uint64_t* P_hat,
@@ -165,7 +165,7 @@ extern "C" int fdsc_encrypt_constants(const fdsc_params* P, const fdsc_layer* L,
     DevLayer D;
     if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
     if ((rc = check_ptr(t_hat, "t_hat")) || (rc = check_ptr(ct, "ct"))) return rc;
-    return launched(launch_constants(P->dev, D, t_hat, seed, ct, (cudaStream_t)stream), "encrypt_constants");
+    return launched(launch_constants(P->dev, D, t_hat, 0, seed, nullptr, ct, (cudaStream_t)stream), "encrypt_constants");
 }
 
 extern "C" int fdsc_encode_share(const fdsc_params* P, const fdsc_layer* L, const uint32_t* x, uint64_t* A,
@@ -222,5 +222,45 @@ extern "C" int fdsc_decrypt_share(const fdsc_params* P, const fdsc_layer* L, con
     if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
     if ((rc = check_fused(P, D, decrypt_share_smem_bytes(P->dev, D), "decrypt_share"))) return rc;
     if ((rc = check_ptr(t_hat, "t_hat")) || (rc = check_ptr(ct, "ct")) || (rc = check_ptr(y, "y"))) return rc;
-    return launched(launch_decrypt_share(P->dev, D, t_hat, ct, y, (cudaStream_t)stream), "decrypt_share");
+    return launched(launch_decrypt_share(P->dev, D, t_hat, 0, ct, y, (cudaStream_t)stream), "decrypt_share");
+}
+
+// ---------------------------------------------------------------- several clients in one call
+extern "C" int fdsc_encrypt_constants_multi(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hats,
+                                            uint64_t key_stride, const uint64_t* seeds, uint64_t* ct, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_ptr(t_hats, "t_hats")) || (rc = check_ptr(seeds, "seeds", false)) || (rc = check_ptr(ct, "ct")))
+        return rc;
+    if (key_stride % 2) return fdsc_set_error(FDSC_ERR_ARG, "key_stride must keep keys 16-byte aligned");
+    return launched(launch_constants(P->dev, D, t_hats, key_stride, 0, seeds, ct, (cudaStream_t)stream),
+                    "encrypt_constants_multi");
+}
+
+extern "C" int fdsc_mask_prepare_multi(const fdsc_params* P, const fdsc_layer* L, const uint64_t* seeds,
+                                       uint64_t* M_hat, uint32_t* sB_hat, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_ptr(seeds, "seeds", false)) || (rc = check_ptr(M_hat, "M_hat")) ||
+        (rc = check_ptr(sB_hat, "sB_hat")))
+        return rc;
+    return launched(launch_mask_prepare(P->dev, D, 0, seeds, M_hat, sB_hat, (cudaStream_t)stream),
+                    "mask_prepare_multi");
+}
+
+extern "C" int fdsc_decrypt_share_multi(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hats,
+                                        uint64_t key_stride, const uint64_t* ct, uint32_t* y, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_fused(P, D, decrypt_share_smem_bytes(P->dev, D), "decrypt_share_multi"))) return rc;
+    if ((rc = check_ptr(t_hats, "t_hats")) || (rc = check_ptr(ct, "ct")) || (rc = check_ptr(y, "y"))) return rc;
+    if (key_stride % 2) return fdsc_set_error(FDSC_ERR_ARG, "key_stride must keep keys 16-byte aligned");
+    return launched(launch_decrypt_share(P->dev, D, t_hats, key_stride, ct, y, (cudaStream_t)stream),
+                    "decrypt_share_multi");
 }

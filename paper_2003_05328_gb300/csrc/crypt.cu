@@ -175,13 +175,19 @@ __device__ __forceinline__ u32 mask_value(const DevParams& P, const DevLayer& L,
     return v;
 }
 
-__global__ void __launch_bounds__(kMaxThreads) mask_kernel(DevParams P, DevLayer L, u64 seed, u64* __restrict__ Mhat,
+// seeds == nullptr: one seed for the call, randomness indexed by the global
+// image number.  Otherwise image group bb draws from seeds[bb] with images
+// numbered from 0 inside the group, exactly as if it were a call of its own.
+__global__ void __launch_bounds__(kMaxThreads) mask_kernel(DevParams P, DevLayer L, u64 seed,
+                                                        const u64* __restrict__ seeds, u64* __restrict__ Mhat,
                                                         u32* __restrict__ sB) {
     extern __shared__ u64 smem[];
     u64* c = smem;
     u32* slots = reinterpret_cast<u32*>(smem + P.n);
     const u32 v = blockIdx.x;
     const u32 h = v % L.beta, co = (v / L.beta) % L.Co, bb = v / (L.beta * L.Co);
+    const u32 b_off = seeds ? bb * P.d * L.g_b : 0;  // first image of the group, for indexing randomness
+    if (seeds) seed = seeds[bb];
     const u64 kMask = stream_key(seed, DOM_MASK), kSplit = stream_key(seed, DOM_MASK_SPLIT);
     for (u32 sg = threadIdx.x; sg < P.n; sg += blockDim.x) {
         const u32 r = sg >> P.logS, s = sg & (P.S - 1);
@@ -192,16 +198,17 @@ __global__ void __launch_bounds__(kMaxThreads) mask_kernel(DevParams P, DevLayer
                 const u32 ic = blk % L.g_c, f = s & (L.HW - 1);
                 const u32 b = (bb * P.d + r) * L.g_b + blk / L.g_c;
                 if (b < L.B) {
-                    val = mask_value(P, L, kMask, kSplit, b, co, ic, f);
+                    const u32 br = b - b_off;
+                    val = mask_value(P, L, kMask, kSplit, br, co, ic, f);
                     if (ic == 0)
                         sB[((u64)b * L.Co + co) * L.HW + f] =
-                            uniform_p(stream_at(kMask, ((u64)b * L.Co + co) * L.HW + f), P.p);
+                            uniform_p(stream_at(kMask, ((u64)br * L.Co + co) * L.HW + f), P.p);
                 }
             }
         } else {
             const u32 b = bb * P.d + r, f = h * P.S + s;
             if (b < L.B) {
-                val = uniform_p(stream_at(kMask, ((u64)b * L.Co + co) * L.HW + f), P.p);
+                val = uniform_p(stream_at(kMask, ((u64)(b - b_off) * L.Co + co) * L.HW + f), P.p);
                 sB[((u64)b * L.Co + co) * L.HW + f] = val;
             }
         }
@@ -325,12 +332,12 @@ cudaError_t launch_filter_prepare(const DevParams& P, const DevLayer& L, const i
     return cudaGetLastError();
 }
 
-cudaError_t launch_mask_prepare(const DevParams& P, const DevLayer& L, u64 seed, u64* Mhat, u32* sB,
+cudaError_t launch_mask_prepare(const DevParams& P, const DevLayer& L, u64 seed, const u64* seeds, u64* Mhat, u32* sB,
                                 cudaStream_t s) {
     const size_t sm = (size_t)P.n * 12;
     cudaError_t e = set_smem(mask_kernel, sm);
     if (e != cudaSuccess) return e;
-    mask_kernel<<<L.n_out, threads_for(P.n), sm, s>>>(P, L, seed, Mhat, sB);
+    mask_kernel<<<L.n_out, threads_for(P.n), sm, s>>>(P, L, seed, seeds, Mhat, sB);
     return cudaGetLastError();
 }
 

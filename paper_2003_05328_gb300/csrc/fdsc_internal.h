@@ -75,16 +75,19 @@ cudaError_t launch_encrypt(const DevParams& P, const DevLayer& L, const u64* t_h
 cudaError_t launch_homrec(const DevParams& P, const DevLayer& L, const u32* XB, u64* ct, cudaStream_t s);
 cudaError_t launch_filter_prepare(const DevParams& P, const DevLayer& L, const int8_t* w, u32 fh, u32 fw,
                                   u64* Phat, cudaStream_t s);
-cudaError_t launch_mask_prepare(const DevParams& P, const DevLayer& L, u64 seed, u64* Mhat, u32* sB,
+cudaError_t launch_mask_prepare(const DevParams& P, const DevLayer& L, u64 seed, const u64* seeds, u64* Mhat, u32* sB,
                                 cudaStream_t s);
 cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
                            const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s);
-cudaError_t launch_constants(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 seed, u64* ct,
-                             cudaStream_t s);
+cudaError_t launch_homconv_v(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                             const u64* Phat, const u64* Mhat, u64* ct_out, int variant, cudaStream_t s);
+int homconv_default_variant(const DevLayer& L);
+cudaError_t launch_constants(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, u64 seed,
+                             const u64* seeds, u64* ct, cudaStream_t s);
 cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u64* out, bool add_to_ct,
                          cudaStream_t s);
-cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u64* t_hat, const u64* ct, u32* y,
-                                 cudaStream_t s);
+cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, const u64* ct,
+                                 u32* y, cudaStream_t s);
 size_t share_smem_bytes(const DevParams& P, const DevLayer& L);
 size_t decrypt_share_smem_bytes(const DevParams& P, const DevLayer& L);
 cudaError_t launch_decrypt(const DevParams& P, const DevLayer& L, const u64* t_hat, const u64* ct, u32* SA,

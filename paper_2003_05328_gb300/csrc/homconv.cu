@@ -378,10 +378,11 @@ cudaError_t launch_adds(const DevParams& P, const DevLayer& L, const u64* ct_in,
     return launch_variant<NB, W, 2>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
 }
 
-cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
-                           const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
-    int v = g_homconv_variant;
-    if (v == 0) v = 3;
+int homconv_default_variant(const DevLayer& L) { return L.T <= 256 ? 4 : 3; }
+
+cudaError_t launch_homconv_v(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                             const u64* Phat, const u64* Mhat, u64* ct_out, int v, cudaStream_t s) {
+    if (v <= 0 || v > 5) v = homconv_default_variant(L);
     // the staged tile must fit in shared memory (T <= 256 words x 2 x 32 lanes)
     if ((v == 4 || v == 5) && L.T > 256) v = 3;
     switch (v) {
@@ -391,4 +392,9 @@ cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_
         case 2: return launch_adds<2, true>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
         default: return launch_adds<1, false>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
     }
+}
+
+cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                           const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
+    return launch_homconv_v(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, g_homconv_variant, s);
 }

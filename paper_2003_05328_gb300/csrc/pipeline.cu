@@ -26,7 +26,11 @@ constexpr u32 kMaxThreads = 512;
 inline u32 threads_for(u32 n) { return n / 8 < 32 ? 32 : n / 8; }
 
 // ---------------------------------------------------------------- encryption constants
-__global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, const u64* __restrict__ t_hat, u64 seed,
+// Image group g = u / per_group uses the key t_hat + g key_stride; with
+// seeds != nullptr it draws from seeds[g] with ciphertexts numbered from 0
+// inside the group (as if it were a call of its own).
+__global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, const u64* __restrict__ t_hat, u64 key_stride,
+                                                                u32 per_group, u64 seed, const u64* __restrict__ seeds,
                                                                 u64* __restrict__ ct) {
     extern __shared__ __align__(16) unsigned char sm[];
     const u32 n = P.n;
@@ -36,10 +40,13 @@ __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, con
     stage_async(tq, P.qfw2, n * 16);
     if (threadIdx.x < 19) cdt[threadIdx.x] = P.cdt[threadIdx.x];
     __syncthreads();
-    const u32 u = blockIdx.x;
+    const u32 u = blockIdx.x, grp = u / per_group;
+    t_hat += (u64)grp * key_stride;
+    const u32 ur = seeds ? u - grp * per_group : u;  // ciphertext number for the randomness
+    if (seeds) seed = seeds[grp];
     const u64 keyE = stream_key(seed, DOM_E);
     for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
-        const int e = gauss_sample(stream_at(keyE, (u64)u * n + i), cdt);
+        const int e = gauss_sample(stream_at(keyE, (u64)ur * n + i), cdt);
         c[padx(i)] = e >= 0 ? (u64)e : P.q - (u64)(-e);
     }
     stage_wait();
@@ -48,7 +55,7 @@ __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, con
     u64* c0 = ct + (u64)u * 2 * n;
     u64* c1 = c0 + n;
     for (u32 j = threadIdx.x; j < n; j += blockDim.x) {
-        const u64 idx = 2 * ((u64)u * n + j);
+        const u64 idx = 2 * ((u64)ur * n + j);
         const u64 a = uniform_q(stream_at(keyA, idx), stream_at(keyA, idx + 1), P.q);
         c0[j] = a ? P.q - a : 0;
         c1[j] = addmod_q(mulmod_q(a, __ldg(t_hat + j), P), c[padx(j)], P.q);
@@ -121,8 +128,8 @@ __device__ __forceinline__ u32 round_pq2(u64 v, const DevParams& P) {
 }
 
 __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
-                                                                    const u64* __restrict__ ct, u32* __restrict__ y,
-                                                                    u32 scale, u32 scale_s) {
+                                                                    u64 key_stride, const u64* __restrict__ ct,
+                                                                    u32* __restrict__ y, u32 scale, u32 scale_s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const u32 n = P.n, S = P.S;
     const u32 np = padded_len(n);
@@ -141,6 +148,7 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
     load_pairs_for_length(tw_col, L.logH, true, P);
 
     const u32 v = blockIdx.x, co = v % L.Co, bb = v / L.Co;
+    t_hat += (u64)bb * key_stride;
     const u64* c0 = ct + (u64)v * 2 * n;
     const u64* c1 = c0 + n;
     for (u32 j = threadIdx.x; j < n; j += blockDim.x)
@@ -193,12 +201,12 @@ size_t decrypt_share_smem_bytes(const DevParams& P, const DevLayer& L) {
 }
 size_t constants_smem_bytes(const DevParams& P) { return (size_t)P.n * 16 + (size_t)padded_len(P.n) * 8; }
 
-cudaError_t launch_constants(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 seed, u64* ct,
-                             cudaStream_t s) {
+cudaError_t launch_constants(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, u64 seed,
+                             const u64* seeds, u64* ct, cudaStream_t s) {
     const size_t sm = constants_smem_bytes(P);
     cudaError_t e = opt_in(constants_kernel, sm);
     if (e != cudaSuccess) return e;
-    constants_kernel<<<L.n_in, threads_for(P.n), sm, s>>>(P, t_hat, seed, ct);
+    constants_kernel<<<L.n_in, threads_for(P.n), sm, s>>>(P, t_hat, key_stride, L.T * L.beta, seed, seeds, ct);
     return cudaGetLastError();
 }
 
@@ -212,12 +220,13 @@ cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u6
     return cudaGetLastError();
 }
 
-cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u64* t_hat, const u64* ct, u32* y,
-                                 cudaStream_t s) {
+cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, const u64* ct,
+                                 u32* y, cudaStream_t s) {
     const size_t sm = decrypt_share_smem_bytes(P, L);
     cudaError_t e = opt_in(decrypt_share_kernel, sm);
     if (e != cudaSuccess) return e;
     const u32 scale = fdsc_powmod32(L.HW % P.p, P.p - 2, P.p);
-    decrypt_share_kernel<<<L.n_out, threads_for(P.n), sm, s>>>(P, L, t_hat, ct, y, scale, fdsc_shoup32(scale, P.p));
+    decrypt_share_kernel<<<L.n_out, threads_for(P.n), sm, s>>>(P, L, t_hat, key_stride, ct, y, scale,
+                                                                fdsc_shoup32(scale, P.p));
     return cudaGetLastError();
 }

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_PKG, "libfdsc.so")
 
 FDSC_OK = 0
 ERR_NAMES = {-1: "FDSC_ERR_ARG", -2: "FDSC_ERR_NOISE", -3: "FDSC_ERR_OOM", -4: "FDSC_ERR_CUDA",
-             -5: "FDSC_ERR_UNSUPPORTED"}
+             -5: "FDSC_ERR_UNSUPPORTED", -6: "FDSC_ERR_TIMEOUT", -7: "FDSC_ERR_BUDGET"}
 
 
 class FdscError(RuntimeError):
@@ -75,6 +75,21 @@ _SIGS = {
     "fdsc_homrec_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
     "fdsc_homconv_sum": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fdsc_decrypt_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
+    "fdsc_encrypt_constants_multi": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp, _vp]),
+    "fdsc_mask_prepare_multi": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
+    "fdsc_decrypt_share_multi": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp, _vp]),
+    "fdsc_plan_create": (C.c_int, [_vp, C.c_uint32, C.c_uint32, _vp, C.POINTER(_vp)]),
+    "fdsc_plan_launch": (C.c_int, [_vp, _vp]),
+    "fdsc_plan_layer_info_get": (C.c_int, [_vp, C.c_uint32, _vp]),
+    "fdsc_plan_destroy": (C.c_int, [_vp]),
+    "fdsc_server_create": (C.c_int, [_vp, C.POINTER(_vp)]),
+    "fdsc_server_add_type": (C.c_int, [_vp, _vp, _PL, _vp, C.c_uint32, C.c_uint32, _vp, C.c_uint32,
+                                       C.POINTER(C.c_uint32)]),
+    "fdsc_server_start": (C.c_int, [_vp]),
+    "fdsc_server_submit": (C.c_int, [_vp, _vp, C.POINTER(C.c_uint64)]),
+    "fdsc_server_wait": (C.c_int, [_vp, C.c_uint64, C.c_uint32, C.POINTER(C.c_double)]),
+    "fdsc_server_stats_get": (C.c_int, [_vp, _vp]),
+    "fdsc_server_destroy": (C.c_int, [_vp]),
 }
 # entry points declared in include/fdsc.h (checked against the library's exports by the tests)
 EXPORTS = tuple(_SIGS)
@@ -336,3 +351,165 @@ def decrypt_share(P: Params, L: LayerSpec, t_hat, ct, out=None, stream=None) -> 
           _ptr(ct, torch.int64, lay.ct_out_words, "ct"), _ptr(out, torch.int32, lay.out_spectra_words, "y"),
           _stream(stream))
     return out
+
+
+# ---------------------------------------------------------------- several clients in one call
+def encrypt_constants_multi(P: Params, L: LayerSpec, t_hats, seeds, key_stride=None, out=None, stream=None):
+    """Enc(0) with a key and a seed per image group (t_hats [GB][n] or one key, seeds int64 [GB] on the device)."""
+    lay = layout(P, L)
+    if key_stride is None:
+        key_stride = P.n if t_hats.numel() > P.n else 0
+    if out is None:
+        out = torch.empty(lay.ct_in_words, dtype=torch.int64, device="cuda")
+    _call("fdsc_encrypt_constants_multi", P.handle, C.byref(L.c()), _ptr(t_hats, torch.int64, t_hats.numel(), "t_hats"),
+          key_stride, _ptr(seeds, torch.int64, lay.GB, "seeds"), _ptr(out, torch.int64, lay.ct_in_words, "ct"),
+          _stream(stream))
+    return out
+
+
+def mask_prepare_multi(P: Params, L: LayerSpec, seeds, M_hat=None, sB_hat=None, stream=None):
+    lay = layout(P, L)
+    if M_hat is None:
+        M_hat = torch.empty(lay.mask_words, dtype=torch.int64, device="cuda")
+    if sB_hat is None:
+        sB_hat = torch.empty(lay.out_spectra_words, dtype=torch.int32, device="cuda")
+    _call("fdsc_mask_prepare_multi", P.handle, C.byref(L.c()), _ptr(seeds, torch.int64, lay.GB, "seeds"),
+          _ptr(M_hat, torch.int64, lay.mask_words, "M_hat"), _ptr(sB_hat, torch.int32, lay.out_spectra_words, "sB_hat"),
+          _stream(stream))
+    return M_hat, sB_hat
+
+
+def decrypt_share_multi(P: Params, L: LayerSpec, t_hats, ct, key_stride=None, out=None, stream=None):
+    lay = layout(P, L)
+    if key_stride is None:
+        key_stride = P.n if t_hats.numel() > P.n else 0
+    if out is None:
+        out = torch.empty((L.B, L.Co, L.H, L.W), dtype=torch.int32, device="cuda")
+    _call("fdsc_decrypt_share_multi", P.handle, C.byref(L.c()), _ptr(t_hats, torch.int64, t_hats.numel(), "t_hats"),
+          key_stride, _ptr(ct, torch.int64, lay.ct_out_words, "ct"), _ptr(out, torch.int32, lay.out_spectra_words, "y"),
+          _stream(stream))
+    return out
+
+
+# ---------------------------------------------------------------- batched plan
+class PlanLayerC(C.Structure):
+    _fields_ = [("params", _vp), ("layer", Layer), ("fh", C.c_uint32), ("fw", C.c_uint32), ("w", _vp),
+                ("t_hat", _vp), ("enc_seed", C.c_uint64), ("mask_seed", C.c_uint64), ("xA", _vp), ("xB", _vp),
+                ("yA", _vp), ("yB", _vp)]
+
+
+class PlanLayerInfo(C.Structure):
+    _fields_ = [(k, C.c_uint32) for k in ("g_c", "g_b", "homconv_variant", "fused", "candidates", "pad0")] + \
+               [("tuned_step_us", C.c_double)]
+
+
+PLAN_TUNE = 1
+
+
+class Plan:
+    """Many layers' online paths recorded as one CUDA graph (setup at creation).
+
+    ``layers``: dicts with keys params, layer (LayerSpec; g_c = 0 lets the plan
+    choose), w (int8 [Co][Ci][fh][fw]), t_hat, enc_seed, mask_seed, xA, xB, yA,
+    yB (device tensors)."""
+
+    def __init__(self, layers, tune=False, stream=None):
+        arr = (PlanLayerC * len(layers))()
+        self._keep = layers
+        for i, d in enumerate(layers):
+            L, w = d["layer"], d["w"]
+            Co, Ci, fh, fw = w.shape
+            arr[i] = PlanLayerC(d["params"].handle, L.c(), fh, fw, _ptr(w, torch.int8, w.numel(), "w"),
+                                _ptr(d["t_hat"], torch.int64, d["params"].n, "t_hat"), d["enc_seed"], d["mask_seed"],
+                                d["xA"].data_ptr(), d["xB"].data_ptr(), d["yA"].data_ptr(), d["yB"].data_ptr())
+        h = _vp()
+        _call("fdsc_plan_create", C.addressof(arr), len(layers), PLAN_TUNE if tune else 0, _stream(stream),
+              C.byref(h))
+        self.handle = h
+
+    def launch(self, stream=None):
+        _call("fdsc_plan_launch", self.handle, _stream(stream))
+
+    def info(self, i) -> PlanLayerInfo:
+        out = PlanLayerInfo()
+        _call("fdsc_plan_layer_info_get", self.handle, i, C.byref(out))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().fdsc_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- serving
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("max_batch", C.c_uint32), ("lanes", C.c_uint32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("type", C.c_uint32), ("key", C.c_uint32), ("enc_seed", C.c_uint64), ("mask_seed", C.c_uint64),
+                ("xA", _vp), ("xB", _vp), ("yA", _vp), ("yB", _vp)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in ("submitted", "completed", "batches", "peak_inflight_bytes")] + \
+               [(k, C.c_double) for k in ("mean_batch", "p50_us", "p99_us", "mean_us", "max_us")]
+
+
+class Server:
+    """Continuous-batching server (a scheduling thread inside libfdsc).
+    Request buffers are host numpy arrays (uint32) kept alive by the caller
+    until the request is done."""
+
+    def __init__(self, hbm_budget_bytes, max_batch=16, lanes=4):
+        cfg = ServerConfig(hbm_budget_bytes, max_batch, lanes)
+        h = _vp()
+        _call("fdsc_server_create", C.byref(cfg), C.byref(h))
+        self.handle = h
+        self._keep = []
+
+    def add_type(self, P: Params, L: LayerSpec, w, keys) -> int:
+        Co, Ci, fh, fw = w.shape
+        tid = C.c_uint32()
+        nkeys = keys.numel() // P.n
+        self._keep += [w, keys]
+        _call("fdsc_server_add_type", self.handle, P.handle, C.byref(L.c()), _ptr(w, torch.int8, w.numel(), "w"), fh,
+              fw, _ptr(keys, torch.int64, keys.numel(), "keys"), nkeys, C.byref(tid))
+        return tid.value
+
+    def start(self):
+        _call("fdsc_server_start", self.handle)
+
+    def submit(self, type_id, key, enc_seed, mask_seed, xA, xB, yA, yB) -> int:
+        r = Request(type_id, key, enc_seed, mask_seed, xA.ctypes.data, xB.ctypes.data, yA.ctypes.data,
+                    yB.ctypes.data)
+        t = C.c_uint64()
+        _call("fdsc_server_submit", self.handle, C.byref(r), C.byref(t))
+        return t.value
+
+    def wait(self, ticket, timeout_ms=60000) -> float:
+        lat = C.c_double()
+        _call("fdsc_server_wait", self.handle, ticket, timeout_ms, C.byref(lat))
+        return lat.value
+
+    def stats(self) -> ServerStats:
+        out = ServerStats()
+        _call("fdsc_server_stats_get", self.handle, C.byref(out))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().fdsc_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

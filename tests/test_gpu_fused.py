@@ -99,3 +99,43 @@ def test_fused_path_rejects_unsupported_shapes(F):
         F.encode_share(P, L2, torch.zeros(2 * 4 * 64, dtype=torch.int32, device="cuda"))
     assert e.value.code == -5
     P.close()
+
+
+def test_multi_client_batch_equals_single_requests(F):
+    """Three clients (own key, encryption seed and HomShare seed) in one
+    launch: every client's ciphertexts and shares are the words of the oracle
+    run on that client alone."""
+    n, p, Ci, Co, H, W, G = 2048, 65537, 64, 8, 32, 32, 3
+    OP = O.params(n, p)
+    OL1 = O.layer(OP, 1, Ci, Co, H, W, 2, 1)
+    P = F.Params(n, p, max_T=OL1.T)
+    LB = F.LayerSpec(G, Ci, Co, H, W, 2, 1)
+    g = np.random.default_rng(99)
+    xA = g.integers(0, p, (G, Ci, H, W)).astype(np.uint32)
+    xB = g.integers(0, p, (G, Ci, H, W)).astype(np.uint32)
+    w = g.integers(-8, 8, (Co, Ci, 3, 3)).astype(np.int8)
+    ks = [11, 12, 13]
+    es = [int(v) for v in g.integers(0, 2**62, G)]
+    ss = [int(v) for v in g.integers(0, 2**62, G)]
+    t_hats = torch.stack([F.keygen(P, k) for k in ks]).reshape(-1)
+    seeds_e = torch.tensor(es, dtype=torch.int64, device="cuda")
+    seeds_s = torch.tensor(ss, dtype=torch.int64, device="cuda")
+    Phat = F.filter_prepare(P, LB, dev(w, np.int8))
+    C0 = F.encrypt_constants_multi(P, LB, t_hats, seeds_e)
+    M, sB = F.mask_prepare_multi(P, LB, seeds_s)
+    A = F.encode_share(P, LB, dev(xA, np.int32))
+    R = F.encode_share(P, LB, dev(xB, np.int32))
+    out = F.homconv_sum(P, LB, C0, A, R, Phat, M)
+    yA = F.decrypt_share_multi(P, LB, t_hats, out)
+    yB = F.intt2d(P, sB.view(G, Co, H, W))
+    yA_n, yB_n = u32(yA).reshape(G, Co, H, W), u32(yB).reshape(G, Co, H, W)
+    C0_n = u64(C0).reshape(G, OL1.n_in, 2, n)
+    for i in range(G):
+        ref = O.round_trip(OP, OL1, xA[i:i + 1], xB[i:i + 1], w, ks[i], es[i], ss[i])
+        zero = np.zeros((1, Ci, H * W), np.uint32)
+        assert np.array_equal(C0_n[i], O.encrypt(OP, OL1, ref["t_hat"], zero, es[i])), i
+        assert np.array_equal(yA_n[i], ref["yA"][0]), i
+        assert np.array_equal(yB_n[i], ref["yB"][0]), i
+        y = O.conv_plain(p, (xA[i:i + 1].astype(np.int64) + xB[i:i + 1]) % p, w)[0]
+        assert np.array_equal((yA_n[i].astype(np.int64) + yB_n[i]) % p, y)
+    P.close()

@@ -1,0 +1,157 @@
+"""GPU tests of the batching runtime: a plan of several uneven layers in one
+graph launch (fused and step-by-step layers, default and autotuned packing)
+and the continuous-batching server.  Results are compared word for word with
+the oracle; the final shares do not depend on the packing, so the oracle runs
+with its default packing."""
+import numpy as np
+import pytest
+import torch
+
+from fdsc_harness import dev, u32
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_05328_gb300 import build
+
+    build.build()
+    from paper_2003_05328_gb300 import fdsc
+
+    torch.cuda.set_device(0)
+    return fdsc
+
+
+LAYERS = [  # (n, p, B, Ci, Co, H, W, fh)
+    (2048, 65537, 2, 64, 16, 32, 32, 3),
+    (2048, 65537, 2, 128, 8, 16, 16, 3),
+    (4096, 65537, 2, 256, 4, 8, 8, 3),
+    (4096, 12289, 2, 3, 2, 64, 64, 3),   # spectra span two ciphertexts: step-by-step path
+    (1024, 65537, 3, 4, 4, 16, 16, 5),
+]
+
+
+def _make_layers(F, seed):
+    g = np.random.default_rng(seed)
+    specs, refs, params = [], [], []
+    for i, (n, p, B, Ci, Co, H, W, fh) in enumerate(LAYERS):
+        P = F.Params(n, p, max_T=256)
+        params.append(P)
+        xA = g.integers(0, p, (B, Ci, H, W)).astype(np.uint32)
+        xB = g.integers(0, p, (B, Ci, H, W)).astype(np.uint32)
+        w = g.integers(-8, 8, (Co, Ci, fh, fh)).astype(np.int8)
+        ks, es, ss = 100 + i, 200 + i, 300 + i
+        specs.append(dict(params=P, layer=F.LayerSpec(B, Ci, Co, H, W, 0, 0), w=dev(w, np.int8),
+                          t_hat=F.keygen(P, ks), enc_seed=es, mask_seed=ss, xA=dev(xA, np.int32),
+                          xB=dev(xB, np.int32),
+                          yA=torch.empty((B, Co, H, W), dtype=torch.int32, device="cuda"),
+                          yB=torch.empty((B, Co, H, W), dtype=torch.int32, device="cuda")))
+        OP = O.params(n, p)
+        refs.append(O.round_trip(OP, O.layer(OP, B, Ci, Co, H, W), xA, xB, w, ks, es, ss))
+    return specs, refs, params
+
+
+@pytest.mark.parametrize("tune", [False, True])
+def test_plan_of_uneven_layers_matches_oracle(F, tune):
+    specs, refs, params = _make_layers(F, 5 + tune)
+    plan = F.Plan(specs, tune=tune)
+    for rep in range(2):
+        for d in specs:
+            d["yA"].zero_()
+            d["yB"].zero_()
+        plan.launch()
+        torch.cuda.synchronize()
+        for i, (d, ref) in enumerate(zip(specs, refs)):
+            assert np.array_equal(u32(d["yA"]).reshape(ref["yA"].shape), ref["yA"]), (i, rep)
+            assert np.array_equal(u32(d["yB"]).reshape(ref["yB"].shape), ref["yB"]), (i, rep)
+    infos = [plan.info(i) for i in range(len(LAYERS))]
+    assert [x.fused for x in infos] == [1, 1, 1, 0, 1]
+    if tune:
+        assert all(x.candidates > 0 for x, f in zip(infos, [1, 1, 1, 0, 1]) if f)
+    plan.close()
+    for P in params:
+        P.close()
+
+
+def _server_case(F, g, S, types, pools, OPs):
+    t = int(g.integers(len(types)))
+    (n, p, Ci, Co, H, W, fh), w = types[t]
+    key = int(g.integers(4))
+    xA = g.integers(0, p, (Ci, H, W)).astype(np.uint32)
+    xB = g.integers(0, p, (Ci, H, W)).astype(np.uint32)
+    es, ss = int(g.integers(2**62)), int(g.integers(2**62))
+    return dict(t=t, key=key, xA=xA, xB=xB, es=es, ss=ss, yA=np.zeros((Co, H, W), np.uint32),
+                yB=np.zeros((Co, H, W), np.uint32))
+
+
+def test_server_results_same_alone_and_in_the_mix(F):
+    g = np.random.default_rng(17)
+    types_def = [(2048, 65537, 64, 8, 32, 32, 3), (2048, 65537, 8, 4, 16, 16, 3), (2048, 65537, 1, 4, 32, 32, 5)]
+    P = F.Params(2048, 65537, max_T=64)
+    OP = O.params(2048, 65537)
+    key_seeds = [7, 8, 9, 10]
+    keys = torch.stack([F.keygen(P, k) for k in key_seeds]).reshape(-1)
+    types = []
+    for (n, p, Ci, Co, H, W, fh) in types_def:
+        w = g.integers(-8, 8, (Co, Ci, fh, fh)).astype(np.int8)
+        types.append(((n, p, Ci, Co, H, W, fh), w))
+
+    def make_server(max_batch, lanes):
+        S = F.Server(hbm_budget_bytes=8 << 30, max_batch=max_batch, lanes=lanes)
+        ids = [S.add_type(P, F.LayerSpec(1, d[2], d[3], d[4], d[5], 0, 1), dev(w, np.int8), keys)
+               for d, w in types]
+        S.start()
+        return S, ids
+
+    reqs = [_server_case(F, g, None, types, None, None) for _ in range(14)]
+    # all at once: batched and overlapped
+    S, ids = make_server(max_batch=4, lanes=3)
+    tickets = [S.submit(ids[r["t"]], r["key"], r["es"], r["ss"], r["xA"], r["xB"], r["yA"], r["yB"]) for r in reqs]
+    for tk in tickets:
+        assert S.wait(tk) > 0
+    st = S.stats()
+    assert st.completed == len(reqs) and st.batches < len(reqs)  # some batches held several requests
+    assert st.p99_us >= st.p50_us > 0
+    S.close()
+    mixed = [(r["yA"].copy(), r["yB"].copy()) for r in reqs]
+    # one at a time: every request alone
+    S, ids = make_server(max_batch=1, lanes=1)
+    for r, (yA_m, yB_m) in zip(reqs, mixed):
+        r["yA"][:] = 0
+        r["yB"][:] = 0
+        S.wait(S.submit(ids[r["t"]], r["key"], r["es"], r["ss"], r["xA"], r["xB"], r["yA"], r["yB"]))
+        assert np.array_equal(r["yA"], yA_m) and np.array_equal(r["yB"], yB_m)
+    S.close()
+    # and both are the oracle's shares for that request alone
+    for r in reqs[:5]:
+        (n, p, Ci, Co, H, W, fh), w = types[r["t"]]
+        OL = O.layer(OP, 1, Ci, Co, H, W)
+        ref = O.round_trip(OP, OL, r["xA"][None], r["xB"][None], w, key_seeds[r["key"]], r["es"], r["ss"])
+        assert np.array_equal(r["yA"], ref["yA"][0]) and np.array_equal(r["yB"], ref["yB"][0])
+    P.close()
+
+
+def test_server_budget_and_timeouts(F):
+    P = F.Params(2048, 65537, max_T=64)
+    keys = F.keygen(P, 1)
+    w = dev(np.ones((8, 64, 3, 3), np.int8), np.int8)
+    S = F.Server(hbm_budget_bytes=1 << 20, max_batch=4, lanes=2)  # 1 MiB: less than one request needs
+    tid = S.add_type(P, F.LayerSpec(1, 64, 8, 32, 32, 0, 1), w, keys)
+    S.start()
+    x = np.zeros((64, 32, 32), np.uint32)
+    y = np.zeros((8, 32, 32), np.uint32)
+    with pytest.raises(F.FdscError) as e:
+        S.submit(tid, 0, 1, 2, x, x, y, y)
+    assert e.value.code == -7
+    with pytest.raises(F.FdscError) as e:
+        S.wait(12345, timeout_ms=20)  # a ticket nobody submitted
+    assert e.value.code == -6
+    with pytest.raises(F.FdscError) as e:
+        S.submit(tid, 5, 1, 2, x, x, y, y)  # key outside the pool
+    assert e.value.code == -1
+    S.close()
+    P.close()
