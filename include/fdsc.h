@@ -336,6 +336,41 @@ int fdsc_server_stats_get(fdsc_server* s, fdsc_server_stats* out);
 int fdsc_server_destroy(fdsc_server* s);
 
 /* ---------------------------------------------------------------------- */
+/* One layer without any device allocation                                 */
+/* ---------------------------------------------------------------------- */
+/* The paper has no counterpart: this serves callers that cannot let a
+ * library allocate device memory -- applications whose device memory is
+ * entirely reserved by their own pooling allocator, and latency-critical
+ * request threads that must never enter the CUDA allocator (its calls can
+ * block on device-wide synchronisation).
+ *
+ * Runs the fused online path of one layer -- the same kernels as
+ * fdsc_encrypt_constants(t_hat, enc_seed), fdsc_encode_share(xA),
+ * fdsc_encode_share(xB), fdsc_homconv_sum(P_hat, M_hat),
+ * fdsc_decrypt_share(t_hat) -> yA and fdsc_intt2d(sB_hat) -> yB -- and
+ * writes exactly their words, but keeps the intermediate ciphertexts in one
+ * fixed device array of FDSC_NOALLOC_SCRATCH_BYTES compiled into the library
+ * (every device that loads the library holds it until the process exits).  It
+ * calls no allocator.  Inputs and outputs are the caller's device buffers,
+ * with the shapes of those calls (t_hat [n], P_hat [Co][T][n], M_hat
+ * [GB][Co][n], sB_hat, yA, yB [B][Co][H][W], xA, xB [B][Ci][H][W]).
+ *
+ *  - The first call on a device looks up the array's device address (once per
+ *    device); make that first call before any stream capture.
+ *  - Layers whose intermediate ciphertexts need more than the array
+ *    (8 (2 n_in + 2 n_in + 2 n_out) n bytes, each part rounded up to 256)
+ *    are rejected with FDSC_ERR_UNSUPPORTED; so are shapes the fused kernels do
+ *    not take (H W > S, H or W outside [8, 512]).
+ *  - Every call uses the same array and leaves its last contents there; each
+ *    call writes every word before reading it, so nothing needs clearing.
+ *    Calls whose work overlaps on the GPU (other streams, other threads) race
+ *    on the array: serialise them. */
+#define FDSC_NOALLOC_SCRATCH_BYTES (8u << 20)
+int fdsc_layer_online_noalloc(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, uint64_t enc_seed,
+                              const uint64_t* P_hat, const uint64_t* M_hat, const uint32_t* sB_hat, const uint32_t* xA,
+                              const uint32_t* xB, uint32_t* yA, uint32_t* yB, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Tuning                                                                  */
 /* ---------------------------------------------------------------------- */
 /* Selects the HomConv kernel variant for later fdsc_homconv calls in this

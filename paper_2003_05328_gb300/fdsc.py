@@ -90,6 +90,7 @@ _SIGS = {
     "fdsc_server_wait": (C.c_int, [_vp, C.c_uint64, C.c_uint32, C.POINTER(C.c_double)]),
     "fdsc_server_stats_get": (C.c_int, [_vp, _vp]),
     "fdsc_server_destroy": (C.c_int, [_vp]),
+    "fdsc_layer_online_noalloc": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 # entry points declared in include/fdsc.h (checked against the library's exports by the tests)
 EXPORTS = tuple(_SIGS)
@@ -513,3 +514,18 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- one layer, no device allocation
+def layer_online_noalloc(P: Params, L: LayerSpec, t_hat, enc_seed: int, P_hat, M_hat, sB_hat, xA, xB, yA, yB,
+                         stream=None) -> None:
+    """The fused online path of one layer with its intermediate ciphertexts
+    in the library's fixed device array: for callers that must not allocate
+    device memory (the outputs yA, yB are the caller's buffers)."""
+    lay = layout(P, L)
+    _call("fdsc_layer_online_noalloc", P.handle, C.byref(L.c()), _ptr(t_hat, torch.int64, P.n, "t_hat"), enc_seed,
+          _ptr(P_hat, torch.int64, lay.filter_words, "P_hat"), _ptr(M_hat, torch.int64, lay.mask_words, "M_hat"),
+          _ptr(sB_hat, torch.int32, lay.out_spectra_words, "sB_hat"),
+          _ptr(xA, torch.int32, lay.in_spectra_words, "xA"), _ptr(xB, torch.int32, lay.in_spectra_words, "xB"),
+          _ptr(yA, torch.int32, lay.out_spectra_words, "yA"), _ptr(yB, torch.int32, lay.out_spectra_words, "yB"),
+          _stream(stream))
