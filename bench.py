@@ -196,6 +196,177 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+
+# ------------------------------------------------------------------ end to end, batched, served
+def e2e_through_server(F, P, ls, g_c, w_dev, t_hat, xA1, xB1, n_req, window=256):
+    """Single-image requests of the bench layer through the server's C ABI
+    (host buffers in and out), submitted back to back with at most `window`
+    outstanding; whole-job wall time from the first submit to the last
+    completion."""
+    S = F.Server(hbm_budget_bytes=120 * 10**9, max_batch=16, lanes=4)
+    tid = S.add_type(P, F.LayerSpec(1, ls.Ci, ls.Co, ls.H, ls.W, g_c, 1), w_dev, t_hat)
+    S.start()
+    xA1 = np.ascontiguousarray(xA1, dtype=np.uint32)
+    xB1 = np.ascontiguousarray(xB1, dtype=np.uint32)
+    outs = [(np.empty((ls.Co, ls.H, ls.W), np.uint32), np.empty((ls.Co, ls.H, ls.W), np.uint32))
+            for _ in range(window)]
+    for i in range(32):  # warm-up
+        S.wait(S.submit(tid, 0, i, i, xA1, xB1, *outs[i % window]))
+    tickets = [None] * n_req
+    t0 = time.perf_counter()
+    for i in range(n_req):
+        if i >= window:
+            S.wait(tickets[i - window])
+        tickets[i] = S.submit(tid, 0, 1000 + i, 2000 + i, xA1, xB1, *outs[i % window])
+    for i in range(max(0, n_req - window), n_req):
+        S.wait(tickets[i])
+    t1 = time.perf_counter()
+    st = S.stats()
+    S.close()
+    return {"seconds": t1 - t0, "requests": n_req, "h2d": 2 * xA1.nbytes + 16, "d2h": 2 * outs[0][0].nbytes,
+            "p50_us": st.p50_us, "p99_us": st.p99_us, "mean_batch": st.mean_batch}
+
+
+def run_batched(F, flush, sleep_cycles, args):
+    """The uneven stack (16 images through 32x32x64->64, 16x16x128->128 and
+    8x8x256->256) as one autotuned plan (one graph launch) against the plain
+    per-layer path: every (layer, image) pair launched on its own."""
+    import torch
+
+    c = FI.CONFIGS["cfg2"]
+    params, specs, singles = {}, [], []
+    dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
+    for li, ls in enumerate(c.layers):
+        P = params.setdefault((ls.n, ls.p), F.Params(ls.n, ls.p, max_T=256))
+        xA, xB = FI.shares(ls, c.cid, li)
+        w = dev(FI.weights(ls, c.cid, li), np.int8)
+        ks, es, ss = FI.seeds(c.cid, li)
+        t_hat = F.keygen(P, ks)
+        base = dict(params=P, w=w, t_hat=t_hat, enc_seed=es, mask_seed=ss)
+        specs.append(dict(base, layer=F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, 0, 0), xA=dev(xA, np.int32),
+                          xB=dev(xB, np.int32),
+                          yA=torch.empty((ls.B, ls.Co, ls.H, ls.W), dtype=torch.int32, device="cuda"),
+                          yB=torch.empty((ls.B, ls.Co, ls.H, ls.W), dtype=torch.int32, device="cuda")))
+        for b in range(ls.B):
+            singles.append(dict(base, layer=F.LayerSpec(1, ls.Ci, ls.Co, ls.H, ls.W, 0, 0),
+                                xA=dev(xA[b:b + 1], np.int32), xB=dev(xB[b:b + 1], np.int32),
+                                yA=torch.empty((1, ls.Co, ls.H, ls.W), dtype=torch.int32, device="cuda"),
+                                yB=torch.empty((1, ls.Co, ls.H, ls.W), dtype=torch.int32, device="cuda")))
+    t0 = time.perf_counter()
+    plan = F.Plan(specs, tune=True)
+    tune_s = time.perf_counter() - t0
+    per_pair = [F.Plan([d]) for d in singles]
+
+    def timed(fn, reps):
+        for _ in range(3):
+            flush.fill_(1)
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda._sleep(sleep_cycles)
+        for i, (a, b) in enumerate(ev):
+            flush.fill_(i & 0xFF)
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    reps = max(5, min(args.steps // 20, 100))
+    ms_plan = timed(plan.launch, reps)
+    ms_single = timed(lambda: [pp.launch() for pp in per_pair], max(3, reps // 5))
+    units = sum(ls.B for ls in c.layers)
+    info = [plan.info(i) for i in range(len(c.layers))]
+    out = {"workload": "cfg2", "layers": [f"{ls.H}x{ls.W}x{ls.Ci}->{ls.Co}, n={ls.n}" for ls in c.layers],
+           "images": c.layers[0].B, "layers_per_s": units / (np.mean(ms_plan) * 1e-3),
+           "ms_per_launch": float(np.mean(ms_plan)), "per_layer_path_layers_per_s": units / (np.mean(ms_single) * 1e-3),
+           "per_layer_path_ms": float(np.mean(ms_single)), "speedup_vs_per_layer": float(np.mean(ms_single) / np.mean(ms_plan)),
+           "tuning_s": tune_s,
+           "tuned": [{"g_c": x.g_c, "g_b": x.g_b, "homconv_variant": x.homconv_variant, "candidates": x.candidates,
+                      "step_us": x.tuned_step_us} for x in info],
+           "l2": "flushed before every timed launch", "launches": "1 graph (plan) vs %d graphs" % len(per_pair)}
+    plan.close()
+    for pp in per_pair:
+        pp.close()
+    for P in params.values():
+        P.close()
+    return out
+
+
+def run_serving(F, args):
+    """The served mix: Poisson arrivals (mean 2000 requests/s) of single-image
+    requests drawn uniformly from three layer types, each from one of a pool
+    of client keys; continuous batching inside the library's server under a
+    120 GB HBM budget; latency from submit to completion."""
+    import threading
+
+    import torch
+
+    c = FI.CONFIGS["cfg3"]
+    rate = c.extra["rate_per_s"]
+    n_req = args.serve_requests
+    P = F.Params(2048, 65537, max_T=64)
+    t0 = time.perf_counter()
+    keys = torch.stack([F.keygen(P, 5000 + k) for k in range(args.serve_keys)]).reshape(-1)
+    torch.cuda.synchronize()
+    keygen_us = (time.perf_counter() - t0) / args.serve_keys * 1e6
+    S = F.Server(hbm_budget_bytes=c.extra["hbm_budget_bytes"], max_batch=16, lanes=4)
+    dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
+    types, pools = [], []
+    for ti, ls in enumerate(c.layers):
+        g_c, g_b = FI.default_pack(ls, P.info.S)
+        tid = S.add_type(P, F.LayerSpec(1, ls.Ci, ls.Co, ls.H, ls.W, g_c, 1), dev(FI.weights(ls, c.cid, ti), np.int8),
+                         keys)
+        xA, xB = FI.shares(ls, c.cid, ti)  # batch 1: reuse as a pool by rolling the plane
+        ins = [(np.ascontiguousarray(np.roll(xA[0], k, axis=-1)), np.ascontiguousarray(np.roll(xB[0], k, axis=-1)))
+               for k in range(16)]
+        outs = [(np.empty((ls.Co, ls.H, ls.W), np.uint32), np.empty((ls.Co, ls.H, ls.W), np.uint32))
+                for _ in range(512)]
+        types.append(tid)
+        pools.append((ins, outs))
+    S.start()
+    g = np.random.default_rng(FI.SEED_BASE + c.cid)
+    kinds = g.integers(0, len(types), n_req)
+    keyidx = g.integers(0, args.serve_keys, n_req)
+    arrivals = np.cumsum(g.exponential(1.0 / rate, n_req))
+    tickets = [None] * n_req
+    slot_owner = {}
+    progress = [0]  # requests known complete, in submission order
+
+    def waiter():
+        for i in range(n_req):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            S.wait(tickets[i])
+            progress[0] = i + 1
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    start = time.perf_counter()
+    for i in range(n_req):
+        while time.perf_counter() - start < arrivals[i]:
+            pass
+        t = int(kinds[i])
+        ins, outs = pools[t]
+        slot = i % len(outs)
+        prev = slot_owner.get((t, slot))
+        while prev is not None and progress[0] <= prev:  # the slot's previous request must be done
+            time.sleep(0.0001)
+        xa, xb = ins[i % len(ins)]
+        tickets[i] = S.submit(types[t], int(keyidx[i]), 7000 + i, 9000 + i, xa, xb, *outs[slot])
+        slot_owner[(t, slot)] = i
+    th.join()
+    wall = time.perf_counter() - start
+    st = S.stats()
+    S.close()
+    P.close()
+    return {"workload": "cfg3", "requests": n_req, "rate_per_s": rate, "completed": int(st.completed),
+            "throughput_req_per_s": st.completed / wall, "p50_us": st.p50_us, "p99_us": st.p99_us,
+            "mean_us": st.mean_us, "max_us": st.max_us, "mean_batch": st.mean_batch, "batches": int(st.batches),
+            "peak_inflight_bytes": int(st.peak_inflight_bytes), "client_keys": args.serve_keys,
+            "keygen_us_per_key": keygen_us, "hbm_budget_bytes": c.extra["hbm_budget_bytes"],
+            "types": ["28x28(pad 32)x1->16 5x5", "32x32x64->64 3x3", "16x16x128->128 3x3"]}
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, local_rank, world):
     import torch
@@ -353,31 +524,14 @@ def run_gpu(args, rank, local_rank, world):
     hc_ms = [a.elapsed_time(b) for a, b in zip(hs, he)]
     clk = clocks.stop()
 
-    # end to end through the public API: pinned host in, host out
-    e2e_steps = max(10, min(args.steps, 500))
-    xA_pin = torch.from_numpy(xA_h.astype(np.int32)).pin_memory()
-    xB_pin = torch.from_numpy(xB_h.astype(np.int32)).pin_memory()
-    yA_pin = torch.empty(yA.shape, dtype=torch.int32).pin_memory()
-    yB_pin = torch.empty(yB.shape, dtype=torch.int32).pin_memory()
-    es_ = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
-    ee_ = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
-    for i in range(e2e_steps):
-        flush.fill_(i & 0xFF)
-        es_[i].record()
-        xA.copy_(xA_pin, non_blocking=True)
-        xB.copy_(xB_pin, non_blocking=True)
-        step()
-        yA_pin.copy_(yA, non_blocking=True)
-        yB_pin.copy_(yB, non_blocking=True)
-        ee_[i].record()
-        ee_[i].synchronize()
-    e2e_ms = [a.elapsed_time(b) for a, b in zip(es_, ee_)]
-    h2d = xA_pin.numel() * 4 + xB_pin.numel() * 4
-    d2h = yA_pin.numel() * 4 + yB_pin.numel() * 4
+    # end to end through the C ABI with HOST buffers: the serving API, closed loop
+    e2e = e2e_through_server(F, P, ls, g_c, dev(w_h, np.int8), t_hat, xA_h[0], xB_h[0], args.e2e_requests)
+    batched = None if args.skip_batched else run_batched(F, flush, sleep_cycles, args)
+    serving = None if args.skip_serving else run_serving(F, args)
 
     local_sec = sum(step_ms) / 1e3
     tot_sec, tot_units = aggregate(local_sec, float(args.steps * ls.B), world)
-    e2e_sec, e2e_units = aggregate(sum(e2e_ms) / 1e3, float(e2e_steps * ls.B), world)
+    e2e_sec, e2e_units = aggregate(e2e["seconds"], float(e2e["requests"]), world)
     if rank != 0:
         return
     value = tot_units / tot_sec
@@ -416,9 +570,13 @@ def run_gpu(args, rank, local_rank, world):
         "roofline": {"kernel": "homconv_kernel (homconv_sum: HomRec addends + HomConv + HomShare)", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src + " (hbm_gbs, burst copy)", "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "alg_bytes_per_launch": alg_bytes, "launch_us": hc_avg * 1e3},
-        "e2e": {"value": e2e_units / e2e_sec, "unit": "layers/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms),
-                "path": "python binding of the C ABI, eager launches on 4 streams, pinned host buffers"},
+        "e2e": {"value": e2e_units / e2e_sec, "unit": "layers/s", "h2d_bytes_per_step": e2e["h2d"],
+                "d2h_bytes_per_step": e2e["d2h"], "requests": e2e["requests"], "p50_us": e2e["p50_us"],
+                "p99_us": e2e["p99_us"], "mean_batch": e2e["mean_batch"],
+                "path": "fdsc_server_submit/wait (C ABI) with host buffers, closed loop of single-image requests; "
+                        "copies in and out inside the timed region; host wall clock"},
+        "batched": batched,
+        "serving": serving,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps + hc_steps,
         "homconv_variant": args.homconv_variant,
         "clocks": clk,
@@ -437,6 +595,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--homconv-variant", type=int, default=0)
+    ap.add_argument("--e2e-requests", type=int, default=2000)
+    ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--serve-keys", type=int, default=64)
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
     args = ap.parse_args()
     rank, local_rank, world = dist_env()
     if world > 1:
