@@ -10,9 +10,11 @@ before timing (the paper's t_setup); the step is the paper's t_online.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 The device number (`value`) replays the step as a CUDA graph with inputs
-resident in HBM; L2 is flushed (a write larger than L2) before every timed
-step, outside its events.  `e2e` runs the same step through the Python
-binding of the C ABI from pinned host buffers, copies in and out included.
+resident in HBM, K steps back to back between CUDA events; the steps rotate
+over independent instances of the layer whose data together exceed 3x L2,
+so no step finds its inputs in L2.  `e2e` runs single-image requests of the same
+layer through the server's C ABI with host buffers, copies in and out
+included.
 `--impl reference` times the CPU oracle (single thread) on a bounded sample.
 Under torchrun every rank runs an independent replica on its own GPU (the
 path has no exchange step) and rank 0 prints one JSON line.
@@ -368,6 +370,55 @@ def run_serving(F, args):
             "types": ["28x28(pad 32)x1->16 5x5", "32x32x64->64 3x3", "16x16x128->128 3x3"]}
 
 # ------------------------------------------------------------------ GPU arm
+def ntt2d_sweep(F, P, ls, back_to_back, args):
+    """Forward NTT2D of B images x Ci planes (H x W, uint32) for a sweep of B:
+    consecutive launches read and write consecutive slices of a 2 x 512 MiB
+    window, so a slice comes round again only after 1 GiB of traffic (no L2
+    reuse).  Algorithmic bytes: 4 B read + 4 B written per element."""
+    import torch
+
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    peak = peaks.get("hbm_gbs") or 6800.0
+    plane = ls.H * ls.W
+    win = (512 << 20) // 4
+    x = torch.randint(0, ls.p, (win,), dtype=torch.int32, device="cuda")
+    X = torch.empty_like(x)
+    pts = []
+    s = torch.cuda.Stream()
+    for B in (1, 4, 16, 64, 256, 1024, 2048):
+        planes = B * ls.Ci
+        elems = planes * plane
+        if elems > win:
+            break
+        nslices = win // elems  # one graph = one launch per slice, in order
+        views = [(x[i * elems:(i + 1) * elems].view(planes, ls.H, ls.W), X[i * elems:(i + 1) * elems].view(planes, ls.H, ls.W))
+                 for i in range(nslices)]
+        gr = torch.cuda.CUDAGraph()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for a, b in views:
+                F.ntt2d(P, a, out=b)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(gr, stream=s):
+                for a, b in views:
+                    F.ntt2d(P, a, out=b)
+        torch.cuda.current_stream().wait_stream(s)
+        reps = max(2, min(64, (4 * 1024) // nslices))
+        gr.replay()
+        ev = back_to_back([gr], reps)
+        torch.cuda.synchronize()
+        us = ev[0].elapsed_time(ev[-1]) * 1e3 / (reps * nslices)
+        gbs = 8 * elems / (us * 1e-6) / 1e9
+        pts.append({"images": B, "planes": planes, "us": us, "GB_per_s": gbs, "frac": gbs / peak,
+                    "launches": reps * nslices})
+        del gr
+    first = next((p["images"] for p in pts if p["frac"] >= 0.6), None)
+    return {"plane": "%dx%d" % (ls.H, ls.W), "planes_per_image": ls.Ci, "peak_GB_per_s": peak,
+            "launch": "fdsc_ntt2d launches over consecutive slices, one CUDA graph per batch size, replayed back to "
+                      "back between CUDA events", "points": pts,
+            "images_at_60pct": first}
+
+
 def run_gpu(args, rank, local_rank, world):
     import torch
 
@@ -385,29 +436,36 @@ def run_gpu(args, rank, local_rank, world):
     P = F.Params(ls.n, ls.p, max_T=64)
     F.set_homconv_variant(args.homconv_variant)
     lay = F.layout(P, L)
-    xA_h, xB_h = FI.shares(ls, c.cid)
-    w_h = FI.weights(ls, c.cid)
-    ks, es, ss = FI.seeds(c.cid)
     dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
+    l2 = torch.cuda.get_device_properties(local_rank).L2_cache_size
 
-    # setup (t_setup): key, filter spectra, HomShare masks
-    t_hat = F.keygen(P, ks)
-    Phat = F.filter_prepare(P, L, dev(w_h, np.int8))
-    Mhat, sB = F.mask_prepare(P, L, ss)
-    xA, xB = dev(xA_h, np.int32), dev(xB_h, np.int32)
-    XA, XB = torch.empty_like(xA), torch.empty_like(xB)
-    ct = torch.empty(lay.ct_in_words, dtype=torch.int64, device="cuda")
-    ct_out = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
-    SA = torch.empty(lay.out_spectra_words, dtype=torch.int32, device="cuda")
-    yA = torch.empty((ls.B, ls.Co, ls.H, ls.W), dtype=torch.int32, device="cuda")
-    yB = torch.empty_like(yA)
-    sB4 = sB.view(ls.B, ls.Co, ls.H, ls.W)
-    A_msg = torch.empty(lay.n_in * ls.n, dtype=torch.int64, device="cuda")
-    A_rec = torch.empty_like(A_msg)
+    # R independent instances of the layer (own weights, masks, shares, key,
+    # ciphertext buffers), rotated step by step: every step's filter spectra
+    # were last read R - 1 steps earlier, with more than 3x L2 of other data
+    # in between, so no step finds its inputs in L2 (no flush needed).
+    inst_bytes = 8 * (lay.filter_words + lay.mask_words + lay.ct_in_words + 2 * lay.n_in * ls.n + lay.ct_out_words)
+    R = int(min(32, max(4, -(-3 * l2 // inst_bytes))))
+    insts = []
+    for r in range(R):
+        xA_h, xB_h = FI.shares(ls, c.cid, r)
+        ks, es, ss = FI.seeds(c.cid, r)
+        d = dict(es=es, t_hat=F.keygen(P, ks), Phat=F.filter_prepare(P, L, dev(FI.weights(ls, c.cid, r), np.int8)))
+        d["Mhat"], d["sB"] = F.mask_prepare(P, L, ss)
+        d["sB4"] = d["sB"].view(ls.B, ls.Co, ls.H, ls.W)
+        d["xA"], d["xB"] = dev(xA_h, np.int32), dev(xB_h, np.int32)
+        d["XA"], d["XB"] = torch.empty_like(d["xA"]), torch.empty_like(d["xB"])
+        d["ct"] = torch.empty(lay.ct_in_words, dtype=torch.int64, device="cuda")
+        d["ct_out"] = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
+        d["SA"] = torch.empty(lay.out_spectra_words, dtype=torch.int32, device="cuda")
+        d["yA"] = torch.empty((ls.B, ls.Co, ls.H, ls.W), dtype=torch.int32, device="cuda")
+        d["yB"] = torch.empty_like(d["yA"])
+        d["A_msg"] = torch.empty(lay.n_in * ls.n, dtype=torch.int64, device="cuda")
+        d["A_rec"] = torch.empty_like(d["A_msg"])
+        insts.append(d)
     LAUNCHES_PER_STEP = 6
     side = [torch.cuda.Stream() for _ in range(3)]
 
-    def step():
+    def step(d):
         """One online layer.  Four independent producers run concurrently:
         Alice's encryption constants (Enc(0)), Alice's share encoding, Bob's
         HomRec plaintext from his share, and Bob's INTT2D of his mask share;
@@ -416,35 +474,36 @@ def run_gpu(args, rank, local_rank, world):
         main = torch.cuda.current_stream()
         for st in side:
             st.wait_stream(main)
-        F.encrypt_constants(P, L, t_hat, es, out=ct)
+        F.encrypt_constants(P, L, d["t_hat"], d["es"], out=d["ct"])
         with torch.cuda.stream(side[0]):
-            F.encode_share(P, L, xA, out=A_msg)
+            F.encode_share(P, L, d["xA"], out=d["A_msg"])
         with torch.cuda.stream(side[1]):
-            F.encode_share(P, L, xB, out=A_rec)
+            F.encode_share(P, L, d["xB"], out=d["A_rec"])
         with torch.cuda.stream(side[2]):
-            F.intt2d(P, sB4, out=yB)
+            F.intt2d(P, d["sB4"], out=d["yB"])
         for st in side:
             main.wait_stream(st)
-        F.homconv_sum(P, L, ct, A_msg, A_rec, Phat, Mhat, out=ct_out)
-        F.decrypt_share(P, L, t_hat, ct_out, out=yA)
+        F.homconv_sum(P, L, d["ct"], d["A_msg"], d["A_rec"], d["Phat"], d["Mhat"], out=d["ct_out"])
+        F.decrypt_share(P, L, d["t_hat"], d["ct_out"], out=d["yA"])
 
-    def step_unfused():
+    def step_unfused(d):
         """The same layer through the step-by-step entry points, one stream."""
-        F.ntt2d(P, xA, out=XA)
-        F.encrypt(P, L, t_hat, XA, es, out=ct)
-        F.ntt2d(P, xB, out=XB)
-        F.homrec(P, L, XB, ct)
-        F.homconv(P, L, ct, Phat, Mhat, out=ct_out)
-        F.decrypt(P, L, t_hat, ct_out, out=SA)
-        F.intt2d(P, SA.view(ls.B, ls.Co, ls.H, ls.W), out=yA)
-        F.intt2d(P, sB4, out=yB)
+        F.ntt2d(P, d["xA"], out=d["XA"])
+        F.encrypt(P, L, d["t_hat"], d["XA"], d["es"], out=d["ct"])
+        F.ntt2d(P, d["xB"], out=d["XB"])
+        F.homrec(P, L, d["XB"], d["ct"])
+        F.homconv(P, L, d["ct"], d["Phat"], d["Mhat"], out=d["ct_out"])
+        F.decrypt(P, L, d["t_hat"], d["ct_out"], out=d["SA"])
+        F.intt2d(P, d["SA"].view(ls.B, ls.Co, ls.H, ls.W), out=d["yA"])
+        F.intt2d(P, d["sB4"], out=d["yB"])
 
-    l2 = torch.cuda.get_device_properties(local_rank).L2_cache_size
-    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.int32, device="cuda")
+    def homconv_only(d):
+        F.homconv_sum(P, L, d["ct"], d["A_msg"], d["A_rec"], d["Phat"], d["Mhat"], out=d["ct_out"])
 
     for _ in range(max(1, args.warmup)):
-        step()
-        step_unfused()
+        for d in insts:
+            step(d)
+            step_unfused(d)
     torch.cuda.synchronize()
     s = torch.cuda.Stream()
 
@@ -459,18 +518,14 @@ def run_gpu(args, rank, local_rank, world):
         torch.cuda.current_stream().wait_stream(s)
         return gr
 
-    g = capture(step)
-    g_unfused = capture(step_unfused)
-    # HomConv alone, same launch configuration, for the roofline figure
-    g_hc = torch.cuda.CUDAGraph()
-    s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
-        with torch.cuda.graph(g_hc, stream=s):
-            F.homconv_sum(P, L, ct, A_msg, A_rec, Phat, Mhat, out=ct_out)
-    torch.cuda.current_stream().wait_stream(s)
+    g_step = [capture(lambda d=d: step(d)) for d in insts]
+    g_unfused = [capture(lambda d=d: step_unfused(d)) for d in insts]
+    # HomConv alone: one graph of R launches, one per instance, back to back
+    g_hc = capture(lambda: [homconv_only(d) for d in insts])
+    g_hc_warm = capture(lambda: [homconv_only(insts[0]) for _ in insts])
     for _ in range(args.warmup):
-        flush.fill_(1)
-        g.replay()
+        for gr in g_step:
+            gr.replay()
         g_hc.replay()
     torch.cuda.synchronize()
     sleep_cycles = int(60e6)  # about 30 ms at 2 GHz
@@ -482,60 +537,66 @@ def run_gpu(args, rank, local_rank, world):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def back_to_back(graphs, k, every=0):
+        """Replays graphs[i % len] for i < k back to back between two CUDA
+        events (plus one at every step boundary when `every`); returns the
+        events.  A short spin kernel first lets the host queue steps ahead,
+        so no step waits for its launch."""
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range((k if every else 1) + 1)]
+        torch.cuda._sleep(sleep_cycles)
+        ev[0].record()
+        for i in range(k):
+            graphs[i % len(graphs)].replay()
+            if every:
+                ev[i + 1].record()
+        ev[-1].record()
+        return ev
+
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
-    # a short spin kernel lets the host queue steps ahead, so no timed step
-    # waits for its launch; the flush before each step is outside its events
-    torch.cuda._sleep(sleep_cycles)
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        starts[i].record()
-        g.replay()
-        ends[i].record()
+    ev = back_to_back(g_step, args.steps)
     barrier()
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    # per-step distribution: a shorter pass with an event at every boundary
+    # (the events themselves add a few microseconds per step)
+    ev_d = back_to_back(g_step, min(args.steps, 1000), every=1)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev_d[:-2], ev_d[1:-1])]
 
     # the step-by-step path, for comparison
-    us = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(min(args.steps, 500))]
-    torch.cuda._sleep(sleep_cycles)
-    for i, (a, b) in enumerate(us):
-        flush.fill_(i & 0xFF)
-        a.record()
-        g_unfused.replay()
-        b.record()
+    n_unfused = min(args.steps, 600)
+    ev_u = back_to_back(g_unfused, n_unfused)
     torch.cuda.synchronize()
-    unfused_ms = [a.elapsed_time(b) for a, b in us]
+    unfused_ms = ev_u[0].elapsed_time(ev_u[-1]) / n_unfused
 
-    # HomConv launches alone (graph of the same launch), L2 flushed before each
-    hc_steps = max(20, min(args.steps, 2000))
-    hs = [torch.cuda.Event(enable_timing=True) for _ in range(hc_steps)]
-    he = [torch.cuda.Event(enable_timing=True) for _ in range(hc_steps)]
-    torch.cuda._sleep(sleep_cycles)
-    for i in range(hc_steps):
-        flush.fill_(i & 0xFF)
-        hs[i].record()
-        g_hc.replay()
-        he[i].record()
+    # HomConv launches alone: R per graph replay, cold (rotated) and warm
+    hc_reps = max(4, min(args.steps, 4000) // R)
+    ev_h = back_to_back([g_hc], hc_reps)
+    ev_w = back_to_back([g_hc_warm], hc_reps)
     torch.cuda.synchronize()
-    hc_ms = [a.elapsed_time(b) for a, b in zip(hs, he)]
+    hc_avg = ev_h[0].elapsed_time(ev_h[-1]) / (hc_reps * R)
+    hc_warm_ms = ev_w[0].elapsed_time(ev_w[-1]) / (hc_reps * R)
+
+    # NTT2D over a batch sweep of 32x32 planes (64 per image)
+    sweep = ntt2d_sweep(F, P, ls, back_to_back, args)
     clk = clocks.stop()
 
     # end to end through the C ABI with HOST buffers: the serving API, closed loop
-    e2e = e2e_through_server(F, P, ls, g_c, dev(w_h, np.int8), t_hat, xA_h[0], xB_h[0], args.e2e_requests)
+    xA_h, xB_h = FI.shares(ls, c.cid, 0)
+    e2e = e2e_through_server(F, P, ls, g_c, dev(FI.weights(ls, c.cid, 0), np.int8), insts[0]["t_hat"], xA_h[0],
+                             xB_h[0], args.e2e_requests)
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.int32, device="cuda")
     batched = None if args.skip_batched else run_batched(F, flush, sleep_cycles, args)
     serving = None if args.skip_serving else run_serving(F, args)
 
-    local_sec = sum(step_ms) / 1e3
+    local_sec = total_ms / 1e3
     tot_sec, tot_units = aggregate(local_sec, float(args.steps * ls.B), world)
     e2e_sec, e2e_units = aggregate(e2e["seconds"], float(e2e["requests"]), world)
     if rank != 0:
         return
     value = tot_units / tot_sec
-    hc_avg = float(np.mean(hc_ms))
     alg_bytes, macs = layer_counts(ls, lay.T, lay.beta, lay.GB, ls.n)
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     peak = peaks.get("hbm_gbs")
@@ -554,22 +615,29 @@ def run_gpu(args, rank, local_rank, world):
         cpu = {"value": 1.0 / per_layer, "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": sample}
     line = {
         "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "layer": "32x32x64->64 3x3", "batch": ls.B, "n": ls.n, "p": ls.p,
                    "q_bits": 60, "packing": {"g_c": g_c, "g_b": g_b, "T": lay.T},
-                   "l2": "flushed before every timed step (write of %d MiB)" % (flush.numel() * 4 >> 20),
+                   "l2": "inputs larger than L2: %d independent instances of the layer (%d MiB; L2 %d MiB) "
+                         "rotated step by step, each step's inputs last read %d steps earlier"
+                         % (R, R * inst_bytes >> 20, l2 >> 20, R - 1),
                    "step": "[encrypt_constants | encode_share(x_A) | encode_share(x_B) | intt2d(s_B)] -> "
-                           "homconv_sum (HomRec + HomConv + HomShare) -> decrypt_share (CUDA graph, 4 streams)"},
+                           "homconv_sum (HomRec + HomConv + HomShare) -> decrypt_share (CUDA graph, 4 streams); "
+                           "K graph replays back to back, events at step boundaries"},
         "mac_per_s": value * 2 * ls.Co * ls.Ci * ls.H * ls.W,
         "homconv_layers_per_s": ls.B / (hc_avg * 1e-3),
         "homconv_mac_per_s": macs / (hc_avg * 1e-3),
+        "homconv_warm_us": hc_warm_ms * 1e3,
         "useful_macs_per_layer": useful_macs // ls.B,
         "step_ms_p50": float(np.percentile(step_ms, 50)), "step_ms_p99": float(np.percentile(step_ms, 99)),
-        "step_by_step_ms": float(np.mean(unfused_ms)),
-        "roofline": {"kernel": "homconv_kernel (homconv_sum: HomRec addends + HomConv + HomShare)", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "peak_source": peak_src + " (hbm_gbs, burst copy)", "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "alg_bytes_per_launch": alg_bytes, "launch_us": hc_avg * 1e3},
+        "step_ms_distribution": "%d steps with an event at every boundary" % len(step_ms),
+        "step_by_step_ms": unfused_ms,
+        "roofline": {"kernel": "homconv_kernel (homconv_sum: HomRec addends + HomConv + HomShare)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "peak_source": peak_src + " (hbm_gbs, burst copy)",
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                     "launch_us": hc_avg * 1e3,
+                     "timing": "%d launches back to back over the %d instances (cold), CUDA events" % (hc_reps * R, R)},
         "e2e": {"value": e2e_units / e2e_sec, "unit": "layers/s", "h2d_bytes_per_step": e2e["h2d"],
                 "d2h_bytes_per_step": e2e["d2h"], "requests": e2e["requests"], "p50_us": e2e["p50_us"],
                 "p99_us": e2e["p99_us"], "mean_batch": e2e["mean_batch"],
@@ -577,7 +645,9 @@ def run_gpu(args, rank, local_rank, world):
                         "copies in and out inside the timed region; host wall clock"},
         "batched": batched,
         "serving": serving,
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps + hc_steps,
+        "ntt2d_sweep": sweep,
+        "gpu_launches": LAUNCHES_PER_STEP * (args.steps + len(step_ms)) + 8 * n_unfused + 2 * hc_reps * R
+                        + sum(pt["launches"] for pt in sweep["points"]),
         "homconv_variant": args.homconv_variant,
         "clocks": clk,
         "cpu_baseline": cpu,

@@ -378,9 +378,23 @@ int fdsc_layer_online_noalloc(const fdsc_params* P, const fdsc_layer* L, const u
  * 1 limb-column accumulation with one image group per thread, 2 the same
  * with two image groups per thread, 3 carry-chained 128-bit accumulation,
  * 4 input tile staged in shared memory with carry-chained accumulation,
- * 5 staged tile with limb columns.  FDSC_ERR_ARG for other values.  Not
- * synchronised with concurrent calls. */
+ * 5 staged tile with limb columns, 6 staged tile with lazy 32-bit-limb
+ * columns.  FDSC_ERR_ARG for other values.  Not synchronised with concurrent
+ * calls. */
 int fdsc_set_homconv_variant(int variant);
+
+/* Launch overlap for the online kernels (on = 1; off = 0, the default):
+ * each online kernel (NTT2D/INTT2D, encryption, HomRec, HomConv, masks,
+ * decryption, and the fused kernels) is launched with programmatic stream
+ * serialisation, so it may start while the kernel before it in the stream
+ * finishes.  It stages the params' twiddle tables, and the encryption
+ * constants draw and transform their error polynomial from the seed, before
+ * it waits for that kernel; it touches caller memory only after the wait.
+ * Results are identical either way.  Off by default: measured on GB300, the
+ * early start saved under 1 us per layer step and made graph replays of
+ * consecutive steps slower.  Returns the previous setting.  Applies to
+ * launches issued after the call, process-wide. */
+int fdsc_set_launch_overlap(int on);
 
 #ifdef __cplusplus
 }

@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(kMaxThreads) encode_kernel(DevParams P, DevLay
     __shared__ u64 cdt[19];
     const u32 u = blockIdx.x;
     const u32 h = u % L.beta, k = (u / L.beta) % L.T, bb = u / (L.beta * L.T);
+    griddep_release();
+    griddep_wait();
     if (kMode == 0 && threadIdx.x < 19) cdt[threadIdx.x] = P.cdt[threadIdx.x];
     for (u32 sg = threadIdx.x; sg < P.n; sg += blockDim.x)
         slots[sg] = input_slot(P, L, X, bb, k, h, sg >> P.logS, sg & (P.S - 1));
@@ -187,6 +189,8 @@ __global__ void __launch_bounds__(kMaxThreads) mask_kernel(DevParams P, DevLayer
     const u32 v = blockIdx.x;
     const u32 h = v % L.beta, co = (v / L.beta) % L.Co, bb = v / (L.beta * L.Co);
     const u32 b_off = seeds ? bb * P.d * L.g_b : 0;  // first image of the group, for indexing randomness
+    griddep_release();
+    griddep_wait();
     if (seeds) seed = seeds[bb];
     const u64 kMask = stream_key(seed, DOM_MASK), kSplit = stream_key(seed, DOM_MASK_SPLIT);
     for (u32 sg = threadIdx.x; sg < P.n; sg += blockDim.x) {
@@ -249,6 +253,8 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_kernel(DevParams P, DevLa
     const u32 h = v % L.beta, co = (v / L.beta) % L.Co, bb = v / (L.beta * L.Co);
     const u64* c0 = ct + (u64)v * 2 * P.n;
     const u64* c1 = c0 + P.n;
+    griddep_release();
+    griddep_wait();
     for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) c[j] = addmod_q(mulmod_q(c0[j], t_hat[j], P), c1[j], P.q);
     __syncthreads();
     ntt_q_inv8(c, P);
@@ -309,16 +315,14 @@ cudaError_t launch_encrypt(const DevParams& P, const DevLayer& L, const u64* t_h
     const size_t sm = (size_t)P.n * 12;
     cudaError_t e = set_smem(encode_kernel<0>, sm);
     if (e != cudaSuccess) return e;
-    encode_kernel<0><<<L.n_in, threads_for(P.n), sm, s>>>(P, L, t_hat, X, seed, ct);
-    return cudaGetLastError();
+    return launch_online(encode_kernel<0>, L.n_in, threads_for(P.n), sm, s, P, L, t_hat, X, seed, ct);
 }
 
 cudaError_t launch_homrec(const DevParams& P, const DevLayer& L, const u32* XB, u64* ct, cudaStream_t s) {
     const size_t sm = (size_t)P.n * 12;
     cudaError_t e = set_smem(encode_kernel<1>, sm);
     if (e != cudaSuccess) return e;
-    encode_kernel<1><<<L.n_in, threads_for(P.n), sm, s>>>(P, L, nullptr, XB, 0, ct);
-    return cudaGetLastError();
+    return launch_online(encode_kernel<1>, L.n_in, threads_for(P.n), sm, s, P, L, (const u64*)nullptr, XB, (u64)0, ct);
 }
 
 cudaError_t launch_filter_prepare(const DevParams& P, const DevLayer& L, const int8_t* w, u32 fh, u32 fw, u64* Phat,
@@ -337,8 +341,7 @@ cudaError_t launch_mask_prepare(const DevParams& P, const DevLayer& L, u64 seed,
     const size_t sm = (size_t)P.n * 12;
     cudaError_t e = set_smem(mask_kernel, sm);
     if (e != cudaSuccess) return e;
-    mask_kernel<<<L.n_out, threads_for(P.n), sm, s>>>(P, L, seed, seeds, Mhat, sB);
-    return cudaGetLastError();
+    return launch_online(mask_kernel, L.n_out, threads_for(P.n), sm, s, P, L, seed, seeds, Mhat, sB);
 }
 
 cudaError_t launch_decrypt(const DevParams& P, const DevLayer& L, const u64* t_hat, const u64* ct, u32* SA,
@@ -346,6 +349,5 @@ cudaError_t launch_decrypt(const DevParams& P, const DevLayer& L, const u64* t_h
     const size_t sm = (size_t)P.n * 12;
     cudaError_t e = set_smem(decrypt_kernel, sm);
     if (e != cudaSuccess) return e;
-    decrypt_kernel<<<L.n_out, threads_for(P.n), sm, s>>>(P, L, t_hat, ct, SA);
-    return cudaGetLastError();
+    return launch_online(decrypt_kernel, L.n_out, threads_for(P.n), sm, s, P, L, t_hat, ct, SA);
 }

@@ -18,6 +18,7 @@ struct DevParams {
     u32 n, logn, p, S, logS, d;
     u32 Sinv, Sinv_s;      // S^-1 mod p and its 32-bit Shoup companion
     u32 lmax, loglmax;     // NTT2D twiddle table covers w_lmax^k, k < lmax/2
+    u32 g_p;               // the primitive root of p the roots of unity come from
     u64 q, twoq, delta;
     u64 r64, r64_s;        // 2^64 mod q, floor(r64 2^64 / q)
     u64 one_s;             // floor(2^64 / q): Shoup companion of 1
@@ -59,6 +60,31 @@ struct fdsc_params {
 
 // ---- host helpers (params.cu) ----
 int fdsc_set_error(int code, const char* fmt, ...);
+
+// Whether online kernels are launched with programmatic stream serialisation
+// (fdsc_set_launch_overlap; off by default).
+bool fdsc_launch_overlap();
+
+#ifdef __CUDACC__
+// Launches an online kernel (one that calls griddep_wait() before touching
+// caller memory) so that it may start while its predecessor in the stream
+// finishes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_online(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = fdsc_launch_overlap() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+#endif
 int fdsc_derive(u32 n, u32 p, fdsc_params_info* out);
 int fdsc_make_layer(const fdsc_params_info& I, const fdsc_layer* L, DevLayer* out, fdsc_layout* lay);
 void fdsc_host_cdt(u64* cdt19);

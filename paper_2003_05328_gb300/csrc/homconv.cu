@@ -96,6 +96,51 @@ __device__ __forceinline__ void acc_set(AccLimb& a, u64 r) {
     a.c2 = a.c3 = 0;
 }
 
+// ---- lazy 32-bit-limb columns.  With a = a1 2^32 + a0, b = b1 2^32 + b0
+// (a1, b1 < 2^28 since q < 2^60): the low products a0 b0 go into a 96-bit
+// word (one add-with-carry chain), the middle products a0 b1 + a1 b0 (each
+// < 2^60) into a 64-bit column folded into `mh` every 4 terms, the high
+// products a1 b1 (< 2^56) into a 64-bit column that cannot overflow within
+// 256 terms.  Four 32x32+64-bit multiply-adds and three adds per product.
+struct AccLazy {
+    u32 l0, l1, l2;
+    u64 mid, mh, hi;
+};
+__device__ __forceinline__ void acc_zero(AccLazy& a) {
+    a.l0 = a.l1 = a.l2 = 0;
+    a.mid = a.mh = a.hi = 0;
+}
+__device__ __forceinline__ void acc_mac(AccLazy& A, u64 a, u64 b) {
+    const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
+    const u64 p = (u64)a0 * b0;
+    asm("add.cc.u32  %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32    %2, %2, 0;"
+        : "+r"(A.l0), "+r"(A.l1), "+r"(A.l2)
+        : "r"((u32)p), "r"((u32)(p >> 32)));
+    A.mid += (u64)a0 * b1;
+    A.mid += (u64)a1 * b0;
+    A.hi += (u64)a1 * b1;
+}
+// Fold the middle column: afterwards mid < 2^32; between folds at most 4
+// products (8 middle terms < 2^60 each) are added, so mid stays below 2^64.
+__device__ __forceinline__ void acc_normalize(AccLazy& A) {
+    A.mh += A.mid >> 32;
+    A.mid &= 0xFFFFFFFFull;
+}
+__device__ __forceinline__ u64 acc_reduce(AccLazy A, const DevParams& P) {
+    acc_normalize(A);
+    const u64 L = ((u64)A.l1 << 32) | A.l0;
+    const u64 lo = L + (A.mid << 32);
+    const u64 hi = (u64)A.l2 + A.mh + A.hi + (lo < L ? 1 : 0);
+    return reduce128(hi, lo, P);
+}
+__device__ __forceinline__ void acc_set(AccLazy& a, u64 r) {
+    acc_zero(a);
+    a.l0 = (u32)r;
+    a.l1 = (u32)(r >> 32);
+}
+
 __device__ __forceinline__ ulonglong2 ldg2(const u64* p) { return __ldg(reinterpret_cast<const ulonglong2*>(p)); }
 
 // kAdd extra c1 addends A1, A2 ([n_in][n] words) are added to every input
@@ -108,6 +153,8 @@ __global__ void __launch_bounds__(kThreads) homconv_kernel(DevParams P, DevLayer
                                                            const u64* __restrict__ Mhat, u64* __restrict__ ct_out,
                                                            u32 btiles, u32 jtiles) {
     using Acc = typename std::conditional<kWide, AccLimb, Acc128>::type;
+    griddep_release();
+    griddep_wait();
     u32 blk = blockIdx.x;
     const u32 bt = blk % btiles;
     blk /= btiles;
@@ -239,9 +286,8 @@ cudaError_t launch_variant(const DevParams& P, const DevLayer& L, const u64* ct_
     const u32 btiles = (L.GB + NB - 1) / NB;
     const u64 grid = (u64)jtiles * ctiles * btiles;
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
-    homconv_kernel<NB, W, kAdd><<<(u32)grid, kThreads, 0, s>>>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, btiles,
-                                                               jtiles);
-    return cudaGetLastError();
+    return launch_online(homconv_kernel<NB, W, kAdd>, (u32)grid, kThreads, 0, s, P, L, ct_in, A1, A2, Phat, Mhat,
+                         ct_out, btiles, jtiles);
 }
 
 
@@ -253,20 +299,25 @@ cudaError_t launch_variant(const DevParams& P, const DevLayer& L, const u64* ct_
 // HBM, prefetching the next kPF3 terms while the current ones are multiplied.
 constexpr u32 kJ3 = 32, kW3 = 8, kThreads3 = 32 * kW3, kPF3 = 8;
 
-template <bool kWide>
+// kAcc: 0 carry-chained 128-bit, 1 30-bit limb columns, 2 lazy 32-bit-limb columns
+template <int kAcc>
 __global__ void __launch_bounds__(kThreads3) homconv3_kernel(DevParams P, DevLayer L, const u64* __restrict__ ct_in,
                                                              const u64* __restrict__ A1, const u64* __restrict__ A2,
                                                              const u64* __restrict__ Phat,
                                                              const u64* __restrict__ Mhat, u64* __restrict__ ct_out,
                                                              u32 jtiles, u32 ctiles) {
     extern __shared__ __align__(16) u64 xs[];  // [T][2][kJ3] canonical words, or 30-bit limb pairs
-    using Acc = typename std::conditional<kWide, AccLimb, Acc128>::type;
+    constexpr bool kWide = kAcc == 1;
+    using Acc = typename std::conditional<kAcc == 1, AccLimb,
+                                          typename std::conditional<kAcc == 2, AccLazy, Acc128>::type>::type;
     u32 blk = blockIdx.x;
     const u32 jt = blk % jtiles;
     blk /= jtiles;
     const u32 ct = blk % ctiles, bb = blk / ctiles;
     const u32 nJ = L.beta * P.n, T = L.T;
     const u64 n = P.n, beta = L.beta;
+    griddep_release();
+    griddep_wait();
     // stage the input tile (all threads)
     for (u32 e = threadIdx.x; e < T * kJ3; e += kThreads3) {
         const u32 k = e / kJ3, jj = e % kJ3, J = jt * kJ3 + jj;
@@ -320,8 +371,14 @@ __global__ void __launch_bounds__(kThreads3) homconv3_kernel(DevParams P, DevLay
                 acc_mac(acc0, xa, wcur[u]);
                 acc_mac(acc1, xb, wcur[u]);
             }
+            if constexpr (kAcc == 2) {
+                if ((u & 3) == 3) {
+                    acc_normalize(acc0);
+                    acc_normalize(acc1);
+                }
+            }
         }
-        if constexpr (kWide) {
+        if constexpr (kAcc != 0) {
             acc_normalize(acc0);
             acc_normalize(acc1);
         }
@@ -338,7 +395,7 @@ __global__ void __launch_bounds__(kThreads3) homconv3_kernel(DevParams P, DevLay
     ct_out[v * 2 * n + n + j] = r1;
 }
 
-template <bool W>
+template <int W>
 cudaError_t launch_v3(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
                       const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
     const u32 nJ = L.beta * P.n;
@@ -350,18 +407,19 @@ cudaError_t launch_v3(const DevParams& P, const DevLayer& L, const u64* ct_in, c
         cudaError_t e = cudaFuncSetAttribute(homconv3_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    homconv3_kernel<W><<<(u32)grid, kThreads3, smem, s>>>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, jtiles, ctiles);
-    return cudaGetLastError();
+    return launch_online(homconv3_kernel<W>, (u32)grid, kThreads3, smem, s, P, L, ct_in, A1, A2, Phat, Mhat, ct_out,
+                         jtiles, ctiles);
 }
+
 
 }  // namespace
 
 // Variant selection: 0 = automatic, 1 = limb columns NB=1, 2 = limb columns
 // NB=2, 3 = carry chain NB=1, 4 = staged tile with carry chain, 5 = staged
-// tile with limb columns.
+// tile with limb columns, 6 = staged tile with lazy 32-bit-limb columns.
 static int g_homconv_variant = 0;
 extern "C" int fdsc_set_homconv_variant(int v) {
-    if (v < 0 || v > 5) return FDSC_ERR_ARG;
+    if (v < 0 || v > 6) return FDSC_ERR_ARG;
     g_homconv_variant = v;
     return FDSC_OK;
 }
@@ -382,12 +440,13 @@ int homconv_default_variant(const DevLayer& L) { return L.T <= 256 ? 4 : 3; }
 
 cudaError_t launch_homconv_v(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
                              const u64* Phat, const u64* Mhat, u64* ct_out, int v, cudaStream_t s) {
-    if (v <= 0 || v > 5) v = homconv_default_variant(L);
+    if (v <= 0 || v > 6) v = homconv_default_variant(L);
     // the staged tile must fit in shared memory (T <= 256 words x 2 x 32 lanes)
-    if ((v == 4 || v == 5) && L.T > 256) v = 3;
+    if (v >= 4 && L.T > 256) v = 3;
     switch (v) {
-        case 4: return launch_v3<false>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
-        case 5: return launch_v3<true>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+        case 4: return launch_v3<0>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+        case 5: return launch_v3<1>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+        case 6: return launch_v3<2>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
         case 1: return launch_adds<1, true>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
         case 2: return launch_adds<2, true>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
         default: return launch_adds<1, false>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);

@@ -432,6 +432,17 @@ __device__ __forceinline__ void stage_wait() {
     __syncthreads();
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may start while the kernel before it in the stream is still
+// running; griddep_wait() returns once that kernel has completed and its
+// writes are visible (at once when there is none).  Every online kernel calls
+// griddep_wait() before its first access to caller memory, read or write, so
+// only work that depends on the params alone (twiddle tables, randomness
+// from a seed argument) runs ahead.  griddep_release() lets the next kernel
+// in the stream start its own launch early.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Cyclic radix-8 line transforms over `planes` stacked H x W planes in
 // shared memory (plane stride HW).  Rows: planes*H lines of length W; columns:
 // planes*W lines of length H.  `tw` holds w_T^k (k < T/2) for T = 2^logT >=

@@ -25,6 +25,12 @@ int fdsc_set_error(int code, const char* fmt, ...) {
 
 extern "C" const char* fdsc_last_error(void) { return g_err; }
 
+// ---------------------------------------------------------------- launch overlap
+#include <atomic>
+static std::atomic<int> g_launch_overlap{0};
+bool fdsc_launch_overlap() { return g_launch_overlap.load(std::memory_order_relaxed) != 0; }
+extern "C" int fdsc_set_launch_overlap(int on) { return g_launch_overlap.exchange(on ? 1 : 0); }
+
 // ---------------------------------------------------------------- number theory
 static u64 mul_mod(u64 a, u64 b, u64 m) { return (u64)((u128)a * b % m); }
 
@@ -305,6 +311,10 @@ extern "C" int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_p
         return fdsc_set_error(FDSC_ERR_ARG, "internal: table layout %zu > %zu bytes", off, total);
     }
     e = cudaMemcpy(P->table_mem, h, off, cudaMemcpyHostToDevice);
+    // a copy from pageable memory may return before it lands; kernels on
+    // other streams (and those that read the tables before their
+    // programmatic wait) must see the finished tables
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(P->table_mem);
         delete P;
@@ -312,7 +322,7 @@ extern "C" int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_p
     }
     unsigned char* dbase = (unsigned char*)P->table_mem;
     DevParams& D = P->dev;
-    D.n = n; D.logn = I.logn; D.p = p; D.S = S; D.logS = I.logS; D.d = I.d;
+    D.n = n; D.logn = I.logn; D.p = p; D.S = S; D.logS = I.logS; D.d = I.d; D.g_p = I.g_p;
     D.Sinv = (u32)pow_mod(S, p - 2, p);
     D.Sinv_s = fdsc_shoup32(D.Sinv, p);
     D.lmax = lmax;

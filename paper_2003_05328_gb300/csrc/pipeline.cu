@@ -36,14 +36,19 @@ __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, con
     const u32 n = P.n;
     ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^brv, companion)
     u64* c = reinterpret_cast<u64*>(tq + n);             // padded [n]
+    u64* key = c + padded_len(n);                        // [n], the key's NTT_q words
     __shared__ u64 cdt[19];
+    const u32 u = blockIdx.x, grp = u / per_group;
+    griddep_release();
     stage_async(tq, P.qfw2, n * 16);
     if (threadIdx.x < 19) cdt[threadIdx.x] = P.cdt[threadIdx.x];
     __syncthreads();
-    const u32 u = blockIdx.x, grp = u / per_group;
-    t_hat += (u64)grp * key_stride;
     const u32 ur = seeds ? u - grp * per_group : u;  // ciphertext number for the randomness
-    if (seeds) seed = seeds[grp];
+    if (seeds) {
+        griddep_wait();
+        seed = seeds[grp];
+    }
+    // NTT_q(e) needs the seed alone: it runs while the previous kernel finishes
     const u64 keyE = stream_key(seed, DOM_E);
     for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
         const int e = gauss_sample(stream_at(keyE, (u64)ur * n + i), cdt);
@@ -51,14 +56,29 @@ __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, con
     }
     stage_wait();
     ntt_r8p<true, u64>(c, P.logn, 1, tq, 0, 0, P);
+    if (!seeds) griddep_wait();
+    stage_async(key, t_hat + (u64)grp * key_stride, n * 8);
     const u64 keyA = stream_key(seed, DOM_A);
     u64* c0 = ct + (u64)u * 2 * n;
     u64* c1 = c0 + n;
-    for (u32 j = threadIdx.x; j < n; j += blockDim.x) {
-        const u64 idx = 2 * ((u64)ur * n + j);
-        const u64 a = uniform_q(stream_at(keyA, idx), stream_at(keyA, idx + 1), P.q);
-        c0[j] = a ? P.q - a : 0;
-        c1[j] = addmod_q(mulmod_q(a, __ldg(t_hat + j), P), c[padx(j)], P.q);
+    // c0 = -a while the key arrives; a stays in registers for c1
+    for (u32 j0 = 0; j0 < n; j0 += 8 * blockDim.x) {
+        u64 a[8];
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const u32 j = j0 + threadIdx.x + (u32)r * blockDim.x;
+            if (j < n) {
+                const u64 idx = 2 * ((u64)ur * n + j);
+                a[r] = uniform_q(stream_at(keyA, idx), stream_at(keyA, idx + 1), P.q);
+                c0[j] = a[r] ? P.q - a[r] : 0;
+            }
+        }
+        stage_wait();
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+            const u32 j = j0 + threadIdx.x + (u32)r * blockDim.x;
+            if (j < n) c1[j] = addmod_q(mulmod_q(a[r], key[j], P), c[padx(j)], P.q);
+        }
     }
 }
 
@@ -81,19 +101,31 @@ __global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLaye
     stage_async(tp, P.pinv2, S * 8);
     load_pairs_for_length(tw_row, L.logW, false, P);
     load_pairs_for_length(tw_col, L.logH, false, P);
+    griddep_release();
+    griddep_wait();
 
     const u32 u = blockIdx.x, k = u % L.T, bb = u / L.T;
     const u32 HW = L.HW, logHW = L.logH + L.logW, blocks = L.g_c * L.g_b;
-    // planes of the packed slot vector, loaded in bit-reversed order along both axes
-    for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
-        const u32 r = e >> P.logS, s = e & (S - 1), blk = s >> logHW, f = s & (HW - 1);
-        u32 v = 0;
-        if (blk < blocks) {
-            const u32 b = (bb * P.d + r) * L.g_b + blk / L.g_c, ci = k * L.g_c + blk % L.g_c;
-            if (b < L.B && ci < L.Ci) v = __ldg(x + ((u64)b * L.Ci + ci) * HW + f);
+    // planes of the packed slot vector, loaded in bit-reversed order along
+    // both axes; each thread issues its eight loads before storing any
+    for (u32 e0 = 0; e0 < n; e0 += 8 * blockDim.x) {
+        u32 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            const u32 e = e0 + threadIdx.x + (u32)t * blockDim.x;
+            const u32 r = e >> P.logS, s = e & (S - 1), blk = s >> logHW, f = s & (HW - 1);
+            v[t] = 0;
+            if (e < n && blk < blocks) {
+                const u32 b = (bb * P.d + r) * L.g_b + blk / L.g_c, ci = k * L.g_c + blk % L.g_c;
+                if (b < L.B && ci < L.Ci) v[t] = __ldg(x + ((u64)b * L.Ci + ci) * HW + f);
+            }
         }
-        const u32 pos = (e & ~(HW - 1)) + (brv_bits(f >> L.logW, L.logH) << L.logW) + brv_bits(f & (L.W - 1), L.logW);
-        slots[padx(pos)] = v;
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            const u32 e = e0 + threadIdx.x + (u32)t * blockDim.x, f = e & (HW - 1);
+            const u32 pos = (e & ~(HW - 1)) + (brv_bits(f >> L.logW, L.logH) << L.logW) + brv_bits(f & (L.W - 1), L.logW);
+            if (e < n) slots[padx(pos)] = v[t];
+        }
     }
     __syncthreads();
     // NTT2D of every plane (zero planes included): rows, then columns
@@ -146,13 +178,31 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
     stage_async(tp, P.pfw2, S * 8);
     load_pairs_for_length(tw_row, L.logW, true, P);
     load_pairs_for_length(tw_col, L.logH, true, P);
+    griddep_release();
+    griddep_wait();
 
     const u32 v = blockIdx.x, co = v % L.Co, bb = v / L.Co;
     t_hat += (u64)bb * key_stride;
     const u64* c0 = ct + (u64)v * 2 * n;
     const u64* c1 = c0 + n;
-    for (u32 j = threadIdx.x; j < n; j += blockDim.x)
-        c[padx(j)] = addmod_q(mulmod_q(__ldg(c0 + j), __ldg(t_hat + j), P), __ldg(c1 + j), P.q);
+    // v = c0 t + c1; each thread issues the loads of four elements at a time
+    for (u32 j0 = 0; j0 < n; j0 += 4 * blockDim.x) {
+        u64 a[4], t[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const u32 j = j0 + threadIdx.x + (u32)r * blockDim.x;
+            if (j < n) {
+                a[r] = __ldg(c0 + j);
+                t[r] = __ldg(t_hat + j);
+                b[r] = __ldg(c1 + j);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const u32 j = j0 + threadIdx.x + (u32)r * blockDim.x;
+            if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
+        }
+    }
     stage_wait();
     ntt_r8p<false, u64>(c, P.logn, 1, tq, P.ninv, P.ninv_s, P);
     for (u32 coef = threadIdx.x; coef < n; coef += blockDim.x) {
@@ -199,15 +249,15 @@ size_t decrypt_share_smem_bytes(const DevParams& P, const DevLayer& L) {
     const size_t np = padded_len(P.n), npl = padded_len(P.d * L.g_b * L.HW);
     return (size_t)P.n * 16 + np * 8 + (size_t)P.S * 8 + np * 4 + npl * 4 + (size_t)4 * (L.W + L.H);
 }
-size_t constants_smem_bytes(const DevParams& P) { return (size_t)P.n * 16 + (size_t)padded_len(P.n) * 8; }
+size_t constants_smem_bytes(const DevParams& P) { return (size_t)P.n * 24 + (size_t)padded_len(P.n) * 8; }
 
 cudaError_t launch_constants(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, u64 seed,
                              const u64* seeds, u64* ct, cudaStream_t s) {
     const size_t sm = constants_smem_bytes(P);
     cudaError_t e = opt_in(constants_kernel, sm);
     if (e != cudaSuccess) return e;
-    constants_kernel<<<L.n_in, threads_for(P.n), sm, s>>>(P, t_hat, key_stride, L.T * L.beta, seed, seeds, ct);
-    return cudaGetLastError();
+    return launch_online(constants_kernel, L.n_in, threads_for(P.n), sm, s, P, t_hat, key_stride, L.T * L.beta, seed,
+                         seeds, ct);
 }
 
 cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u64* out, bool add_to_ct,
@@ -215,9 +265,7 @@ cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u6
     const size_t sm = share_smem_bytes(P, L);
     cudaError_t e = add_to_ct ? opt_in(share_kernel<1>, sm) : opt_in(share_kernel<0>, sm);
     if (e != cudaSuccess) return e;
-    if (add_to_ct) share_kernel<1><<<L.n_in, threads_for(P.n), sm, s>>>(P, L, x, out);
-    else share_kernel<0><<<L.n_in, threads_for(P.n), sm, s>>>(P, L, x, out);
-    return cudaGetLastError();
+    return launch_online(add_to_ct ? share_kernel<1> : share_kernel<0>, L.n_in, threads_for(P.n), sm, s, P, L, x, out);
 }
 
 cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, const u64* ct,
@@ -226,7 +274,6 @@ cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u6
     cudaError_t e = opt_in(decrypt_share_kernel, sm);
     if (e != cudaSuccess) return e;
     const u32 scale = fdsc_powmod32(L.HW % P.p, P.p - 2, P.p);
-    decrypt_share_kernel<<<L.n_out, threads_for(P.n), sm, s>>>(P, L, t_hat, key_stride, ct, y, scale,
-                                                                fdsc_shoup32(scale, P.p));
-    return cudaGetLastError();
+    return launch_online(decrypt_share_kernel, L.n_out, threads_for(P.n), sm, s, P, L, t_hat, key_stride, ct, y, scale,
+                         fdsc_shoup32(scale, P.p));
 }

@@ -233,6 +233,8 @@ extern "C" int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, u
             return fail(fdsc_set_error(FDSC_ERR_ARG, "layer %u: params missing or on another device", i));
         if (!sp.w || !sp.t_hat || !sp.xA || !sp.xB || !sp.yA || !sp.yB)
             return fail(fdsc_set_error(FDSC_ERR_ARG, "layer %u: NULL buffer", i));
+        if (((uintptr_t)sp.t_hat | (uintptr_t)sp.xA | (uintptr_t)sp.xB | (uintptr_t)sp.yA | (uintptr_t)sp.yB) & 15)
+            return fail(fdsc_set_error(FDSC_ERR_ARG, "layer %u: buffers must be 16-byte aligned", i));
         const fdsc_params_info& I = sp.params->info;
         pl.L = sp.layer;
         if (pl.L.g_c == 0 || pl.L.g_b == 0) default_pack(I, pl.L, &pl.L.g_c, &pl.L.g_b);

@@ -70,6 +70,7 @@ _SIGS = {
     "fdsc_homconv": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp, _vp]),
     "fdsc_decrypt": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
     "fdsc_set_homconv_variant": (C.c_int, [C.c_int]),
+    "fdsc_set_launch_overlap": (C.c_int, [C.c_int]),
     "fdsc_encrypt_constants": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp]),
     "fdsc_encode_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
     "fdsc_homrec_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
@@ -260,6 +261,12 @@ def mask_prepare(P: Params, L: LayerSpec, seed: int, M_hat=None, sB_hat=None, st
 def set_homconv_variant(v: int) -> None:
     """Kernel variant for HomConv (0 automatic; results are identical)."""
     _call("fdsc_set_homconv_variant", v)
+
+
+def set_launch_overlap(on: bool) -> bool:
+    """Programmatic dependent launch of the online kernels (default off);
+    returns the previous setting."""
+    return bool(lib().fdsc_set_launch_overlap(1 if on else 0))
 
 
 # ---------------------------------------------------------------- online

@@ -281,7 +281,7 @@ def test_homconv_variants_identical(F, shape):
     ref = O.homconv(OP, OL, summed.astype(np.uint64), Ph, Mh)
     d = lambda a: dev(a.view(np.int64), np.int64)
     try:
-        for v in range(1, 6):
+        for v in range(1, 7):
             F.set_homconv_variant(v)
             out = F.homconv_sum(P, L, d(ct), d(A1), d(A2), d(Ph), d(Mh))
             assert np.array_equal(u64(out).reshape(ref.shape), ref), v

@@ -155,3 +155,30 @@ def test_server_budget_and_timeouts(F):
     assert e.value.code == -1
     S.close()
     P.close()
+
+
+def test_launch_overlap_gives_identical_results(F):
+    """Programmatic dependent launch changes when kernels start, not what
+    they compute: a plan captured with and without it, and eager calls in
+    one stream, give the same words."""
+    specs, refs, params = _make_layers(F, 11)
+    prev = F.set_launch_overlap(False)
+    try:
+        plan_off = F.Plan(specs[:3])
+        F.set_launch_overlap(True)
+        plan_on = F.Plan(specs[:3])
+        for plan in (plan_off, plan_on, plan_off, plan_on):
+            for d in specs[:3]:
+                d["yA"].zero_()
+                d["yB"].zero_()
+            plan.launch()
+            torch.cuda.synchronize()
+            for d, ref in zip(specs[:3], refs[:3]):
+                assert np.array_equal(u32(d["yA"]).reshape(ref["yA"].shape), ref["yA"])
+                assert np.array_equal(u32(d["yB"]).reshape(ref["yB"].shape), ref["yB"])
+        plan_off.close()
+        plan_on.close()
+    finally:
+        F.set_launch_overlap(prev)
+    for P in params:
+        P.close()
