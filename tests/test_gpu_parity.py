@@ -259,7 +259,11 @@ def test_argument_errors_are_reported(F):
 
 @pytest.mark.parametrize("shape", [(2048, 1, 64, 64, 32, 32, 2, 1), (4096, 2, 256, 8, 8, 8, 64, 1),
                                    (1024, 3, 5, 7, 16, 16, 2, 2), (64, 1, 300, 3, 8, 8, 1, 1),
-                                   (256, 2, 3, 5, 32, 16, 1, 1)])
+                                   (256, 2, 3, 5, 32, 16, 1, 1),
+                                   # many image groups per CTA (tile slots recycled), T not a multiple of 8
+                                   (2048, 16, 50, 8, 32, 32, 2, 1),
+                                   # beta = 4 halves per plane, Co not a multiple of 8
+                                   (1024, 2, 12, 12, 64, 64, 1, 1)])
 def test_homconv_variants_identical(F, shape):
     """Every HomConv kernel variant (accumulation scheme, tiling, fused c1
     addends) gives the oracle's words."""
@@ -289,6 +293,8 @@ def test_homconv_variants_identical(F, shape):
             part = ct.astype(object)
             part[:, 1] = (part[:, 1] + A1.astype(object)) % OP.q
             assert np.array_equal(u64(out).reshape(ref.shape), O.homconv(OP, OL, part.astype(np.uint64), Ph, None)), v
+            out = F.homconv_sum(P, L, d(summed.astype(np.uint64)), None, None, d(Ph), d(Mh))
+            assert np.array_equal(u64(out).reshape(ref.shape), ref), v
     finally:
         F.set_homconv_variant(0)
     P.close()
