@@ -419,6 +419,59 @@ def ntt2d_sweep(F, P, ls, back_to_back, args):
             "images_at_60pct": first}
 
 
+def run_kernel_only(args):
+    """A few launches of one part of the path, for profiler captures (no
+    timing, no JSON line): `homconv` (HomConv + HomShare of the 32x32x64
+    layer on seeded random words), `ntt2d` (forward NTT2D of --planes 32x32
+    planes) or `step` (the fused online step of that layer, eager)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2003_05328_gb300 import build as B
+
+    B.build()
+    from paper_2003_05328_gb300 import fdsc as F
+
+    c = FI.CONFIGS[WORKLOAD]
+    ls = c.layers[0]
+    info = F.params_query(ls.n, ls.p)
+    g_c, g_b = FI.default_pack(ls, info.S)
+    L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
+    P = F.Params(ls.n, ls.p, max_T=64)
+    lay = F.layout(P, L)
+    F.set_homconv_variant(args.homconv_variant)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(FI.SEED_BASE)
+    rnd = lambda hi, k: torch.randint(0, hi, (k,), dtype=torch.int64, device="cuda", generator=g)
+    if args.kernel_only == "homconv":
+        ct, Ph, Mh = rnd(info.q, lay.ct_in_words), rnd(info.q, lay.filter_words), rnd(info.q, lay.mask_words)
+        A1, A2 = rnd(info.q, lay.n_in * ls.n), rnd(info.q, lay.n_in * ls.n)
+        out = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
+        for _ in range(args.steps):
+            F.homconv_sum(P, L, ct, A1, A2, Ph, Mh, out=out)
+    elif args.kernel_only == "ntt2d":
+        x = rnd(ls.p, args.planes * ls.H * ls.W).to(torch.int32).view(args.planes, ls.H, ls.W)
+        X = torch.empty_like(x)
+        for _ in range(args.steps):
+            F.ntt2d(P, x, out=X)
+    else:
+        dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
+        xA_h, xB_h = FI.shares(ls, c.cid)
+        ks, es, ss = FI.seeds(c.cid)
+        t_hat = F.keygen(P, ks)
+        Phat = F.filter_prepare(P, L, dev(FI.weights(ls, c.cid), np.int8))
+        Mhat, sB = F.mask_prepare(P, L, ss)
+        xA, xB = dev(xA_h, np.int32), dev(xB_h, np.int32)
+        for _ in range(args.steps):
+            ct = F.encrypt_constants(P, L, t_hat, es)
+            A, R = F.encode_share(P, L, xA), F.encode_share(P, L, xB)
+            F.intt2d(P, sB.view(ls.B, ls.Co, ls.H, ls.W))
+            F.decrypt_share(P, L, t_hat, F.homconv_sum(P, L, ct, A, R, Phat, Mhat))
+    torch.cuda.synchronize()
+    print("ran %d x %s" % (args.steps, args.kernel_only))
+    P.close()
+
+
 def run_gpu(args, rank, local_rank, world):
     import torch
 
@@ -670,6 +723,9 @@ def main():
     ap.add_argument("--serve-keys", type=int, default=64)
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--kernel-only", choices=["homconv", "ntt2d", "step"],
+                    help="only run --steps launches of one part of the path (for profiler captures)")
+    ap.add_argument("--planes", type=int, default=65536, help="planes for --kernel-only ntt2d")
     args = ap.parse_args()
     rank, local_rank, world = dist_env()
     if world > 1:
@@ -678,7 +734,9 @@ def main():
         backend = "nccl" if args.impl == "fdsc" else "gloo"
         dist.init_process_group(backend)
     try:
-        if args.impl == "reference":
+        if args.kernel_only:
+            run_kernel_only(args)
+        elif args.impl == "reference":
             run_reference(args, rank, world)
         else:
             run_gpu(args, rank, local_rank, world)
