@@ -295,6 +295,65 @@ def run_batched(F, flush, sleep_cycles, args):
     return out
 
 
+# the appendix network (MiniONN's CIFAR-10 network, Fig. 13 there): its six
+# convolution layers, (Ci, Co, H, filter, 2x2 pooling after); the
+# fully-connected layer and the activations are not part of the path
+APPENDIX_CONVS = [(3, 64, 32, 3, False), (64, 64, 32, 3, True), (64, 64, 16, 3, False), (64, 64, 16, 3, True),
+                  (64, 64, 8, 3, False), (64, 64, 8, 1, False)]
+
+
+def run_chain(F, flush, sleep_cycles, args):
+    """One inference of the appendix network's convolution stack (batch 1)
+    as a chained plan: each layer reads the shares the previous one wrote,
+    sum-pooled where the network pools (activations left to their own
+    protocol).  L2 flushed before every timed launch."""
+    import torch
+
+    P = F.Params(2048, 65537, max_T=64)
+    g = np.random.default_rng(FI.SEED_BASE + 7)
+    dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
+    Ci0, H0 = APPENDIX_CONVS[0][0], APPENDIX_CONVS[0][2]
+    inA = dev(g.integers(0, 65537, (1, Ci0, H0, H0)), np.int32)
+    inB = dev(g.integers(0, 65537, (1, Ci0, H0, H0)), np.int32)
+    specs = []
+    for i, (Ci, Co, H, fh, pool) in enumerate(APPENDIX_CONVS):
+        d = dict(params=P, layer=F.LayerSpec(1, Ci, Co, H, H, 0, 0), w=dev(g.integers(-8, 8, (Co, Ci, fh, fh)), np.int8),
+                 t_hat=F.keygen(P, 700 + i), enc_seed=710 + i, mask_seed=720 + i, xA=inA, xB=inB,
+                 yA=torch.empty((1, Co, H, H), dtype=torch.int32, device="cuda"),
+                 yB=torch.empty((1, Co, H, H), dtype=torch.int32, device="cuda"))
+        if pool:
+            d["pA"] = torch.empty((1, Co, H // 2, H // 2), dtype=torch.int32, device="cuda")
+            d["pB"] = torch.empty_like(d["pA"])
+        inA, inB = (d["pA"], d["pB"]) if pool else (d["yA"], d["yB"])
+        specs.append(d)
+    plan = F.Plan(specs, tune=True, chain=True)
+    reps = max(5, min(args.steps // 10, 200))
+    for _ in range(3):
+        flush.fill_(1)
+        plan.launch()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda._sleep(sleep_cycles)
+    for i, (a, b) in enumerate(ev):
+        flush.fill_(i & 0xFF)
+        a.record()
+        plan.launch()
+        b.record()
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    info = [plan.info(i) for i in range(len(specs))]
+    plan.close()
+    P.close()
+    return {"network": "appendix network (MiniONN CIFAR-10, Fig. 13 there): 6 convolution layers, 2 sum poolings",
+            "layers": ["%dx%dx%d->%d %dx%d%s" % (H, H, Ci, Co, fh, fh, " +pool" if pl else "")
+                       for Ci, Co, H, fh, pl in APPENDIX_CONVS],
+            "inference_us_p50": float(np.percentile(ms, 50)) * 1e3, "inference_us_p99": float(np.percentile(ms, 99)) * 1e3,
+            "conv_layers_per_s": len(APPENDIX_CONVS) / (float(np.mean(ms)) * 1e-3),
+            "packing": [{"g_c": x.g_c, "homconv_variant": x.homconv_variant} for x in info],
+            "launches": reps, "l2": "flushed before every timed launch",
+            "path": "one chained plan (FDSC_PLAN_CHAIN), one graph launch per inference"}
+
+
 def run_serving(F, args):
     """The served mix: Poisson arrivals (mean 2000 requests/s) of single-image
     requests drawn uniformly from three layer types, each from one of a pool
@@ -642,6 +701,7 @@ def run_gpu(args, rank, local_rank, world):
                              xB_h[0], args.e2e_requests)
     flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.int32, device="cuda")
     batched = None if args.skip_batched else run_batched(F, flush, sleep_cycles, args)
+    chain = None if args.skip_batched else run_chain(F, flush, sleep_cycles, args)
     serving = None if args.skip_serving else run_serving(F, args)
 
     local_sec = total_ms / 1e3
@@ -697,6 +757,7 @@ def run_gpu(args, rank, local_rank, world):
                 "path": "fdsc_server_submit/wait (C ABI) with host buffers, closed loop of single-image requests; "
                         "copies in and out inside the timed region; host wall clock"},
         "batched": batched,
+        "chain": chain,
         "serving": serving,
         "ntt2d_sweep": sweep,
         "gpu_launches": LAUNCHES_PER_STEP * (args.steps + len(step_ms)) + 8 * n_unfused + 2 * hc_reps * R

@@ -128,6 +128,15 @@ int fdsc_ntt2d(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_t* x, 
 int fdsc_intt2d(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_t* X, uint32_t* x,
                 uint64_t planes, void* stream);
 
+/* The average-pooling layers of the paper's appendix networks, on a share:
+ * y[pl][i][j] = sum_{a,b < 2} x[pl][2i+a][2j+b] mod p (H, W even; x in
+ * [0, p)).  It is linear mod p, so each party pools its own share and the
+ * pooled shares add up to the pooled value; the 1/4 of the average is left
+ * to the next layer's weights (a sum pool).  x: [planes][H][W], y:
+ * [planes][H/2][W/2], both device, not overlapping. */
+int fdsc_pool2x2_sum(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_t* x, uint32_t* y,
+                     uint64_t planes, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Setup                                                                   */
 /* ---------------------------------------------------------------------- */
@@ -256,6 +265,9 @@ typedef struct {
     const uint32_t* xB;         /* device [B][Ci][H][W]: Bob's share (HomRec)  */
     uint32_t* yA;               /* device [B][Co][H][W]: Alice's output share  */
     uint32_t* yB;               /* device [B][Co][H][W]: Bob's output share    */
+    uint32_t* pA;               /* NULL, or device [B][Co][H/2][W/2]: yA after
+                                   fdsc_pool2x2_sum (H, W even)                */
+    uint32_t* pB;               /* NULL, or the same for yB                    */
 } fdsc_plan_layer;
 
 typedef struct {
@@ -267,7 +279,13 @@ typedef struct {
     double tuned_step_us;       /* the chosen candidate's median step time     */
 } fdsc_plan_layer_info;
 
-enum { FDSC_PLAN_TUNE = 1 };    /* time packings x HomConv variants, keep the fastest */
+enum {
+    FDSC_PLAN_TUNE = 1,         /* time packings x HomConv variants, keep the fastest */
+    FDSC_PLAN_CHAIN = 2         /* layer i starts once layer i-1 (and its pooling) has
+                                   finished, so it may read the shares layer i-1 wrote:
+                                   a network's convolution stack (Fig. 2 lines 7-13,
+                                   with the activation protocol left to the caller) */
+};
 
 typedef struct fdsc_plan fdsc_plan;
 

@@ -767,6 +767,19 @@ void orc_decrypt(const orc_params* P, const orc_layer* L, const u64* t_hat, cons
  * cyclic 2D convolution of the summed shares with the filters, summed over
  * input channels, mod p:
  *   y[b][co][i][j] = sum_ci sum_{a<fh, c<fw} w[co][ci][a][c] x[b][ci][(i-a) mod H][(j-c) mod W]. */
+/* Appendix, "Average Pooling" layers: each 2x2 window of a share summed mod p
+   (the 1/4 of the average belongs to the next layer's weights). */
+void orc_pool2x2_sum(u32 p, u64 planes, u32 H, u32 W, const u32* x, u32* y) {
+    for (u64 pl = 0; pl < planes; pl++)
+        for (u32 i = 0; i < H / 2; i++)
+            for (u32 j = 0; j < W / 2; j++) {
+                u64 acc = 0;
+                for (u32 a = 0; a < 2; a++)
+                    for (u32 c = 0; c < 2; c++) acc += x[(pl * H + 2 * i + a) * W + 2 * j + c];
+                y[(pl * (H / 2) + i) * (W / 2) + j] = (u32)(acc % p);
+            }
+}
+
 void orc_conv_plain(u32 p, u32 B, u32 Ci, u32 Co, u32 H, u32 W, const u32* x, const int8_t* w, u32 fh,
                     u32 fw, u32* y) {
     for (u32 b = 0; b < B; b++)

@@ -101,6 +101,10 @@ void orc_decrypt(const orc_params* P, const orc_layer* L, const uint64_t* t_hat,
 void orc_decrypt_raw(const orc_params* P, const uint64_t* t_hat, const uint64_t* ct,
                      uint32_t* m, int64_t* noise);
 
+/* the appendix networks' average pooling on a share, as a 2x2 sum pool mod p:
+   y[pl][i][j] = sum_{a,b<2} x[pl][2i+a][2j+b] mod p */
+void orc_pool2x2_sum(uint32_t p, uint64_t planes, uint32_t H, uint32_t W, const uint32_t* x, uint32_t* y);
+
 /* the result the protocol must reproduce: cyclic 2D convolution mod p */
 void orc_conv_plain(uint32_t p, uint32_t B, uint32_t Ci, uint32_t Co, uint32_t H, uint32_t W,
                     const uint32_t* x, const int8_t* w, uint32_t fh, uint32_t fw, uint32_t* y);

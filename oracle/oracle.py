@@ -89,6 +89,7 @@ _SIGS = {
     "orc_decrypt": (None, [_P, _L, _u64p, _u64p, _u32p, _i64p]),
     "orc_decrypt_raw": (None, [_P, _u64p, _u64p, _u32p, _i64p]),
     "orc_conv_plain": (None, [C.c_uint32] * 6 + [_u32p, _i8p, C.c_uint32, C.c_uint32, _u32p]),
+    "orc_pool2x2_sum": (None, [C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32, _u32p, _u32p]),
 }
 
 
@@ -310,6 +311,16 @@ def conv_plain(p, x, w):
     assert Ci == Ci2
     y = np.empty((B, Co, H, W), np.uint32)
     lib().orc_conv_plain(p, B, Ci, Co, H, W, _ptr(x, _u32p), _ptr(w, _i8p), fh, fw, _ptr(y, _u32p))
+    return y
+
+
+def pool2x2_sum(p, x):
+    """Appendix average pooling on a share (2x2 sum mod p): [..., H, W] -> [..., H/2, W/2]."""
+    x = _u32(x)
+    H, W = x.shape[-2:]
+    planes = x.size // (H * W)
+    y = np.empty(x.shape[:-2] + (H // 2, W // 2), np.uint32)
+    lib().orc_pool2x2_sum(p, planes, H, W, _ptr(x, _u32p), _ptr(y, _u32p))
     return y
 
 

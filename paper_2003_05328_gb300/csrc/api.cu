@@ -59,6 +59,17 @@ extern "C" int fdsc_intt2d(const fdsc_params* P, uint32_t H, uint32_t W, const u
     return ntt2d_common(P, H, W, X, x, planes, stream, true);
 }
 
+extern "C" int fdsc_pool2x2_sum(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_t* x, uint32_t* y,
+                                uint64_t planes, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (H < 2 || W < 2 || (H & 1) || (W & 1)) return fdsc_set_error(FDSC_ERR_ARG, "pooling needs even H, W >= 2");
+    if ((rc = check_ptr(x, "x")) || (rc = check_ptr(y, "y"))) return rc;
+    const u64 in_bytes = planes * H * W * 4, out_bytes = planes * (H / 2) * (W / 2) * 4;
+    if (overlap(x, in_bytes, y, out_bytes)) return fdsc_set_error(FDSC_ERR_ARG, "x and y overlap");
+    return launched(launch_pool2x2(P->dev, H, W, x, y, planes, (cudaStream_t)stream), "pool2x2_sum");
+}
+
 extern "C" int fdsc_keygen(const fdsc_params* P, uint64_t seed, uint64_t* t_hat, void* stream) {
     int rc = check_params(P);
     if (rc || (rc = check_ptr(t_hat, "t_hat"))) return rc;

@@ -225,3 +225,29 @@ cudaError_t launch_ntt2d(const DevParams& P, u32 H, u32 W, const u32* x, u32* X,
     }
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------- 2 x 2 sum pooling of a share
+__global__ void __launch_bounds__(256) pool2x2_kernel(u32 p, u32 H, u32 W, const u32* __restrict__ x,
+                                                      u32* __restrict__ y, u64 planes) {
+    griddep_release();
+    griddep_wait();
+    const u32 Wo = W / 2, HWo = (H / 2) * Wo;
+    const u64 total = planes * HWo;
+    for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (u64)gridDim.x * blockDim.x) {
+        const u64 pl = e / HWo;
+        const u32 r = (u32)(e % HWo) / Wo, c = (u32)(e % HWo) % Wo;
+        const u32* src = x + pl * H * W + (u64)(2 * r) * W + 2 * c;
+        u32 a = src[0] + src[1], b = src[W] + src[W + 1];  // each < 2p
+        a = a >= p ? a - p : a;
+        b = b >= p ? b - p : b;
+        a += b;
+        y[e] = a >= p ? a - p : a;
+    }
+}
+
+cudaError_t launch_pool2x2(const DevParams& P, u32 H, u32 W, const u32* x, u32* y, u64 planes, cudaStream_t s) {
+    const u64 total = planes * (H / 2) * (W / 2);
+    if (total == 0) return cudaSuccess;
+    const u64 blocks = (total + 255) / 256, cap = 152ull * 8;
+    return launch_online(pool2x2_kernel, (u32)(blocks < cap ? blocks : cap), 256, 0, s, P.p, H, W, x, y, planes);
+}

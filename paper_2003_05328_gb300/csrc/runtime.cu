@@ -130,6 +130,7 @@ int plan_record_layer(PlanLayer& pl, cudaStream_t* st, cudaEvent_t* ev) {
         RT_TRY(launch_share(P, D, sp.xA, pl.A, false, st[1]));
         RT_TRY(launch_share(P, D, sp.xB, pl.R, false, st[2]));
         RT_TRY(launch_ntt2d(P, D.H, D.W, pl.sB, sp.yB, planes_out, true, st[3]));
+        if (sp.pB) RT_TRY(launch_pool2x2(P, D.H, D.W, sp.yB, sp.pB, planes_out, st[3]));
         RT_TRY(cudaEventRecord(ev[1], st[1]));
         RT_TRY(cudaEventRecord(ev[2], st[2]));
         RT_TRY(cudaStreamWaitEvent(st[0], ev[1], 0));
@@ -142,6 +143,7 @@ int plan_record_layer(PlanLayer& pl, cudaStream_t* st, cudaEvent_t* ev) {
         RT_TRY(launch_encrypt(P, D, sp.t_hat, pl.X, sp.enc_seed, pl.ct, st[0]));
         RT_TRY(launch_ntt2d(P, D.H, D.W, sp.xB, pl.XB, planes_in, false, st[1]));
         RT_TRY(launch_ntt2d(P, D.H, D.W, pl.sB, sp.yB, planes_out, true, st[3]));
+        if (sp.pB) RT_TRY(launch_pool2x2(P, D.H, D.W, sp.yB, sp.pB, planes_out, st[3]));
         RT_TRY(cudaEventRecord(ev[1], st[1]));
         RT_TRY(cudaStreamWaitEvent(st[0], ev[1], 0));
         RT_TRY(launch_homrec(P, D, pl.XB, pl.ct, st[0]));
@@ -149,6 +151,7 @@ int plan_record_layer(PlanLayer& pl, cudaStream_t* st, cudaEvent_t* ev) {
         RT_TRY(launch_decrypt(P, D, sp.t_hat, pl.ct_out, pl.SA, st[0]));
         RT_TRY(launch_ntt2d(P, D.H, D.W, pl.SA, sp.yA, planes_out, true, st[0]));
     }
+    if (sp.pA) RT_TRY(launch_pool2x2(P, D.H, D.W, sp.yA, sp.pA, planes_out, st[0]));
     RT_TRY(cudaEventRecord(ev[3], st[3]));
     RT_TRY(cudaStreamWaitEvent(st[0], ev[3], 0));
     return FDSC_OK;
@@ -233,8 +236,11 @@ extern "C" int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, u
             return fail(fdsc_set_error(FDSC_ERR_ARG, "layer %u: params missing or on another device", i));
         if (!sp.w || !sp.t_hat || !sp.xA || !sp.xB || !sp.yA || !sp.yB)
             return fail(fdsc_set_error(FDSC_ERR_ARG, "layer %u: NULL buffer", i));
-        if (((uintptr_t)sp.t_hat | (uintptr_t)sp.xA | (uintptr_t)sp.xB | (uintptr_t)sp.yA | (uintptr_t)sp.yB) & 15)
+        if (((uintptr_t)sp.t_hat | (uintptr_t)sp.xA | (uintptr_t)sp.xB | (uintptr_t)sp.yA | (uintptr_t)sp.yB |
+             (uintptr_t)sp.pA | (uintptr_t)sp.pB) & 15)
             return fail(fdsc_set_error(FDSC_ERR_ARG, "layer %u: buffers must be 16-byte aligned", i));
+        if ((sp.pA || sp.pB) && ((sp.layer.H & 1) || (sp.layer.W & 1)))
+            return fail(fdsc_set_error(FDSC_ERR_ARG, "layer %u: pooling needs even H and W", i));
         const fdsc_params_info& I = sp.params->info;
         pl.L = sp.layer;
         if (pl.L.g_c == 0 || pl.L.g_b == 0) default_pack(I, pl.L, &pl.L.g_c, &pl.L.g_b);
@@ -305,9 +311,21 @@ extern "C" int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, u
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return fail(fdsc_set_error(FDSC_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e)));
     cudaEventRecord(fork, cap);
+    const bool chain = (flags & FDSC_PLAN_CHAIN) != 0;
     for (uint32_t i = 0; i < count && rc == FDSC_OK; i++) {
         cudaStream_t* st = &plan->streams[4 * (size_t)i];
-        if (i > 0) cudaStreamWaitEvent(st[0], fork, 0);
+        if (i > 0 && chain) {  // after the previous layer, whose main stream has joined its others
+            cudaEvent_t prev;
+            if (cudaEventCreateWithFlags(&prev, cudaEventDisableTiming) != cudaSuccess) {
+                rc = fdsc_set_error(FDSC_ERR_CUDA, "event creation failed");
+                break;
+            }
+            plan->events.push_back(prev);
+            cudaEventRecord(prev, plan->streams[4 * (size_t)(i - 1)]);
+            cudaStreamWaitEvent(st[0], prev, 0);
+        } else if (i > 0) {
+            cudaStreamWaitEvent(st[0], fork, 0);
+        }
         rc = plan_record_layer(plan->layers[i], st, &plan->events[4 * (size_t)i]);
     }
     for (uint32_t i = 1; i < count && rc == FDSC_OK; i++) {

@@ -62,6 +62,7 @@ _SIGS = {
     "fdsc_layout_query": (C.c_int, [C.c_uint32, C.c_uint32, _PL, _PO]),
     "fdsc_ntt2d": (C.c_int, [_vp, C.c_uint32, C.c_uint32, _vp, _vp, C.c_uint64, _vp]),
     "fdsc_intt2d": (C.c_int, [_vp, C.c_uint32, C.c_uint32, _vp, _vp, C.c_uint64, _vp]),
+    "fdsc_pool2x2_sum": (C.c_int, [_vp, C.c_uint32, C.c_uint32, _vp, _vp, C.c_uint64, _vp]),
     "fdsc_keygen": (C.c_int, [_vp, C.c_uint64, _vp, _vp]),
     "fdsc_filter_prepare": (C.c_int, [_vp, _PL, _vp, C.c_uint32, C.c_uint32, _vp, _vp]),
     "fdsc_mask_prepare": (C.c_int, [_vp, _PL, C.c_uint64, _vp, _vp, _vp]),
@@ -225,6 +226,17 @@ def ntt2d(P: Params, x: torch.Tensor, out=None, stream=None) -> torch.Tensor:
 
 def intt2d(P: Params, X: torch.Tensor, out=None, stream=None) -> torch.Tensor:
     return _ntt2d("fdsc_intt2d", P, X, out, stream)
+
+
+def pool2x2_sum(P: Params, x: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """2 x 2 sum pooling mod p of a share [..., H, W] -> [..., H/2, W/2]."""
+    H, W = x.shape[-2], x.shape[-1]
+    planes = x.numel() // (H * W)
+    if out is None:
+        out = torch.empty(x.shape[:-2] + (H // 2, W // 2), dtype=torch.int32, device="cuda")
+    _call("fdsc_pool2x2_sum", P.handle, H, W, _ptr(x, torch.int32, x.numel(), "x"),
+          _ptr(out, torch.int32, planes * (H // 2) * (W // 2), "y"), planes, _stream(stream))
+    return out
 
 
 # ---------------------------------------------------------------- setup
@@ -403,7 +415,7 @@ def decrypt_share_multi(P: Params, L: LayerSpec, t_hats, ct, key_stride=None, ou
 class PlanLayerC(C.Structure):
     _fields_ = [("params", _vp), ("layer", Layer), ("fh", C.c_uint32), ("fw", C.c_uint32), ("w", _vp),
                 ("t_hat", _vp), ("enc_seed", C.c_uint64), ("mask_seed", C.c_uint64), ("xA", _vp), ("xB", _vp),
-                ("yA", _vp), ("yB", _vp)]
+                ("yA", _vp), ("yB", _vp), ("pA", _vp), ("pB", _vp)]
 
 
 class PlanLayerInfo(C.Structure):
@@ -412,6 +424,7 @@ class PlanLayerInfo(C.Structure):
 
 
 PLAN_TUNE = 1
+PLAN_CHAIN = 2
 
 
 class Plan:
@@ -421,7 +434,7 @@ class Plan:
     choose), w (int8 [Co][Ci][fh][fw]), t_hat, enc_seed, mask_seed, xA, xB, yA,
     yB (device tensors)."""
 
-    def __init__(self, layers, tune=False, stream=None):
+    def __init__(self, layers, tune=False, stream=None, chain=False):
         arr = (PlanLayerC * len(layers))()
         self._keep = layers
         for i, d in enumerate(layers):
@@ -429,10 +442,12 @@ class Plan:
             Co, Ci, fh, fw = w.shape
             arr[i] = PlanLayerC(d["params"].handle, L.c(), fh, fw, _ptr(w, torch.int8, w.numel(), "w"),
                                 _ptr(d["t_hat"], torch.int64, d["params"].n, "t_hat"), d["enc_seed"], d["mask_seed"],
-                                d["xA"].data_ptr(), d["xB"].data_ptr(), d["yA"].data_ptr(), d["yB"].data_ptr())
+                                d["xA"].data_ptr(), d["xB"].data_ptr(), d["yA"].data_ptr(), d["yB"].data_ptr(),
+                                d["pA"].data_ptr() if d.get("pA") is not None else None,
+                                d["pB"].data_ptr() if d.get("pB") is not None else None)
         h = _vp()
-        _call("fdsc_plan_create", C.addressof(arr), len(layers), PLAN_TUNE if tune else 0, _stream(stream),
-              C.byref(h))
+        flags = (PLAN_TUNE if tune else 0) | (PLAN_CHAIN if chain else 0)
+        _call("fdsc_plan_create", C.addressof(arr), len(layers), flags, _stream(stream), C.byref(h))
         self.handle = h
 
     def launch(self, stream=None):

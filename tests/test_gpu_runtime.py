@@ -182,3 +182,60 @@ def test_launch_overlap_gives_identical_results(F):
         F.set_launch_overlap(prev)
     for P in params:
         P.close()
+
+
+def test_pool2x2_sum_matches_oracle(F):
+    P = F.Params(1024, 65537, max_T=8)
+    g = np.random.default_rng(21)
+    x = g.integers(0, 65537, (3, 5, 16, 12)).astype(np.uint32)
+    y = F.pool2x2_sum(P, dev(x, np.int32))
+    torch.cuda.synchronize()
+    assert np.array_equal(u32(y).reshape(3, 5, 8, 6), O.pool2x2_sum(65537, x))
+    with pytest.raises(F.FdscError):
+        F.pool2x2_sum(P, dev(np.zeros((1, 3, 5), np.uint32), np.int32))  # odd plane
+    P.close()
+
+
+def test_chained_plan_of_a_network_matches_oracle(F):
+    """The appendix network's pattern at reduced width: conv, sum pooling,
+    conv, 1x1 conv, run as one chained plan (each layer reads the shares the
+    previous one wrote) and compared with the oracle run layer by layer."""
+    p, n = 65537, 1024
+    P = F.Params(n, p, max_T=64)
+    OP = O.params(n, p)
+    g = np.random.default_rng(31)
+    shapes = [(3, 8, 16, 3, True), (8, 8, 8, 3, False), (8, 4, 8, 1, False)]  # (Ci, Co, H, fh, pool after)
+    xA = g.integers(0, p, (1, 3, 16, 16)).astype(np.uint32)
+    xB = g.integers(0, p, (1, 3, 16, 16)).astype(np.uint32)
+    specs, ws, seeds = [], [], []
+    inA, inB = dev(xA, np.int32), dev(xB, np.int32)
+    for i, (Ci, Co, H, fh, pool) in enumerate(shapes):
+        w = g.integers(-8, 8, (Co, Ci, fh, fh)).astype(np.int8)
+        ks, es, ss = 40 + i, 50 + i, 60 + i
+        d = dict(params=P, layer=F.LayerSpec(1, Ci, Co, H, H, 0, 0), w=dev(w, np.int8), t_hat=F.keygen(P, ks),
+                 enc_seed=es, mask_seed=ss, xA=inA, xB=inB,
+                 yA=torch.zeros((1, Co, H, H), dtype=torch.int32, device="cuda"),
+                 yB=torch.zeros((1, Co, H, H), dtype=torch.int32, device="cuda"))
+        if pool:
+            d["pA"] = torch.zeros((1, Co, H // 2, H // 2), dtype=torch.int32, device="cuda")
+            d["pB"] = torch.zeros_like(d["pA"])
+        inA, inB = (d["pA"], d["pB"]) if pool else (d["yA"], d["yB"])
+        specs.append(d)
+        ws.append(w)
+        seeds.append((ks, es, ss))
+    plan = F.Plan(specs, chain=True)
+    for _ in range(2):
+        plan.launch()
+        torch.cuda.synchronize()
+        a, b = xA, xB
+        for (Ci, Co, H, fh, pool), w, (ks, es, ss), d in zip(shapes, ws, seeds, specs):
+            ref = O.round_trip(OP, O.layer(OP, 1, Ci, Co, H, H), a, b, w, ks, es, ss)
+            assert np.array_equal(u32(d["yA"]).reshape(ref["yA"].shape), ref["yA"])
+            assert np.array_equal(u32(d["yB"]).reshape(ref["yB"].shape), ref["yB"])
+            a, b = ref["yA"], ref["yB"]
+            if pool:
+                a, b = O.pool2x2_sum(p, a), O.pool2x2_sum(p, b)
+                assert np.array_equal(u32(d["pA"]).reshape(a.shape), a)
+                assert np.array_equal(u32(d["pB"]).reshape(b.shape), b)
+    plan.close()
+    P.close()

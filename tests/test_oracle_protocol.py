@@ -186,3 +186,56 @@ def test_config_round_trip(cfg):
     y = O.conv_plain(ls.p, (xA.astype(np.int64) + xB) % ls.p, w)
     assert np.array_equal((out["yA"].astype(np.int64) + out["yB"]) % ls.p, y)
     assert np.log2(out["noise"].max()) < O.noise_bound_log2(P, L.T) < np.log2(P.delta / 2)
+
+
+def test_pool2x2_sum_pins():
+    """The appendix's average pooling on shares (a 2x2 sum mod p): a delta
+    goes to a delta, every window sum is kept, and pooling commutes with
+    adding the shares (so each party pools its own)."""
+    p = 65537
+    x = np.zeros((1, 8, 6), np.uint32)
+    x[0, 5, 2] = 7
+    y = O.pool2x2_sum(p, x)
+    assert y.shape == (1, 4, 3) and y[0, 2, 1] == 7 and y.sum() == 7
+    g = np.random.default_rng(4)
+    a = g.integers(0, p, (3, 2, 16, 16)).astype(np.uint32)
+    b = g.integers(0, p, (3, 2, 16, 16)).astype(np.uint32)
+    ya, yb = O.pool2x2_sum(p, a), O.pool2x2_sum(p, b)
+    assert int(ya.astype(object).sum()) % p == int(a.astype(object).sum()) % p
+    both = O.pool2x2_sum(p, ((a.astype(np.int64) + b) % p).astype(np.uint32))
+    assert np.array_equal((ya.astype(np.int64) + yb) % p, both)
+    win = a[1, 1, 6:8, 10:12].astype(np.int64).sum() % p  # one window by hand
+    assert ya[1, 1, 3, 5] == win
+
+
+def test_two_layer_chain_with_pooling_reconstructs_the_network():
+    """A chain of FDSC layers (Fig. 2 lines 7-13, the activation protocol
+    left out): layer 2 takes layer 1's output shares after sum pooling; the
+    final shares add up to conv2(pool(conv1(x))) computed directly."""
+    p, n = 65537, 1024
+    g = np.random.default_rng(9)
+    P = O.params(n, p)
+    xA = g.integers(0, p, (1, 3, 16, 16)).astype(np.uint32)
+    xB = g.integers(0, p, (1, 3, 16, 16)).astype(np.uint32)
+    w1 = g.integers(-8, 8, (4, 3, 3, 3)).astype(np.int8)
+    w2 = g.integers(-8, 8, (2, 4, 3, 3)).astype(np.int8)
+    o1 = O.round_trip(P, O.layer(P, 1, 3, 4, 16, 16), xA, xB, w1, 1, 2, 3)
+    pA, pB = O.pool2x2_sum(p, o1["yA"]), O.pool2x2_sum(p, o1["yB"])
+    o2 = O.round_trip(P, O.layer(P, 1, 4, 2, 8, 8), pA, pB, w2, 4, 5, 6)
+    x = (xA.astype(np.int64) + xB) % p
+    h1 = np.zeros((1, 4, 16, 16), dtype=object)  # brute-force cyclic convolution
+    for co in range(4):
+        for ci in range(3):
+            for a in range(3):
+                for c in range(3):
+                    h1[0, co] += int(w1[co, ci, a, c]) * np.roll(np.roll(x[0, ci].astype(object), a, 0), c, 1)
+    h1 = h1 % p
+    pooled = (h1[:, :, 0::2, 0::2] + h1[:, :, 1::2, 0::2] + h1[:, :, 0::2, 1::2] + h1[:, :, 1::2, 1::2]) % p
+    h2 = np.zeros((1, 2, 8, 8), dtype=object)
+    for co in range(2):
+        for ci in range(4):
+            for a in range(3):
+                for c in range(3):
+                    h2[0, co] += int(w2[co, ci, a, c]) * np.roll(np.roll(pooled[0, ci], a, 0), c, 1)
+    h2 = (h2 % p).astype(np.int64)
+    assert np.array_equal((o2["yA"].astype(np.int64) + o2["yB"]) % p, h2)
