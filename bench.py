@@ -573,6 +573,7 @@ def run_gpu(args, rank, local_rank, world):
         d["yB"] = torch.empty_like(d["yA"])
         d["A_msg"] = torch.empty(lay.n_in * ls.n, dtype=torch.int64, device="cuda")
         d["A_rec"] = torch.empty_like(d["A_msg"])
+        d["c1"] = F.encrypt_constants_seeded(P, L, d["t_hat"], es)  # the seeded form: c1 alone
         insts.append(d)
     LAUNCHES_PER_STEP = 6
     side = [torch.cuda.Stream() for _ in range(3)]
@@ -612,6 +613,9 @@ def run_gpu(args, rank, local_rank, world):
     def homconv_only(d):
         F.homconv_sum(P, L, d["ct"], d["A_msg"], d["A_rec"], d["Phat"], d["Mhat"], out=d["ct_out"])
 
+    def homconv_seeded_only(d):
+        F.homconv_seeded(P, L, d["es"], d["c1"], d["A_msg"], d["A_rec"], d["Phat"], d["Mhat"], out=d["ct_out"])
+
     for _ in range(max(1, args.warmup)):
         for d in insts:
             step(d)
@@ -635,6 +639,7 @@ def run_gpu(args, rank, local_rank, world):
     # HomConv alone: one graph of R launches, one per instance, back to back
     g_hc = capture(lambda: [homconv_only(d) for d in insts])
     g_hc_warm = capture(lambda: [homconv_only(insts[0]) for _ in insts])
+    g_hc_seeded = capture(lambda: [homconv_seeded_only(d) for d in insts])
     for _ in range(args.warmup):
         for gr in g_step:
             gr.replay()
@@ -688,8 +693,11 @@ def run_gpu(args, rank, local_rank, world):
     ev_h = back_to_back([g_hc], hc_reps)
     ev_w = back_to_back([g_hc_warm], hc_reps)
     torch.cuda.synchronize()
+    ev_s = back_to_back([g_hc_seeded], hc_reps)
+    torch.cuda.synchronize()
     hc_avg = ev_h[0].elapsed_time(ev_h[-1]) / (hc_reps * R)
     hc_warm_ms = ev_w[0].elapsed_time(ev_w[-1]) / (hc_reps * R)
+    hc_seeded_ms = ev_s[0].elapsed_time(ev_s[-1]) / (hc_reps * R)
 
     # NTT2D over a batch sweep of 32x32 planes (64 per image)
     sweep = ntt2d_sweep(F, P, ls, back_to_back, args)
@@ -742,6 +750,8 @@ def run_gpu(args, rank, local_rank, world):
         "homconv_layers_per_s": ls.B / (hc_avg * 1e-3),
         "homconv_mac_per_s": macs / (hc_avg * 1e-3),
         "homconv_warm_us": hc_warm_ms * 1e3,
+        "homconv_seeded": {"us": hc_seeded_ms * 1e3, "alg_bytes_per_launch": alg_bytes - 8 * lay.n_in * ls.n,
+                           "note": "seeded input ciphertexts: c1 read, c0 drawn again from the encryption seed"},
         "useful_macs_per_layer": useful_macs // ls.B,
         "step_ms_p50": float(np.percentile(step_ms, 50)), "step_ms_p99": float(np.percentile(step_ms, 99)),
         "step_ms_distribution": "%d steps with an event at every boundary" % len(step_ms),
@@ -760,7 +770,7 @@ def run_gpu(args, rank, local_rank, world):
         "chain": chain,
         "serving": serving,
         "ntt2d_sweep": sweep,
-        "gpu_launches": LAUNCHES_PER_STEP * (args.steps + len(step_ms)) + 8 * n_unfused + 2 * hc_reps * R
+        "gpu_launches": LAUNCHES_PER_STEP * (args.steps + len(step_ms)) + 8 * n_unfused + 3 * hc_reps * R
                         + sum(pt["launches"] for pt in sweep["points"]),
         "homconv_variant": args.homconv_variant,
         "clocks": clk,

@@ -160,6 +160,21 @@ int fdsc_filter_prepare(const fdsc_params* P, const fdsc_layer* L, const int8_t*
 int fdsc_mask_prepare(const fdsc_params* P, const fdsc_layer* L, uint64_t seed, uint64_t* M_hat,
                       uint32_t* sB_hat, void* stream);
 
+/* HomShare with noise flooding for circuit privacy (not in the paper, whose
+ * HomShare leaves the filter-dependent noise of HomConv in Bob's output
+ * ciphertext): as fdsc_mask_prepare, but every coefficient of the mask
+ * plaintext Delta m_s also carries an error drawn from `seed` uniformly in
+ * [-2^flood_bits, 2^flood_bits), which c1 - M_hat then carries too.
+ * Decryption rounds it away, so the final shares are those of
+ * fdsc_mask_prepare with the same seed.  FDSC_ERR_NOISE when the layer's
+ * noise bound (T input ciphertexts) plus 2^flood_bits fails; 0 gives
+ * fdsc_mask_prepare's words. */
+int fdsc_mask_prepare_flooded(const fdsc_params* P, const fdsc_layer* L, uint64_t seed, uint32_t flood_bits,
+                              uint64_t* M_hat, uint32_t* sB_hat, void* stream);
+/* The largest flood_bits the noise bound admits for T input ciphertexts at
+ * (n, p); FDSC_ERR_NOISE if T alone breaks it. */
+int fdsc_flood_bits_max(uint32_t n, uint32_t p, uint32_t T, uint32_t* out);
+
 /* ---------------------------------------------------------------------- */
 /* Online path                                                             */
 /* ---------------------------------------------------------------------- */
@@ -218,6 +233,21 @@ int fdsc_homconv_sum(const fdsc_params* P, const fdsc_layer* L, const uint64_t* 
                      const uint64_t* A2, const uint64_t* P_hat, const uint64_t* M_hat, uint64_t* ct_out,
                      void* stream);
 
+/* Seeded ciphertexts.  In Eq. 1 `a` is uniform and public, so a fresh
+ * ciphertext can travel as its encryption seed and c1 alone: half the
+ * client-to-server bytes, and half the input words HomConv reads.
+ * fdsc_encrypt_constants_seeded writes the c1 of fdsc_encrypt_constants,
+ * c1: uint64 [n_in][n] (the message and HomRec plaintexts are then added as
+ * A1 / A2 below, or into c1).  fdsc_homconv_seeded is fdsc_homconv_sum with
+ * c0 = -a drawn again from `seed` (the encryption's) instead of read: the
+ * same output words as fdsc_homconv_sum on the full ciphertexts.  Needs
+ * T <= 256 (FDSC_ERR_UNSUPPORTED otherwise). */
+int fdsc_encrypt_constants_seeded(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, uint64_t seed,
+                                  uint64_t* c1, void* stream);
+int fdsc_homconv_seeded(const fdsc_params* P, const fdsc_layer* L, uint64_t seed, const uint64_t* c1,
+                        const uint64_t* A1, const uint64_t* A2, const uint64_t* P_hat, const uint64_t* M_hat,
+                        uint64_t* ct_out, void* stream);
+
 /* Fig. 2 lines 5-6 (Alice) in one kernel: decrypt, decode, fold the channel
  * blocks and INTT2D, giving her SPATIAL share y: uint32 [B][Co][H][W]
  * (= fdsc_intt2d(fdsc_decrypt(...))).  Same restrictions as
@@ -268,6 +298,9 @@ typedef struct {
     uint32_t* pA;               /* NULL, or device [B][Co][H/2][W/2]: yA after
                                    fdsc_pool2x2_sum (H, W even)                */
     uint32_t* pB;               /* NULL, or the same for yB                    */
+    uint32_t flood_bits;        /* HomShare noise flooding (0: none), as in
+                                   fdsc_mask_prepare_flooded                   */
+    uint32_t pad0;
 } fdsc_plan_layer;
 
 typedef struct {

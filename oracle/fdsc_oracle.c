@@ -210,8 +210,12 @@ static long double noise_max(const orc_params* P, u32 T) {
     return Tn * (19.0L + P->r_q) * h + (long double)P->r_q * carries + P->r_q;
 }
 double orc_noise_bound_log2(const orc_params* P, u32 T) { return (double)log2l(noise_max(P, T)); }
-int orc_noise_ok(const orc_params* P, u32 T) {
-    return noise_max(P, T) * P->p + (long double)P->r_q * (P->p - 1) < (long double)P->q / 2;
+int orc_noise_ok(const orc_params* P, u32 T) { return orc_noise_ok_flood(P, T, 0); }
+/* With HomShare noise flooding of `flood_bits` (every mask coefficient
+ * carries an extra error in [-2^f, 2^f)), |eta| grows by at most 2^f. */
+int orc_noise_ok_flood(const orc_params* P, u32 T, u32 flood_bits) {
+    long double eta = noise_max(P, T) + (flood_bits ? ldexpl(1.0L, (int)flood_bits) : 0.0L);
+    return eta * P->p + (long double)P->r_q * (P->p - 1) < (long double)P->q / 2;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -232,7 +236,7 @@ u64 orc_rng(u64 seed, u64 domain, u64 idx) {
     return splitmix_out(key + (idx + 1) * GAMMA);
 }
 
-enum { DOM_T = 1, DOM_A = 2, DOM_E = 3, DOM_MASK = 4, DOM_MASK_SPLIT = 5 };
+enum { DOM_T = 1, DOM_A = 2, DOM_E = 3, DOM_MASK = 4, DOM_MASK_SPLIT = 5, DOM_FLOOD = 6 };
 
 /* floor(r * m / 2^64): uniform on [0, m) from one 64-bit word. */
 u32 orc_uniform_p(u32 p, u64 r) { return (u32)(((u128)r * p) >> 64); }
@@ -657,7 +661,17 @@ static u32 mask_slot(const orc_params* P, const orc_layer* L, u64 seed, u32 bb, 
     return orc_uniform_p(p, orc_rng(seed, DOM_MASK, ((u64)b * L->Co + co) * L->HW + f));
 }
 
-void orc_mask_prepare(const orc_params* P, const orc_layer* L, u64 seed, u64* Mhat, u32* sB) {
+/* Noise flooding for circuit privacy (not in the paper; it leaves the
+ * filter-dependent noise of HomConv in Bob's output ciphertext): the mask
+ * plaintext Delta m_s gets, coefficient by coefficient, an error drawn
+ * uniformly from [-2^f, 2^f), so that c1 - M_hat carries it too.  Decryption
+ * rounds it away while the bound of orc_noise_ok_flood holds. */
+static int64_t flood_error(u64 seed, u32 f, u64 idx) {
+    return (int64_t)(orc_rng(seed, DOM_FLOOD, idx) >> (63 - f)) - ((int64_t)1 << f);
+}
+
+void orc_mask_prepare_flooded(const orc_params* P, const orc_layer* L, u64 seed, u32 flood_bits, u64* Mhat,
+                              u32* sB) {
     for (u32 b = 0; b < L->B; b++)
         for (u32 co = 0; co < L->Co; co++)
             for (u32 f = 0; f < L->HW; f++)
@@ -671,11 +685,21 @@ void orc_mask_prepare(const orc_params* P, const orc_layer* L, u64 seed, u64* Mh
             for (u32 s = 0; s < P->S; s++) slots[r * P->S + s] = mask_slot(P, L, seed, bb, co, h, r, s);
         encode_sets(P, slots, m);
         u64* out = Mhat + (size_t)v * P->n;
-        for (u32 i = 0; i < P->n; i++) out[i] = mulm(P->delta, m[i], P->q);
+        for (u32 i = 0; i < P->n; i++) {
+            out[i] = mulm(P->delta, m[i], P->q);
+            if (flood_bits) {
+                int64_t e = flood_error(seed, flood_bits, (u64)v * P->n + i);
+                out[i] = e >= 0 ? addm(out[i], (u64)e, P->q) : subm(out[i], (u64)(-e), P->q);
+            }
+        }
         orc_ntt_q(P, out, out);
     }
     free(m);
     free(slots);
+}
+
+void orc_mask_prepare(const orc_params* P, const orc_layer* L, u64 seed, u64* Mhat, u32* sB) {
+    orc_mask_prepare_flooded(P, L, seed, 0, Mhat, sB);
 }
 
 /* Fig. 2 (Bob): [u-hat o w-hat] = [u-hat] (.) w-hat, summed over input

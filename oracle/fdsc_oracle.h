@@ -66,6 +66,7 @@ int      orc_layer_init(const orc_params* P, uint32_t B, uint32_t Ci, uint32_t C
                         uint32_t H, uint32_t W, uint32_t g_c, uint32_t g_b, orc_layer* L);
 double   orc_noise_bound_log2(const orc_params* P, uint32_t T);
 int      orc_noise_ok(const orc_params* P, uint32_t T);
+int      orc_noise_ok_flood(const orc_params* P, uint32_t T, uint32_t flood_bits);
 
 /* counter-based randomness (SplitMix64 output function) */
 uint64_t orc_rng(uint64_t seed, uint64_t domain, uint64_t idx);
@@ -94,6 +95,9 @@ void orc_filter_prepare(const orc_params* P, const orc_layer* L, const int8_t* w
                         uint32_t fh, uint32_t fw, uint64_t* Phat);
 void orc_mask_prepare(const orc_params* P, const orc_layer* L, uint64_t seed,
                       uint64_t* Mhat, uint32_t* sB);
+/* the same mask with noise flooding of 2^flood_bits (0: none) */
+void orc_mask_prepare_flooded(const orc_params* P, const orc_layer* L, uint64_t seed, uint32_t flood_bits,
+                              uint64_t* Mhat, uint32_t* sB);
 void orc_homconv(const orc_params* P, const orc_layer* L, const uint64_t* ct_in,
                  const uint64_t* Phat, const uint64_t* Mhat, uint64_t* ct_out);
 void orc_decrypt(const orc_params* P, const orc_layer* L, const uint64_t* t_hat,

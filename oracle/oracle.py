@@ -68,6 +68,7 @@ _SIGS = {
     "orc_layer_init": (C.c_int, [_P] + [C.c_uint32] * 7 + [_L]),
     "orc_noise_bound_log2": (C.c_double, [_P, C.c_uint32]),
     "orc_noise_ok": (C.c_int, [_P, C.c_uint32]),
+    "orc_noise_ok_flood": (C.c_int, [_P, C.c_uint32, C.c_uint32]),
     "orc_rng": (C.c_uint64, [C.c_uint64, C.c_uint64, C.c_uint64]),
     "orc_cdt": (None, [_u64p]),
     "orc_gauss": (C.c_int64, [C.c_uint64, _u64p]),
@@ -85,6 +86,7 @@ _SIGS = {
     "orc_filter_spectra": (None, [_P, _L, _i8p, C.c_uint32, C.c_uint32, _u32p]),
     "orc_filter_prepare": (None, [_P, _L, _i8p, C.c_uint32, C.c_uint32, _u64p]),
     "orc_mask_prepare": (None, [_P, _L, C.c_uint64, _u64p, _u32p]),
+    "orc_mask_prepare_flooded": (None, [_P, _L, C.c_uint64, C.c_uint32, _u64p, _u32p]),
     "orc_homconv": (None, [_P, _L, _u64p, _u64p, _u64p, _u64p]),
     "orc_decrypt": (None, [_P, _L, _u64p, _u64p, _u32p, _i64p]),
     "orc_decrypt_raw": (None, [_P, _u64p, _u64p, _u32p, _i64p]),
@@ -157,8 +159,8 @@ def noise_bound_log2(P, T):
     return lib().orc_noise_bound_log2(C.byref(P), T)
 
 
-def noise_ok(P, T):
-    return bool(lib().orc_noise_ok(C.byref(P), T))
+def noise_ok(P, T, flood_bits=0):
+    return bool(lib().orc_noise_ok_flood(C.byref(P), T, flood_bits))
 
 
 def rng(seed, domain, idx):
@@ -270,10 +272,10 @@ def filter_prepare(P, L, w):
     return out
 
 
-def mask_prepare(P, L, seed):
+def mask_prepare(P, L, seed, flood_bits=0):
     M = np.empty((L.n_out, P.n), np.uint64)
     sB = np.empty((L.B, L.Co, L.HW), np.uint32)
-    lib().orc_mask_prepare(C.byref(P), C.byref(L), seed, _ptr(M, _u64p), _ptr(sB, _u32p))
+    lib().orc_mask_prepare_flooded(C.byref(P), C.byref(L), seed, flood_bits, _ptr(M, _u64p), _ptr(sB, _u32p))
     return M, sB
 
 
@@ -324,9 +326,10 @@ def pool2x2_sum(p, x):
     return y
 
 
-def round_trip(P, L, xA, xB, w, key_seed, enc_seed, srv_seed, with_homrec=True):
+def round_trip(P, L, xA, xB, w, key_seed, enc_seed, srv_seed, with_homrec=True, flood_bits=0):
     """One FDSC layer (Fig. 2, lines 1-6, with HomRec of Bob's share as in
-    lines 9-11): returns every stage boundary for parity checks."""
+    lines 9-11; optionally HomShare noise flooding): returns every stage
+    boundary for parity checks."""
     H, W = L.H, L.W
     out = {}
     t, t_hat = keygen(P, key_seed)
@@ -342,7 +345,7 @@ def round_trip(P, L, xA, xB, w, key_seed, enc_seed, srv_seed, with_homrec=True):
         out["ct_rec"] = ct
     Phat = filter_prepare(P, L, w)
     out["Phat"] = Phat
-    Mhat, sB = mask_prepare(P, L, srv_seed)
+    Mhat, sB = mask_prepare(P, L, srv_seed, flood_bits)
     out["Mhat"], out["sB_hat"] = Mhat, sB
     ct_out = homconv(P, L, ct, Phat, Mhat)
     out["ct_out"] = ct_out

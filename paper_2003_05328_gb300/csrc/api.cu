@@ -115,7 +115,32 @@ extern "C" int fdsc_mask_prepare(const fdsc_params* P, const fdsc_layer* L, uint
     DevLayer D;
     if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
     if ((rc = check_ptr(M_hat, "M_hat")) || (rc = check_ptr(sB_hat, "sB_hat"))) return rc;
-    return launched(launch_mask_prepare(P->dev, D, seed, nullptr, M_hat, sB_hat, (cudaStream_t)stream), "mask_prepare");
+    return launched(launch_mask_prepare(P->dev, D, seed, nullptr, 0, M_hat, sB_hat, (cudaStream_t)stream), "mask_prepare");
+}
+
+extern "C" int fdsc_mask_prepare_flooded(const fdsc_params* P, const fdsc_layer* L, uint64_t seed, uint32_t flood_bits,
+                                         uint64_t* M_hat, uint32_t* sB_hat, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if (flood_bits > FDSC_MAX_FLOOD_BITS || !fdsc_noise_ok_flood(P->info, D.T, flood_bits))
+        return fdsc_set_error(FDSC_ERR_NOISE, "flooding of 2^%u breaks the noise bound at T = %u", flood_bits, D.T);
+    if ((rc = check_ptr(M_hat, "M_hat")) || (rc = check_ptr(sB_hat, "sB_hat"))) return rc;
+    return launched(launch_mask_prepare(P->dev, D, seed, nullptr, flood_bits, M_hat, sB_hat, (cudaStream_t)stream),
+                    "mask_prepare_flooded");
+}
+
+extern "C" int fdsc_flood_bits_max(uint32_t n, uint32_t p, uint32_t T, uint32_t* out) {
+    if (!out) return fdsc_set_error(FDSC_ERR_ARG, "out is NULL");
+    fdsc_params_info I;
+    int rc = fdsc_params_query(n, p, &I);
+    if (rc) return rc;
+    if (!fdsc_noise_ok(I, T)) return fdsc_set_error(FDSC_ERR_NOISE, "noise bound fails for T = %u", T);
+    u32 f = 0;
+    while (f < FDSC_MAX_FLOOD_BITS && fdsc_noise_ok_flood(I, T, f + 1)) f++;
+    *out = f;
+    return FDSC_OK;
 }
 
 extern "C" int fdsc_homconv(const fdsc_params* P, const fdsc_layer* L, const uint64_t* ct_in, const uint64_t* P_hat,
@@ -225,6 +250,41 @@ extern "C" int fdsc_homconv_sum(const fdsc_params* P, const fdsc_layer* L, const
                     "homconv_sum");
 }
 
+extern "C" int fdsc_encrypt_constants_seeded(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat,
+                                             uint64_t seed, uint64_t* c1, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(P->info, L, &D, nullptr))) return rc;
+    if ((rc = check_ptr(t_hat, "t_hat")) || (rc = check_ptr(c1, "c1"))) return rc;
+    return launched(launch_constants(P->dev, D, t_hat, 0, seed, nullptr, c1, (cudaStream_t)stream, true),
+                    "encrypt_constants_seeded");
+}
+
+extern "C" int fdsc_homconv_seeded(const fdsc_params* P, const fdsc_layer* L, uint64_t seed, const uint64_t* c1,
+                                   const uint64_t* A1, const uint64_t* A2, const uint64_t* P_hat,
+                                   const uint64_t* M_hat, uint64_t* ct_out, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    fdsc_layout lay;
+    if ((rc = fdsc_make_layer(P->info, L, &D, &lay))) return rc;
+    if (D.T > P->max_T)
+        return fdsc_set_error(FDSC_ERR_NOISE, "T = %u input ciphertexts exceed the params' noise budget (max_T = %u)",
+                              D.T, P->max_T);
+    if (D.T > 256) return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "seeded HomConv stages T <= 256 input ciphertexts");
+    if ((rc = check_ptr(c1, "c1")) || (rc = check_ptr(P_hat, "P_hat")) || (rc = check_ptr(ct_out, "ct_out")))
+        return rc;
+    if ((A1 && (rc = check_ptr(A1, "A1"))) || (A2 && (rc = check_ptr(A2, "A2"))) ||
+        (M_hat && (rc = check_ptr(M_hat, "M_hat"))))
+        return rc;
+    const u64 ob = lay.ct_out_words * 8, ab = (u64)D.n_in * P->info.n * 8;
+    if (overlap(c1, ab, ct_out, ob) || (A1 && overlap(A1, ab, ct_out, ob)) || (A2 && overlap(A2, ab, ct_out, ob)))
+        return fdsc_set_error(FDSC_ERR_ARG, "ct_out overlaps an input");
+    return launched(launch_homconv_seeded(P->dev, D, seed, c1, A1, A2, P_hat, M_hat, ct_out, (cudaStream_t)stream),
+                    "homconv_seeded");
+}
+
 extern "C" int fdsc_decrypt_share(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat,
                                   const uint64_t* ct, uint32_t* y, void* stream) {
     int rc = check_params(P);
@@ -259,7 +319,7 @@ extern "C" int fdsc_mask_prepare_multi(const fdsc_params* P, const fdsc_layer* L
     if ((rc = check_ptr(seeds, "seeds", false)) || (rc = check_ptr(M_hat, "M_hat")) ||
         (rc = check_ptr(sB_hat, "sB_hat")))
         return rc;
-    return launched(launch_mask_prepare(P->dev, D, 0, seeds, M_hat, sB_hat, (cudaStream_t)stream),
+    return launched(launch_mask_prepare(P->dev, D, 0, seeds, 0, M_hat, sB_hat, (cudaStream_t)stream),
                     "mask_prepare_multi");
 }
 

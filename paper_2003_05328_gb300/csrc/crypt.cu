@@ -181,8 +181,8 @@ __device__ __forceinline__ u32 mask_value(const DevParams& P, const DevLayer& L,
 // image number.  Otherwise image group bb draws from seeds[bb] with images
 // numbered from 0 inside the group, exactly as if it were a call of its own.
 __global__ void __launch_bounds__(kMaxThreads) mask_kernel(DevParams P, DevLayer L, u64 seed,
-                                                        const u64* __restrict__ seeds, u64* __restrict__ Mhat,
-                                                        u32* __restrict__ sB) {
+                                                        const u64* __restrict__ seeds, u32 flood_bits,
+                                                        u64* __restrict__ Mhat, u32* __restrict__ sB) {
     extern __shared__ u64 smem[];
     u64* c = smem;
     u32* slots = reinterpret_cast<u32*>(smem + P.n);
@@ -220,9 +220,17 @@ __global__ void __launch_bounds__(kMaxThreads) mask_kernel(DevParams P, DevLayer
     }
     __syncthreads();
     ntt_p_inv8(slots, P.d, P);
+    // noise flooding: coefficient i of mask ciphertext v carries an error
+    // uniform in [-2^f, 2^f), from the top f + 1 bits of its random word
+    const u64 kFlood = stream_key(seed, DOM_FLOOD);
     for (u32 sg = threadIdx.x; sg < P.n; sg += blockDim.x) {
-        const u32 r = sg >> P.logS, i = sg & (P.S - 1);
-        c[r + P.d * i] = P.delta * slots[sg];
+        const u32 r = sg >> P.logS, i = sg & (P.S - 1), coef = r + P.d * i;
+        u64 m = P.delta * slots[sg];
+        if (flood_bits) {
+            const u64 t = stream_at(kFlood, (u64)v * P.n + coef) >> (63 - flood_bits), half = 1ull << flood_bits;
+            m = t >= half ? addmod_q(m, t - half, P.q) : submod_q(m, half - t, P.q);
+        }
+        c[coef] = m;
     }
     __syncthreads();
     ntt_q_fwd8(c, P);
@@ -336,12 +344,12 @@ cudaError_t launch_filter_prepare(const DevParams& P, const DevLayer& L, const i
     return cudaGetLastError();
 }
 
-cudaError_t launch_mask_prepare(const DevParams& P, const DevLayer& L, u64 seed, const u64* seeds, u64* Mhat, u32* sB,
+cudaError_t launch_mask_prepare(const DevParams& P, const DevLayer& L, u64 seed, const u64* seeds, u32 flood_bits, u64* Mhat, u32* sB,
                                 cudaStream_t s) {
     const size_t sm = (size_t)P.n * 12;
     cudaError_t e = set_smem(mask_kernel, sm);
     if (e != cudaSuccess) return e;
-    return launch_online(mask_kernel, L.n_out, threads_for(P.n), sm, s, P, L, seed, seeds, Mhat, sB);
+    return launch_online(mask_kernel, L.n_out, threads_for(P.n), sm, s, P, L, seed, seeds, flood_bits, Mhat, sB);
 }
 
 cudaError_t launch_decrypt(const DevParams& P, const DevLayer& L, const u64* t_hat, const u64* ct, u32* SA,

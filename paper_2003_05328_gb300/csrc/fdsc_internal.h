@@ -89,6 +89,8 @@ int fdsc_derive(u32 n, u32 p, fdsc_params_info* out);
 int fdsc_make_layer(const fdsc_params_info& I, const fdsc_layer* L, DevLayer* out, fdsc_layout* lay);
 void fdsc_host_cdt(u64* cdt19);
 bool fdsc_noise_ok(const fdsc_params_info& I, u32 T);
+bool fdsc_noise_ok_flood(const fdsc_params_info& I, u32 T, u32 flood_bits);
+constexpr u32 FDSC_MAX_FLOOD_BITS = 62;
 u32 fdsc_shoup32(u32 w, u32 p);
 u32 fdsc_powmod32(u32 b, u64 e, u32 p);
 
@@ -101,8 +103,10 @@ cudaError_t launch_encrypt(const DevParams& P, const DevLayer& L, const u64* t_h
 cudaError_t launch_homrec(const DevParams& P, const DevLayer& L, const u32* XB, u64* ct, cudaStream_t s);
 cudaError_t launch_filter_prepare(const DevParams& P, const DevLayer& L, const int8_t* w, u32 fh, u32 fw,
                                   u64* Phat, cudaStream_t s);
-cudaError_t launch_mask_prepare(const DevParams& P, const DevLayer& L, u64 seed, const u64* seeds, u64* Mhat, u32* sB,
+cudaError_t launch_mask_prepare(const DevParams& P, const DevLayer& L, u64 seed, const u64* seeds, u32 flood_bits, u64* Mhat, u32* sB,
                                 cudaStream_t s);
+cudaError_t launch_homconv_seeded(const DevParams& P, const DevLayer& L, u64 seed, const u64* c1, const u64* A1,
+                                  const u64* A2, const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s);
 cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
                            const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s);
 cudaError_t launch_homconv_v(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
@@ -110,7 +114,7 @@ cudaError_t launch_homconv_v(const DevParams& P, const DevLayer& L, const u64* c
 int homconv_default_variant(const DevLayer& L);
 cudaError_t launch_pool2x2(const DevParams& P, u32 H, u32 W, const u32* x, u32* y, u64 planes, cudaStream_t s);
 cudaError_t launch_constants(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, u64 seed,
-                             const u64* seeds, u64* ct, cudaStream_t s);
+                             const u64* seeds, u64* ct, cudaStream_t s, bool c1_only = false);
 cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u64* out, bool add_to_ct,
                          cudaStream_t s);
 cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, const u64* ct,

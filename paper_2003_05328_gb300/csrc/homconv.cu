@@ -305,7 +305,9 @@ __global__ void __launch_bounds__(kThreads3) homconv3_kernel(DevParams P, DevLay
                                                              const u64* __restrict__ A1, const u64* __restrict__ A2,
                                                              const u64* __restrict__ Phat,
                                                              const u64* __restrict__ Mhat, u64* __restrict__ ct_out,
-                                                             u32 jtiles, u32 ctiles) {
+                                                             u32 jtiles, u32 ctiles, u64 seed, int seeded) {
+    // seeded: ct_in holds c1 alone ([n_in][n]); c0 = -a is drawn again from
+    // the encryption seed exactly as the encryption constants drew it
     extern __shared__ __align__(16) u64 xs[];  // [T][2][kJ3] canonical words, or 30-bit limb pairs
     constexpr bool kWide = kAcc == 1;
     using Acc = typename std::conditional<kAcc == 1, AccLimb,
@@ -318,6 +320,7 @@ __global__ void __launch_bounds__(kThreads3) homconv3_kernel(DevParams P, DevLay
     const u64 n = P.n, beta = L.beta;
     griddep_release();
     griddep_wait();
+    const u64 keyA = stream_key(seed, DOM_A);
     // stage the input tile (all threads)
     for (u32 e = threadIdx.x; e < T * kJ3; e += kThreads3) {
         const u32 k = e / kJ3, jj = e % kJ3, J = jt * kJ3 + jj;
@@ -325,8 +328,15 @@ __global__ void __launch_bounds__(kThreads3) homconv3_kernel(DevParams P, DevLay
         if (J < nJ) {
             const u32 h = J >> P.logn, j = J & (P.n - 1);
             const u64 u = ((u64)bb * T + k) * beta + h;
-            x0 = __ldg(ct_in + u * 2 * n + j);
-            x1 = __ldg(ct_in + u * 2 * n + n + j);
+            if (seeded) {
+                const u64 idx = 2 * (u * n + j);
+                const u64 a = uniform_q(stream_at(keyA, idx), stream_at(keyA, idx + 1), P.q);
+                x0 = a ? P.q - a : 0;
+                x1 = __ldg(ct_in + u * n + j);
+            } else {
+                x0 = __ldg(ct_in + u * 2 * n + j);
+                x1 = __ldg(ct_in + u * 2 * n + n + j);
+            }
             if (A1) x1 = addmod_q(x1, __ldg(A1 + u * n + j), P.q);
             if (A2) x1 = addmod_q(x1, __ldg(A2 + u * n + j), P.q);
         }
@@ -397,7 +407,7 @@ __global__ void __launch_bounds__(kThreads3) homconv3_kernel(DevParams P, DevLay
 
 template <int W>
 cudaError_t launch_v3(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
-                      const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
+                      const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s, u64 seed = 0, int seeded = 0) {
     const u32 nJ = L.beta * P.n;
     const u32 jtiles = (nJ + kJ3 - 1) / kJ3, ctiles = (L.Co + kW3 - 1) / kW3;
     const u64 grid = (u64)jtiles * ctiles * L.GB;
@@ -408,7 +418,7 @@ cudaError_t launch_v3(const DevParams& P, const DevLayer& L, const u64* ct_in, c
         if (e != cudaSuccess) return e;
     }
     return launch_online(homconv3_kernel<W>, (u32)grid, kThreads3, smem, s, P, L, ct_in, A1, A2, Phat, Mhat, ct_out,
-                         jtiles, ctiles);
+                         jtiles, ctiles, seed, seeded);
 }
 
 
@@ -456,4 +466,12 @@ cudaError_t launch_homconv_v(const DevParams& P, const DevLayer& L, const u64* c
 cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
                            const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
     return launch_homconv_v(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, g_homconv_variant, s);
+}
+
+// HomConv of seeded input ciphertexts (c1 alone, c0 from the encryption seed):
+// the staged-tile kernel, which draws c0 once per tile while staging it.
+cudaError_t launch_homconv_seeded(const DevParams& P, const DevLayer& L, u64 seed, const u64* c1, const u64* A1,
+                                  const u64* A2, const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
+    if (L.T > 256) return cudaErrorInvalidValue;
+    return launch_v3<0>(P, L, c1, A1, A2, Phat, Mhat, ct_out, s, seed, 1);
 }

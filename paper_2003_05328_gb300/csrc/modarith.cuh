@@ -49,7 +49,7 @@ __device__ __forceinline__ u32 submod_p(u32 a, u32 b, u32 p) { return a >= b ? a
 // generator: stream key = out(seed + domain gamma); value idx = out(key +
 // (idx + 1) gamma).
 #define FDSC_GAMMA 0x9E3779B97F4A7C15ull
-enum { DOM_T = 1, DOM_A = 2, DOM_E = 3, DOM_MASK = 4, DOM_MASK_SPLIT = 5 };
+enum { DOM_T = 1, DOM_A = 2, DOM_E = 3, DOM_MASK = 4, DOM_MASK_SPLIT = 5, DOM_FLOOD = 6 };
 
 __device__ __forceinline__ u64 splitmix_out(u64 z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;

@@ -119,12 +119,18 @@ int fdsc_derive(u32 n, u32 p, fdsc_params_info* I) {
 
 // Worst-case noise of a HomConv output summing T inputs (fresh error 19 plus
 // a HomRec carry, the plaintext product's multiples of p, HomShare borrow).
-bool fdsc_noise_ok(const fdsc_params_info& I, u32 T) {
+// Worst-case decryption noise of a HomConv output with T input ciphertexts
+// (fresh Gaussian noise times filter words, plaintext carries past p, the
+// HomRec and HomShare carries), plus 2^flood_bits of HomShare flooding;
+// decryption rounds correctly while p |eta| + r_q (p - 1) < q / 2.
+bool fdsc_noise_ok_flood(const fdsc_params_info& I, u32 T, u32 flood_bits) {
     long double Tn = (long double)T * I.n, half = (long double)(I.p / 2);
     long double carry = ceill(Tn * (I.p - 1) * half / I.p);
     long double eta = Tn * (19.0L + I.r_q) * half + (long double)I.r_q * carry + I.r_q;
+    if (flood_bits) eta += ldexpl(1.0L, (int)flood_bits);
     return eta * I.p + (long double)I.r_q * (I.p - 1) < (long double)I.q / 2;
 }
+bool fdsc_noise_ok(const fdsc_params_info& I, u32 T) { return fdsc_noise_ok_flood(I, T, 0); }
 
 // Discrete Gaussian sigma = 3.2 on |x| <= 19: running sums of
 // rho(0)/Z, 2 rho(k)/Z (rho(k) = exp(-k^2 / (2 sigma^2))) scaled by 2^63.

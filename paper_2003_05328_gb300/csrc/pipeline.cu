@@ -29,9 +29,11 @@ inline u32 threads_for(u32 n) { return n / 8 < 32 ? 32 : n / 8; }
 // Image group g = u / per_group uses the key t_hat + g key_stride; with
 // seeds != nullptr it draws from seeds[g] with ciphertexts numbered from 0
 // inside the group (as if it were a call of its own).
+// c1_only: write c1 alone ([n_in][n]; the seeded form, c0 = -a being
+// recomputable from the seed).
 __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, const u64* __restrict__ t_hat, u64 key_stride,
                                                                 u32 per_group, u64 seed, const u64* __restrict__ seeds,
-                                                                u64* __restrict__ ct) {
+                                                                u64* __restrict__ ct, int c1_only) {
     extern __shared__ __align__(16) unsigned char sm[];
     const u32 n = P.n;
     ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^brv, companion)
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, con
     stage_async(key, t_hat + (u64)grp * key_stride, n * 8);
     const u64 keyA = stream_key(seed, DOM_A);
     u64* c0 = ct + (u64)u * 2 * n;
-    u64* c1 = c0 + n;
+    u64* c1 = c1_only ? ct + (u64)u * n : c0 + n;
     // c0 = -a while the key arrives; a stays in registers for c1
     for (u32 j0 = 0; j0 < n; j0 += 8 * blockDim.x) {
         u64 a[8];
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, con
             if (j < n) {
                 const u64 idx = 2 * ((u64)ur * n + j);
                 a[r] = uniform_q(stream_at(keyA, idx), stream_at(keyA, idx + 1), P.q);
-                c0[j] = a[r] ? P.q - a[r] : 0;
+                if (!c1_only) c0[j] = a[r] ? P.q - a[r] : 0;
             }
         }
         stage_wait();
@@ -252,12 +254,12 @@ size_t decrypt_share_smem_bytes(const DevParams& P, const DevLayer& L) {
 size_t constants_smem_bytes(const DevParams& P) { return (size_t)P.n * 24 + (size_t)padded_len(P.n) * 8; }
 
 cudaError_t launch_constants(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, u64 seed,
-                             const u64* seeds, u64* ct, cudaStream_t s) {
+                             const u64* seeds, u64* ct, cudaStream_t s, bool c1_only) {
     const size_t sm = constants_smem_bytes(P);
     cudaError_t e = opt_in(constants_kernel, sm);
     if (e != cudaSuccess) return e;
     return launch_online(constants_kernel, L.n_in, threads_for(P.n), sm, s, P, t_hat, key_stride, L.T * L.beta, seed,
-                         seeds, ct);
+                         seeds, ct, c1_only ? 1 : 0);
 }
 
 cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u64* out, bool add_to_ct,

@@ -112,7 +112,7 @@ int plan_alloc_layer(PlanLayer& pl, Arena& ar, fdsc_layout& lay) {
 int plan_setup_layer(PlanLayer& pl, cudaStream_t s) {
     const DevParams& P = pl.spec.params->dev;
     RT_TRY(launch_filter_prepare(P, pl.D, pl.spec.w, pl.spec.fh, pl.spec.fw, pl.Phat, s));
-    RT_TRY(launch_mask_prepare(P, pl.D, pl.spec.mask_seed, nullptr, pl.Mhat, pl.sB, s));
+    RT_TRY(launch_mask_prepare(P, pl.D, pl.spec.mask_seed, nullptr, pl.spec.flood_bits, pl.Mhat, pl.sB, s));
     return FDSC_OK;
 }
 
@@ -273,7 +273,9 @@ extern "C" int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, u
                     cand.L.g_b = pk.second;
                     cand.variant = v;
                     DevLayer Dt;
-                    if (fdsc_make_layer(I, &cand.L, &Dt, nullptr) != FDSC_OK || Dt.T > sp.params->max_T) continue;
+                    if (fdsc_make_layer(I, &cand.L, &Dt, nullptr) != FDSC_OK || Dt.T > sp.params->max_T ||
+                        !fdsc_noise_ok_flood(I, Dt.T, sp.flood_bits))
+                        continue;
                     if (v == 2 && Dt.GB < 2) continue;
                     double us = 0;
                     if ((rc = plan_time_candidate(cand, st, ev, &us))) return fail(rc);
@@ -292,6 +294,9 @@ extern "C" int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, u
         }
         if (pl.D.T > sp.params->max_T)
             return fail(fdsc_set_error(FDSC_ERR_NOISE, "layer %u: T = %u exceeds the params' max_T", i, pl.D.T));
+        if (sp.flood_bits > FDSC_MAX_FLOOD_BITS || !fdsc_noise_ok_flood(I, pl.D.T, sp.flood_bits))
+            return fail(fdsc_set_error(FDSC_ERR_NOISE, "layer %u: flooding of 2^%u breaks the noise bound", i,
+                                       sp.flood_bits));
         if ((rc = plan_alloc_layer(pl, plan->arena, lay)) || (rc = plan_setup_layer(pl, st[0]))) return fail(rc);
     }
     // one eager run of every layer before recording: validates the launches and
@@ -471,7 +476,7 @@ int launch_batch(fdsc_server* S, Lane& ln) {
     for (uint32_t b = 0; b < G; b++)
         RT_TRY(cudaMemcpyAsync(ln.keys + b * n, t.keys + (uint64_t)ln.batch[b].r.key * n, n * 8, cudaMemcpyDeviceToDevice,
                                s));
-    RT_TRY(launch_mask_prepare(P, D, 0, ln.seeds + G, ln.M, ln.sB, s));
+    RT_TRY(launch_mask_prepare(P, D, 0, ln.seeds + G, 0, ln.M, ln.sB, s));
     RT_TRY(launch_constants(P, D, ln.keys, n, 0, ln.seeds, ln.ct, s));
     RT_TRY(launch_share(P, D, ln.xA, ln.A, false, s));
     RT_TRY(launch_share(P, D, ln.xB, ln.R, false, s));

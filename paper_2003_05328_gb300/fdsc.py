@@ -66,6 +66,8 @@ _SIGS = {
     "fdsc_keygen": (C.c_int, [_vp, C.c_uint64, _vp, _vp]),
     "fdsc_filter_prepare": (C.c_int, [_vp, _PL, _vp, C.c_uint32, C.c_uint32, _vp, _vp]),
     "fdsc_mask_prepare": (C.c_int, [_vp, _PL, C.c_uint64, _vp, _vp, _vp]),
+    "fdsc_mask_prepare_flooded": (C.c_int, [_vp, _PL, C.c_uint64, C.c_uint32, _vp, _vp, _vp]),
+    "fdsc_flood_bits_max": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32)]),
     "fdsc_encrypt": (C.c_int, [_vp, _PL, _vp, _vp, C.c_uint64, _vp, _vp]),
     "fdsc_homrec": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
     "fdsc_homconv": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp, _vp]),
@@ -76,6 +78,8 @@ _SIGS = {
     "fdsc_encode_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
     "fdsc_homrec_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
     "fdsc_homconv_sum": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fdsc_encrypt_constants_seeded": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp]),
+    "fdsc_homconv_seeded": (C.c_int, [_vp, _PL, C.c_uint64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fdsc_decrypt_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
     "fdsc_encrypt_constants_multi": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp, _vp]),
     "fdsc_mask_prepare_multi": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
@@ -270,6 +274,25 @@ def mask_prepare(P: Params, L: LayerSpec, seed: int, M_hat=None, sB_hat=None, st
     return M_hat, sB_hat
 
 
+def mask_prepare_flooded(P: Params, L: LayerSpec, seed: int, flood_bits: int, M_hat=None, sB_hat=None, stream=None):
+    """HomShare masks with noise flooding of 2^flood_bits per coefficient."""
+    lay = layout(P, L)
+    if M_hat is None:
+        M_hat = torch.empty(lay.mask_words, dtype=torch.int64, device="cuda")
+    if sB_hat is None:
+        sB_hat = torch.empty(lay.out_spectra_words, dtype=torch.int32, device="cuda")
+    _call("fdsc_mask_prepare_flooded", P.handle, C.byref(L.c()), seed, flood_bits,
+          _ptr(M_hat, torch.int64, lay.mask_words, "M_hat"), _ptr(sB_hat, torch.int32, lay.out_spectra_words, "sB_hat"),
+          _stream(stream))
+    return M_hat, sB_hat
+
+
+def flood_bits_max(n: int, p: int, T: int) -> int:
+    out = C.c_uint32(0)
+    _call("fdsc_flood_bits_max", n, p, T, C.byref(out))
+    return out.value
+
+
 def set_homconv_variant(v: int) -> None:
     """Kernel variant for HomConv (0 automatic; results are identical)."""
     _call("fdsc_set_homconv_variant", v)
@@ -362,6 +385,32 @@ def homconv_sum(P: Params, L: LayerSpec, ct_in, A1, A2, P_hat, M_hat=None, out=N
     return out
 
 
+def encrypt_constants_seeded(P: Params, L: LayerSpec, t_hat, seed: int, out=None, stream=None) -> torch.Tensor:
+    """c1 of Enc(0) alone ([n_in][n]): the seeded ciphertext form."""
+    lay = layout(P, L)
+    if out is None:
+        out = torch.empty(lay.n_in * P.n, dtype=torch.int64, device="cuda")
+    _call("fdsc_encrypt_constants_seeded", P.handle, C.byref(L.c()), _ptr(t_hat, torch.int64, P.n, "t_hat"), seed,
+          _ptr(out, torch.int64, lay.n_in * P.n, "c1"), _stream(stream))
+    return out
+
+
+def homconv_seeded(P: Params, L: LayerSpec, seed: int, c1, A1, A2, P_hat, M_hat=None, out=None,
+                   stream=None) -> torch.Tensor:
+    """homconv_sum on seeded ciphertexts: c0 drawn again from the encryption seed."""
+    lay = layout(P, L)
+    if out is None:
+        out = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
+    na = lay.n_in * P.n
+    a1 = None if A1 is None else _ptr(A1, torch.int64, na, "A1")
+    a2 = None if A2 is None else _ptr(A2, torch.int64, na, "A2")
+    m = None if M_hat is None else _ptr(M_hat, torch.int64, lay.mask_words, "M_hat")
+    _call("fdsc_homconv_seeded", P.handle, C.byref(L.c()), seed, _ptr(c1, torch.int64, na, "c1"), a1, a2,
+          _ptr(P_hat, torch.int64, lay.filter_words, "P_hat"), m, _ptr(out, torch.int64, lay.ct_out_words, "ct_out"),
+          _stream(stream))
+    return out
+
+
 def decrypt_share(P: Params, L: LayerSpec, t_hat, ct, out=None, stream=None) -> torch.Tensor:
     """Decrypt, decode, fold and INTT2D: Alice's spatial share int32 [B][Co][H][W]."""
     lay = layout(P, L)
@@ -415,7 +464,8 @@ def decrypt_share_multi(P: Params, L: LayerSpec, t_hats, ct, key_stride=None, ou
 class PlanLayerC(C.Structure):
     _fields_ = [("params", _vp), ("layer", Layer), ("fh", C.c_uint32), ("fw", C.c_uint32), ("w", _vp),
                 ("t_hat", _vp), ("enc_seed", C.c_uint64), ("mask_seed", C.c_uint64), ("xA", _vp), ("xB", _vp),
-                ("yA", _vp), ("yB", _vp), ("pA", _vp), ("pB", _vp)]
+                ("yA", _vp), ("yB", _vp), ("pA", _vp), ("pB", _vp), ("flood_bits", C.c_uint32),
+                ("pad0", C.c_uint32)]
 
 
 class PlanLayerInfo(C.Structure):
@@ -444,7 +494,8 @@ class Plan:
                                 _ptr(d["t_hat"], torch.int64, d["params"].n, "t_hat"), d["enc_seed"], d["mask_seed"],
                                 d["xA"].data_ptr(), d["xB"].data_ptr(), d["yA"].data_ptr(), d["yB"].data_ptr(),
                                 d["pA"].data_ptr() if d.get("pA") is not None else None,
-                                d["pB"].data_ptr() if d.get("pB") is not None else None)
+                                d["pB"].data_ptr() if d.get("pB") is not None else None,
+                                d.get("flood_bits", 0), 0)
         h = _vp()
         flags = (PLAN_TUNE if tune else 0) | (PLAN_CHAIN if chain else 0)
         _call("fdsc_plan_create", C.addressof(arr), len(layers), flags, _stream(stream), C.byref(h))

@@ -298,3 +298,34 @@ def test_homconv_variants_identical(F, shape):
     finally:
         F.set_homconv_variant(0)
     P.close()
+
+
+@pytest.mark.parametrize("shape", [(2048, 1, 64, 64, 32, 32, 2, 1), (1024, 3, 5, 7, 16, 16, 2, 2),
+                                   (1024, 2, 12, 12, 64, 64, 1, 1)])
+def test_seeded_ciphertexts(F, shape):
+    """Seeded input ciphertexts (seed + c1): the c1 words are those of the
+    oracle's encryption, and HomConv drawing c0 = -a again from the seed
+    gives the oracle's HomConv of the full ciphertexts."""
+    n, B, Ci, Co, H, W, g_c, g_b = shape
+    OP = O.params(n, 65537)
+    OL = O.layer(OP, B, Ci, Co, H, W, g_c, g_b)
+    P = F.Params(n, 65537, max_T=max(OL.T, 1))
+    L = F.LayerSpec(B, Ci, Co, H, W, g_c, g_b)
+    es = 0x5EED + n
+    _, t_hat_o = O.keygen(OP, 7)
+    ct_o = O.encrypt(OP, OL, t_hat_o, np.zeros((B, Ci, H * W), np.uint32), es)
+    c1 = F.encrypt_constants_seeded(P, L, F.keygen(P, 7), es)
+    torch.cuda.synchronize()
+    assert np.array_equal(u64(c1).reshape(OL.n_in, n), ct_o[:, 1])
+    g = np.random.default_rng(n + Co)
+    A1 = np.array(g.integers(0, OP.q, (OL.n_in, n), dtype=np.uint64))
+    A2 = np.array(g.integers(0, OP.q, (OL.n_in, n), dtype=np.uint64))
+    Ph = np.array(g.integers(0, OP.q, (Co * OL.T * OL.beta, n), dtype=np.uint64))
+    Mh = np.array(g.integers(0, OP.q, (OL.n_out, n), dtype=np.uint64))
+    d = lambda a: dev(a.view(np.int64), np.int64)
+    out = F.homconv_seeded(P, L, es, c1, d(A1), d(A2), d(Ph), d(Mh))
+    full = ct_o.astype(object)
+    full[:, 1] = (full[:, 1] + A1.astype(object) + A2.astype(object)) % OP.q
+    ref = O.homconv(OP, OL, full.astype(np.uint64), Ph, Mh)
+    assert np.array_equal(u64(out).reshape(ref.shape), ref)
+    P.close()

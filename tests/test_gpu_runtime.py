@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import torch
 
-from fdsc_harness import dev, u32
+from fdsc_harness import dev, u32, u64
 from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -237,5 +237,48 @@ def test_chained_plan_of_a_network_matches_oracle(F):
                 a, b = O.pool2x2_sum(p, a), O.pool2x2_sum(p, b)
                 assert np.array_equal(u32(d["pA"]).reshape(a.shape), a)
                 assert np.array_equal(u32(d["pB"]).reshape(b.shape), b)
+    plan.close()
+    P.close()
+
+
+def test_noise_flooding_masks_and_shares(F):
+    """HomShare flooding: the mask words are the oracle's, and the final
+    shares of the fused path and of a plan equal the unflooded oracle run."""
+    n, p = 1024, 65537
+    P = F.Params(n, p, max_T=8)
+    OP = O.params(n, p)
+    B, Ci, Co, H = 1, 4, 4, 16
+    OL = O.layer(OP, B, Ci, Co, H, H)
+    L = F.LayerSpec(B, Ci, Co, H, H, OL.g_c, OL.g_b)
+    f = F.flood_bits_max(n, p, OL.T)
+    M, sB = F.mask_prepare_flooded(P, L, 33, f)
+    Mo, sBo = O.mask_prepare(OP, OL, 33, f)
+    torch.cuda.synchronize()
+    assert np.array_equal(u64(M).reshape(Mo.shape), Mo) and np.array_equal(u32(sB).reshape(sBo.shape), sBo)
+    with pytest.raises(F.FdscError) as e:
+        F.mask_prepare_flooded(P, L, 33, f + 1)
+    assert e.value.code == -2
+    g = np.random.default_rng(5)
+    xA = g.integers(0, p, (B, Ci, H, H)).astype(np.uint32)
+    xB = g.integers(0, p, (B, Ci, H, H)).astype(np.uint32)
+    w = g.integers(-8, 8, (Co, Ci, 3, 3)).astype(np.int8)
+    ref = O.round_trip(OP, OL, xA, xB, w, 1, 2, 33)
+    t_hat = F.keygen(P, 1)
+    Ph = F.filter_prepare(P, L, dev(w, np.int8))
+    ct = F.encrypt_constants(P, L, t_hat, 2)
+    out = F.homconv_sum(P, L, ct, F.encode_share(P, L, dev(xA, np.int32)), F.encode_share(P, L, dev(xB, np.int32)),
+                        Ph, M)
+    yA = F.decrypt_share(P, L, t_hat, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(u32(yA).reshape(ref["yA"].shape), ref["yA"])
+    d = dict(params=P, layer=F.LayerSpec(B, Ci, Co, H, H, 0, 0), w=dev(w, np.int8), t_hat=t_hat, enc_seed=2,
+             mask_seed=33, xA=dev(xA, np.int32), xB=dev(xB, np.int32), flood_bits=f,
+             yA=torch.zeros((B, Co, H, H), dtype=torch.int32, device="cuda"),
+             yB=torch.zeros((B, Co, H, H), dtype=torch.int32, device="cuda"))
+    plan = F.Plan([d], tune=True)
+    plan.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(u32(d["yA"]).reshape(ref["yA"].shape), ref["yA"])
+    assert np.array_equal(u32(d["yB"]).reshape(ref["yB"].shape), ref["yB"])
     plan.close()
     P.close()

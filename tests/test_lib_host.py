@@ -90,3 +90,12 @@ def test_layout_rejects_bad_packing(F):
 
 def test_gauss_table_matches_oracle(F):
     assert np.array_equal(F.gauss_table(), O.cdt())
+
+
+@pytest.mark.parametrize("n,p,T", [(1024, 65537, 1), (2048, 65537, 32), (4096, 12289, 128), (2048, 65537, 64)])
+def test_flood_bits_max_matches_oracle_bound(F, n, p, T):
+    """The largest admissible HomShare flooding (host arithmetic, no GPU)
+    against the oracle's independent noise bound."""
+    P = O.params(n, p)
+    f = F.flood_bits_max(n, p, T)
+    assert O.noise_ok(P, T, f) and not O.noise_ok(P, T, f + 1)

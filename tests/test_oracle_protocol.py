@@ -239,3 +239,49 @@ def test_two_layer_chain_with_pooling_reconstructs_the_network():
                     h2[0, co] += int(w2[co, ci, a, c]) * np.roll(np.roll(pooled[0, ci], a, 0), c, 1)
     h2 = (h2 % p).astype(np.int64)
     assert np.array_equal((o2["yA"].astype(np.int64) + o2["yB"]) % p, h2)
+
+
+def _max_flood(P, T):
+    f = 0
+    while f < 62 and O.noise_ok(P, T, f + 1):
+        f += 1
+    return f
+
+
+def test_noise_flooding_keeps_the_shares_and_stays_in_the_bound():
+    """HomShare noise flooding (circuit privacy, not in the paper): the mask
+    plaintext carries a uniform error of 2^f per coefficient.  At the largest
+    f the noise bound admits, decryption still rounds it away: the final
+    shares are those of the unflooded run, the ciphertexts differ, and the
+    decryption noise grows to the flood's size but stays under the bound."""
+    p, n = 65537, 1024
+    P = O.params(n, p)
+    L = O.layer(P, 1, 4, 4, 16, 16)
+    f = _max_flood(P, L.T)
+    assert 40 <= f <= 43 and not O.noise_ok(P, L.T, f + 1)
+    g = np.random.default_rng(12)
+    xA = g.integers(0, p, (1, 4, 16, 16)).astype(np.uint32)
+    xB = g.integers(0, p, (1, 4, 16, 16)).astype(np.uint32)
+    w = g.integers(-8, 8, (4, 4, 3, 3)).astype(np.int8)
+    plain = O.round_trip(P, L, xA, xB, w, 1, 2, 3)
+    flood = O.round_trip(P, L, xA, xB, w, 1, 2, 3, flood_bits=f)
+    assert np.array_equal(plain["yA"], flood["yA"]) and np.array_equal(plain["yB"], flood["yB"])
+    assert not np.array_equal(plain["ct_out"], flood["ct_out"])
+    assert flood["noise"].max() > 2 ** (f - 1)  # the flood dominates the noise
+    assert flood["noise"].max() < 2 ** O.noise_bound_log2(P, L.T) + 2 ** f
+
+
+def test_flood_error_is_uniform_on_its_interval():
+    """INTT_q of (flooded mask - plain mask) is the flood error itself: every
+    coefficient in [-2^f, 2^f), the interval's two halves about equally hit."""
+    p, n, f = 65537, 1024, 20
+    P = O.params(n, p)
+    L = O.layer(P, 1, 4, 8, 16, 16)
+    M0, s0 = O.mask_prepare(P, L, 77)
+    M1, s1 = O.mask_prepare(P, L, 77, f)
+    assert np.array_equal(s0, s1)
+    d = ((M1.astype(object) - M0.astype(object)) % P.q).astype(np.uint64)
+    e = np.array([[int(v) if v < P.q // 2 else int(v) - P.q for v in O.intt_q(P, row)] for row in d], dtype=np.int64)
+    assert e.min() >= -(1 << f) and e.max() < (1 << f)
+    assert e.min() < -(1 << (f - 1)) and e.max() > (1 << (f - 1))
+    assert abs(np.mean(e >= 0) - 0.5) < 0.02
