@@ -42,6 +42,8 @@ struct DevParams {
     const ulonglong2* qinv2;
     const uint2* pfw2;       // k < S
     const uint2* pinv2;
+    const uint2* lpf;        // line twiddles: (w_L^k, companion) at L/2 + k, L <= lmax
+    const uint2* lpi;        // the same for w_L^-k
 };
 
 // A layer with its packing, derived (all counts fit in 32 bits).

@@ -431,6 +431,13 @@ __device__ __forceinline__ void stage_wait() {
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
 }
+// Completes every copy group but the N most recently committed ones (each
+// stage_async call commits one group) and synchronises the CTA.
+template <int N>
+__device__ __forceinline__ void stage_wait_groups() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+    __syncthreads();
+}
 
 // Programmatic dependent launch.  A kernel launched with programmatic stream
 // serialisation may start while the kernel before it in the stream is still
@@ -681,11 +688,10 @@ __device__ __forceinline__ void lines_r8p(u32* buf, u32 planes, bool rows, u32 l
     }
 }
 
-// Compact (w_L^k, companion) table for k < L/2, gathered from the params'
-// w_lmax table; plain loads by the whole CTA (no barrier).
-__device__ __forceinline__ void load_pairs_for_length(uint2* dst, u32 logL, bool inverse, const DevParams& P) {
-    const u32* g = inverse ? P.w2di : P.w2d;
-    const u32* gs = inverse ? P.w2di_s : P.w2d_s;
-    const u32 half = 1u << (logL - 1), sh = P.loglmax - logL;
-    for (u32 k = threadIdx.x; k < half; k += blockDim.x) dst[k] = make_uint2(__ldg(g + (k << sh)), __ldg(gs + (k << sh)));
+// Asynchronous copy of the (w_L^k, companion) pairs, k < L/2 (L = 2^logL
+// >= 4), into dst (16-byte aligned); completed by stage_wait().
+__device__ __forceinline__ void stage_pairs_for_length(uint2* dst, u32 logL, bool inverse, const DevParams& P) {
+    const u32 half = 1u << (logL - 1);
+    stage_async(dst, (inverse ? P.lpi : P.lpf) + half, half * 8);
 }
+

@@ -271,6 +271,17 @@ extern "C" int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_p
         qinv2[2 * k] = qinv[k];
         qinv2[2 * k + 1] = qinv_s[k];
     }
+    // line twiddles of every length L <= lmax, (w_L^k, companion) at entry
+    // L/2 + k (k < L/2): a length's pairs are contiguous and 16-byte aligned
+    std::vector<u32> lpf(2ull * lmax, 0), lpi(2ull * lmax, 0);
+    for (u32 Ll = 2; Ll <= lmax; Ll *= 2)
+        for (u32 k = 0; k < Ll / 2; k++) {
+            const u32 idx = Ll / 2 + k, src = k * (lmax / Ll);
+            lpf[2 * idx] = w2[src];
+            lpf[2 * idx + 1] = w2s[src];
+            lpi[2 * idx] = w2i[src];
+            lpi[2 * idx + 1] = w2is[src];
+        }
     std::vector<u32> pfw2(2ull * S), pinv2(2ull * S);
     for (u32 k = 0; k < S; k++) {
         pfw2[2 * k] = pfw[k];
@@ -281,7 +292,7 @@ extern "C" int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_p
 
     // one allocation: [qfw | qfw_s | qinv | qinv_s] [cdt] [pfw .. pinv_s] [w2 .. w2is]
     const size_t bytes_q = 4ull * n * 8, bytes_cdt = 19 * 8 + 8, bytes_p = 4ull * S * 4, bytes_w = 4ull * half * 4;
-    const size_t total = 2 * bytes_q + bytes_cdt + 2 * bytes_p + bytes_w + 256;
+    const size_t total = 2 * bytes_q + bytes_cdt + 2 * bytes_p + bytes_w + 16ull * lmax + 256;
     fdsc_params* P = new (std::nothrow) fdsc_params();
     if (!P) return fdsc_set_error(FDSC_ERR_OOM, "host allocation failed");
     P->info = I;
@@ -311,6 +322,7 @@ extern "C" int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_p
     size_t o_w2i = put(w2i.data(), 4ull * half), o_w2is = put(w2is.data(), 4ull * half);
     size_t o_qfw2 = put(qfw2.data(), 16ull * n), o_qinv2 = put(qinv2.data(), 16ull * n);
     size_t o_pfw2 = put(pfw2.data(), 8ull * S), o_pinv2 = put(pinv2.data(), 8ull * S);
+    size_t o_lpf = put(lpf.data(), 8ull * lmax), o_lpi = put(lpi.data(), 8ull * lmax);
     if (off > total) {  // layout bookkeeping error: never write past the allocation
         cudaFree(P->table_mem);
         delete P;
@@ -349,6 +361,7 @@ extern "C" int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_p
     D.w2di = (const u32*)(dbase + o_w2i); D.w2di_s = (const u32*)(dbase + o_w2is);
     D.qfw2 = (const ulonglong2*)(dbase + o_qfw2); D.qinv2 = (const ulonglong2*)(dbase + o_qinv2);
     D.pfw2 = (const uint2*)(dbase + o_pfw2); D.pinv2 = (const uint2*)(dbase + o_pinv2);
+    D.lpf = (const uint2*)(dbase + o_lpf); D.lpi = (const uint2*)(dbase + o_lpi);
     *out = P;
     return FDSC_OK;
 }

@@ -93,25 +93,20 @@ __global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLaye
     extern __shared__ __align__(16) unsigned char sm[];
     const u32 n = P.n, S = P.S;
     const u32 np = padded_len(n);                        // padded length (even)
-    ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n]
-    u64* c = reinterpret_cast<u64*>(tq + n);             // padded [n]
-    uint2* tp = reinterpret_cast<uint2*>(c + np);        // [S] (psi_p^-brv, companion)
-    u32* slots = reinterpret_cast<u32*>(tp + S);         // padded [n] = d slot sets
-    uint2* tw_row = reinterpret_cast<uint2*>(slots + np); // [W/2]
+    ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^brv, companion)
+    uint2* tp = reinterpret_cast<uint2*>(tq + n);        // [S] (psi_p^-brv, companion)
+    uint2* tw_row = tp + S;                              // [W/2]
     uint2* tw_col = tw_row + (L.W >> 1);                 // [H/2]
-    stage_async(tq, P.qfw2, n * 16);
-    stage_async(tp, P.pinv2, S * 8);
-    load_pairs_for_length(tw_row, L.logW, false, P);
-    load_pairs_for_length(tw_col, L.logH, false, P);
+    u64* c = reinterpret_cast<u64*>(tw_col + (L.H >> 1));  // padded [n]
+    u32* slots = reinterpret_cast<u32*>(c + np);         // padded [n] = d slot sets
     griddep_release();
     griddep_wait();
 
     const u32 u = blockIdx.x, k = u % L.T, bb = u / L.T;
     const u32 HW = L.HW, logHW = L.logH + L.logW, blocks = L.g_c * L.g_b;
-    // planes of the packed slot vector, loaded in bit-reversed order along
-    // both axes; each thread issues its eight loads before storing any
-    for (u32 e0 = 0; e0 < n; e0 += 8 * blockDim.x) {
-        u32 v[8];
+    // every load is issued before anything waits: the share's words (eight
+    // per thread), then the twiddle tables in the order they are needed
+    auto load8 = [&](u32 e0, u32 (&v)[8]) {
 #pragma unroll
         for (int t = 0; t < 8; t++) {
             const u32 e = e0 + threadIdx.x + (u32)t * blockDim.x;
@@ -122,24 +117,38 @@ __global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLaye
                 if (b < L.B && ci < L.Ci) v[t] = __ldg(x + ((u64)b * L.Ci + ci) * HW + f);
             }
         }
+    };
+    // planes of the packed slot vector, in bit-reversed order along both axes
+    auto store8 = [&](u32 e0, const u32 (&v)[8]) {
 #pragma unroll
         for (int t = 0; t < 8; t++) {
             const u32 e = e0 + threadIdx.x + (u32)t * blockDim.x, f = e & (HW - 1);
             const u32 pos = (e & ~(HW - 1)) + (brv_bits(f >> L.logW, L.logH) << L.logW) + brv_bits(f & (L.W - 1), L.logW);
             if (e < n) slots[padx(pos)] = v[t];
         }
+    };
+    u32 v[8];
+    load8(0, v);
+    stage_pairs_for_length(tw_row, L.logW, false, P);  // group 3
+    stage_pairs_for_length(tw_col, L.logH, false, P);  // group 2
+    stage_async(tp, P.pinv2, S * 8);                    // group 1
+    stage_async(tq, P.qfw2, n * 16);                    // group 0
+    store8(0, v);
+    for (u32 e0 = 8 * blockDim.x; e0 < n; e0 += 8 * blockDim.x) {
+        load8(e0, v);
+        store8(e0, v);
     }
-    __syncthreads();
+    stage_wait_groups<2>();  // line twiddles (and the planes) in place
     // NTT2D of every plane (zero planes included): rows, then columns
     lines_r8p<false>(slots, n >> logHW, true, L.logH, L.logW, tw_row, P.p);
     lines_r8p<false>(slots, n >> logHW, false, L.logH, L.logW, tw_col, P.p);
-    stage_wait();
+    stage_wait_groups<1>();
     ntt_r8p<false, u32>(slots, P.logS, P.d, tp, P.Sinv, P.Sinv_s, P);  // slot encode
     for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
         const u32 r = e >> P.logS, i = e & (S - 1);
         c[padx(r + P.d * i)] = P.delta * slots[padx(e)];
     }
-    __syncthreads();
+    stage_wait_groups<0>();
     ntt_r8p<true, u64>(c, P.logn, 1, tq, 0, 0, P);
     if (kMode == 0) {
         u64* A = out + (u64)u * n;
@@ -168,18 +177,14 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
     const u32 n = P.n, S = P.S;
     const u32 np = padded_len(n);
     ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^-brv, companion)
-    u64* c = reinterpret_cast<u64*>(tq + n);             // padded [n]
-    uint2* tp = reinterpret_cast<uint2*>(c + np);        // [S] (psi_p^brv, companion)
-    u32* slots = reinterpret_cast<u32*>(tp + S);         // padded [n]
+    uint2* tp = reinterpret_cast<uint2*>(tq + n);        // [S] (psi_p^brv, companion)
+    uint2* tw_row = tp + S;                              // [W/2]
+    uint2* tw_col = tw_row + (L.W >> 1);                 // [H/2]
+    u64* c = reinterpret_cast<u64*>(tw_col + (L.H >> 1));  // padded [n]
+    u32* slots = reinterpret_cast<u32*>(c + np);         // padded [n]
     const u32 HW = L.HW, logHW = L.logH + L.logW;
     const u32 nplanes = P.d * L.g_b;
     u32* planes = slots + np;                            // padded [d g_b HW]
-    uint2* tw_row = reinterpret_cast<uint2*>(planes + padded_len(nplanes * HW));
-    uint2* tw_col = tw_row + (L.W >> 1);
-    stage_async(tq, P.qinv2, n * 16);
-    stage_async(tp, P.pfw2, S * 8);
-    load_pairs_for_length(tw_row, L.logW, true, P);
-    load_pairs_for_length(tw_col, L.logH, true, P);
     griddep_release();
     griddep_wait();
 
@@ -187,9 +192,11 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
     t_hat += (u64)bb * key_stride;
     const u64* c0 = ct + (u64)v * 2 * n;
     const u64* c1 = c0 + n;
-    // v = c0 t + c1; each thread issues the loads of four elements at a time
-    for (u32 j0 = 0; j0 < n; j0 += 4 * blockDim.x) {
-        u64 a[4], t[4], b[4];
+    // v = c0 t + c1, four elements' loads in flight per thread; the first
+    // batch is issued before the twiddle tables, which are copied in the
+    // order they are needed
+    u64 a[4], t[4], b[4];
+    auto load4 = [&](u32 j0) {
 #pragma unroll
         for (int r = 0; r < 4; r++) {
             const u32 j = j0 + threadIdx.x + (u32)r * blockDim.x;
@@ -199,19 +206,31 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
                 b[r] = __ldg(c1 + j);
             }
         }
+    };
+    auto mac4 = [&](u32 j0) {
 #pragma unroll
         for (int r = 0; r < 4; r++) {
             const u32 j = j0 + threadIdx.x + (u32)r * blockDim.x;
             if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
         }
+    };
+    load4(0);
+    stage_async(tq, P.qinv2, n * 16);                  // group 3
+    stage_async(tp, P.pfw2, S * 8);                    // group 2
+    stage_pairs_for_length(tw_row, L.logW, true, P);  // group 1
+    stage_pairs_for_length(tw_col, L.logH, true, P);  // group 0
+    mac4(0);
+    for (u32 j0 = 4 * blockDim.x; j0 < n; j0 += 4 * blockDim.x) {
+        load4(j0);
+        mac4(j0);
     }
-    stage_wait();
+    stage_wait_groups<3>();
     ntt_r8p<false, u64>(c, P.logn, 1, tq, P.ninv, P.ninv_s, P);
     for (u32 coef = threadIdx.x; coef < n; coef += blockDim.x) {
         const u32 r = coef & (P.d - 1), i = coef / P.d;
         slots[padx(r * S + i)] = round_pq2(c[padx(coef)], P);
     }
-    __syncthreads();
+    stage_wait_groups<2>();
     ntt_r8p<true, u32>(slots, P.logS, P.d, tp, 0, 0, P);  // slot decode
     // fold the g_c channel blocks of every image block: plane (r, ib)
     for (u32 e = threadIdx.x; e < nplanes * HW; e += blockDim.x) {
@@ -221,7 +240,7 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
         for (u32 ic = 0; ic < L.g_c; ic++) acc = addmod_p(acc, slots[padx(src + ic * HW)], P.p);
         planes[padx(e)] = acc;
     }
-    __syncthreads();
+    stage_wait_groups<0>();
     lines_r8p<true>(planes, nplanes, true, L.logH, L.logW, tw_row, P.p);
     lines_r8p<true>(planes, nplanes, false, L.logH, L.logW, tw_col, P.p);
     for (u32 e = threadIdx.x; e < nplanes * HW; e += blockDim.x) {
