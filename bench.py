@@ -701,6 +701,8 @@ def run_gpu(args, rank, local_rank, world):
 
     # NTT2D over a batch sweep of 32x32 planes (64 per image)
     sweep = ntt2d_sweep(F, P, ls, back_to_back, args)
+    # the ALU side of the roofline: measured rates of the exact primitives
+    calib = {name: F.calibrate(P, i) for i, name in enumerate(("mac_60x60_128", "shoup_mulmod_q", "shoup_mulmod_p"))}
     clk = clocks.stop()
 
     # end to end through the C ABI with HOST buffers: the serving API, closed loop
@@ -723,12 +725,29 @@ def run_gpu(args, rank, local_rank, world):
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
-    achieved = alg_bytes / (hc_avg * 1e-3) / 1e9
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         tr = json.load(open(TRAFFIC_FILE))
         if tr.get("kernel_digest") == kernel_digest() and tr.get("workload") == WORKLOAD:
             traffic = tr.get("dram_bytes_per_launch")
+    achieved = alg_bytes / (hc_avg * 1e-3) / 1e9
+    mac_rate = calib["mac_60x60_128"][0]
+    t_hbm_us, t_alu_us = alg_bytes / (peak * 1e9) * 1e6, macs / mac_rate * 1e6
+    bound = "hbm" if t_hbm_us >= t_alu_us else "alu"
+    achieved_mac = macs / (hc_avg * 1e-3)
+    hbm_side = {"achieved": achieved, "peak": peak, "peak_source": peak_src + " (hbm_gbs, burst copy)",
+                "unit": "GB/s", "frac": achieved / peak, "t_us": t_hbm_us}
+    alu_side = {"achieved": achieved_mac / 1e12, "peak": mac_rate / 1e12, "unit": "TMAC/s",
+                "frac": achieved_mac / mac_rate, "t_us": t_alu_us, "mac_per_clk_per_sm": calib["mac_60x60_128"][1],
+                "peak_source": "measured here (fdsc_calibrate: register-resident loop-carried chains of HomConv's "
+                               "exact 60x60->128-bit multiply-accumulate on every SM)"}
+    main = hbm_side if bound == "hbm" else alu_side
+    roofline = {"kernel": "homconv_kernel (homconv_sum: HomRec addends + HomConv + HomShare)", "bound": bound,
+                "achieved": main["achieved"], "peak": main["peak"], "peak_source": main["peak_source"],
+                "unit": main["unit"], "frac": main["frac"], "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                "macs_per_launch": macs, "launch_us": hc_avg * 1e3,
+                "timing": "%d launches back to back over the %d instances (cold), CUDA events" % (hc_reps * R, R),
+                "hbm": hbm_side, "alu": alu_side}
     useful_macs = 2 * ls.Co * ls.Ci * ls.H * ls.W * ls.B
     cpu = None
     if not args.no_cpu_baseline:
@@ -756,11 +775,7 @@ def run_gpu(args, rank, local_rank, world):
         "step_ms_p50": float(np.percentile(step_ms, 50)), "step_ms_p99": float(np.percentile(step_ms, 99)),
         "step_ms_distribution": "%d steps with an event at every boundary" % len(step_ms),
         "step_by_step_ms": unfused_ms,
-        "roofline": {"kernel": "homconv_kernel (homconv_sum: HomRec addends + HomConv + HomShare)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "peak_source": peak_src + " (hbm_gbs, burst copy)",
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
-                     "launch_us": hc_avg * 1e3,
-                     "timing": "%d launches back to back over the %d instances (cold), CUDA events" % (hc_reps * R, R)},
+        "roofline": roofline,
         "e2e": {"value": e2e_units / e2e_sec, "unit": "layers/s", "h2d_bytes_per_step": e2e["h2d"],
                 "d2h_bytes_per_step": e2e["d2h"], "requests": e2e["requests"], "p50_us": e2e["p50_us"],
                 "p99_us": e2e["p99_us"], "mean_batch": e2e["mean_batch"],
@@ -770,6 +785,7 @@ def run_gpu(args, rank, local_rank, world):
         "chain": chain,
         "serving": serving,
         "ntt2d_sweep": sweep,
+        "primitive_rates": {k: {"ops_per_s": v[0], "ops_per_clk_per_sm": v[1]} for k, v in calib.items()},
         "gpu_launches": LAUNCHES_PER_STEP * (args.steps + len(step_ms)) + 8 * n_unfused + 3 * hc_reps * R
                         + sum(pt["launches"] for pt in sweep["points"]),
         "homconv_variant": args.homconv_variant,

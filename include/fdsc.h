@@ -447,6 +447,15 @@ int fdsc_set_homconv_variant(int variant);
  * launches issued after the call, process-wide. */
 int fdsc_set_launch_overlap(int on);
 
+/* Measured throughput of the exact arithmetic primitives on the current
+ * device (the ALU side of the roofline): which = 0, the 60 x 60 -> 128-bit
+ * multiply-accumulate of HomConv; 1, the 64-bit Shoup multiplication mod q
+ * of the NTT_q butterflies; 2, the 32-bit Shoup multiplication mod p of the
+ * NTT2D and slot transforms.  Register-resident, loop-carried chains on every
+ * SM; returns operations per second and per clock per SM (SM count and clock
+ * from the device attributes).  Synchronous; a few milliseconds. */
+int fdsc_calibrate(const fdsc_params* P, int which, double* ops_per_s, double* ops_per_clk_sm);
+
 #ifdef __cplusplus
 }
 #endif

@@ -475,3 +475,89 @@ cudaError_t launch_homconv_seeded(const DevParams& P, const DevLayer& L, u64 see
     if (L.T > 256) return cudaErrorInvalidValue;
     return launch_v3<0>(P, L, c1, A1, A2, Phat, Mhat, ct_out, s, seed, 1);
 }
+
+// ---------------------------------------------------------------- throughput of the exact primitives
+// Register-resident loops of the arithmetic the hot kernels are built from,
+// each chain loop-carried (an operand depends on the previous result) so
+// nothing is hoisted: 0 = the 60 x 60 -> 128-bit multiply-accumulate of
+// HomConv (acc_mac), 1 = the 64-bit Shoup multiplication of the NTT_q
+// butterflies, 2 = the 32-bit Shoup multiplication of the mod-p transforms.
+// Four independent chains per thread.
+namespace {
+__global__ void __launch_bounds__(256) calib_kernel(int which, u32 iters, u64 w, u64 ws, u64 q, u64* sink, int store) {
+    u64 r = threadIdx.x;
+    if (which == 0) {
+        Acc128 acc[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) acc_zero(acc[i]);
+        u64 x[4] = {w ^ threadIdx.x, w + 1, w + 2, w + 3};
+        for (u32 it = 0; it < iters; it++) {
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                acc_mac(acc[i], x[i], ws);
+                x[i] ^= acc[i].w[1];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) r ^= acc[i].w[0] ^ acc[i].w[3];
+    } else if (which == 1) {
+        u64 x[4] = {w ^ threadIdx.x, w + 1, w + 2, w + 3};
+        for (u32 it = 0; it < iters; it++) {
+#pragma unroll
+            for (int i = 0; i < 4; i++) x[i] = shoup_mul(x[i], w, ws, q);
+        }
+        r ^= x[0] ^ x[1] ^ x[2] ^ x[3];
+    } else {
+        u32 x[4] = {(u32)w ^ threadIdx.x, (u32)w + 1, (u32)w + 2, (u32)w + 3};
+        for (u32 it = 0; it < iters; it++) {
+#pragma unroll
+            for (int i = 0; i < 4; i++) x[i] = shoup_mul32(x[i], (u32)w, (u32)ws, (u32)q);
+        }
+        r ^= x[0] ^ x[1] ^ x[2] ^ x[3];
+    }
+    if (store) sink[blockIdx.x * blockDim.x + threadIdx.x] = r;  // a run-time flag (0): the loops stay
+}
+}  // namespace
+
+extern "C" int fdsc_calibrate(const fdsc_params* P, int which, double* ops_per_s, double* ops_per_clk_sm) {
+    if (!P || which < 0 || which > 2 || !ops_per_s || !ops_per_clk_sm) return fdsc_set_error(FDSC_ERR_ARG, "bad arguments");
+    int dev = 0, sms = 0, khz = 0;
+    cudaGetDevice(&dev);
+    if (dev != P->device) return fdsc_set_error(FDSC_ERR_ARG, "params belong to another device");
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    const DevParams& D = P->dev;
+    u64 w, ws, q;
+    if (which == 2) {
+        q = D.p;
+        w = 3;  // any residue below p; its companion follows
+        ws = ((u64)w << 32) / q;
+    } else {
+        q = D.q;
+        w = D.delta % q;
+        ws = (u64)(((unsigned __int128)w << 64) / q);
+    }
+    u64* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&sink, (size_t)sms * 8 * 256 * sizeof(u64));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const u32 blocks = (u32)sms * 8, threads = 256, iters = which == 0 ? 2000 : 8000;
+    float ms = 0;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {  // the first run warms up
+        cudaEventRecord(e0);
+        calib_kernel<<<blocks, threads>>>(which, iters, w, ws, q, sink, 0);
+        cudaEventRecord(e1);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sink) cudaFree(sink);
+    if (e != cudaSuccess) return fdsc_set_error(FDSC_ERR_CUDA, "calibrate: %s", cudaGetErrorString(e));
+    const double ops = (double)blocks * threads * iters * 4;
+    *ops_per_s = ops / (ms * 1e-3);
+    *ops_per_clk_sm = *ops_per_s / ((double)khz * 1e3) / sms;
+    return FDSC_OK;
+}

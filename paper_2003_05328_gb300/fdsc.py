@@ -74,6 +74,7 @@ _SIGS = {
     "fdsc_decrypt": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
     "fdsc_set_homconv_variant": (C.c_int, [C.c_int]),
     "fdsc_set_launch_overlap": (C.c_int, [C.c_int]),
+    "fdsc_calibrate": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "fdsc_encrypt_constants": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp]),
     "fdsc_encode_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
     "fdsc_homrec_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
@@ -296,6 +297,14 @@ def flood_bits_max(n: int, p: int, T: int) -> int:
 def set_homconv_variant(v: int) -> None:
     """Kernel variant for HomConv (0 automatic; results are identical)."""
     _call("fdsc_set_homconv_variant", v)
+
+
+def calibrate(P: Params, which: int):
+    """(ops/s, ops per clock per SM) of primitive `which`: 0 HomConv's exact
+    MAC, 1 the 64-bit Shoup mulmod, 2 the 32-bit one."""
+    a, b = C.c_double(0), C.c_double(0)
+    _call("fdsc_calibrate", P.handle, which, C.byref(a), C.byref(b))
+    return a.value, b.value
 
 
 def set_launch_overlap(on: bool) -> bool:

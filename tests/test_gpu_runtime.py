@@ -282,3 +282,17 @@ def test_noise_flooding_masks_and_shares(F):
     assert np.array_equal(u32(d["yB"]).reshape(ref["yB"].shape), ref["yB"])
     plan.close()
     P.close()
+
+
+def test_calibration_rates_are_plausible(F):
+    """The measured rates of the exact primitives: positive, below the
+    SM's issue rate (128 thread-instructions per clock), the 128-bit MAC
+    slower than a 32-bit modular multiply."""
+    P = F.Params(2048, 65537, max_T=8)
+    rates = [F.calibrate(P, i) for i in range(3)]
+    for per_s, per_clk in rates:
+        assert per_s > 0 and 0 < per_clk < 128
+    assert rates[0][1] < rates[2][1]
+    with pytest.raises(F.FdscError):
+        F.calibrate(P, 3)
+    P.close()
