@@ -296,3 +296,28 @@ def test_calibration_rates_are_plausible(F):
     with pytest.raises(F.FdscError):
         F.calibrate(P, 3)
     P.close()
+
+
+def test_new_entry_points_reject_bad_arguments(F):
+    """Argument checks of the seeded, pooling and flooding calls: errors
+    come back as status codes, nothing is launched."""
+    P = F.Params(64, 65537, max_T=400)
+    L = F.LayerSpec(1, 300, 3, 8, 8, 1, 1)  # T = 300 input ciphertexts: more than the seeded HomConv stages
+    lay = F.layout(P, L)
+    c1 = torch.zeros(lay.n_in * 64, dtype=torch.int64, device="cuda")
+    Ph = torch.zeros(lay.filter_words, dtype=torch.int64, device="cuda")
+    with pytest.raises(F.FdscError) as e:
+        F.homconv_seeded(P, L, 1, c1, None, None, Ph)
+    assert e.value.code == -5
+    x = torch.zeros((2, 8, 8), dtype=torch.int32, device="cuda")
+    with pytest.raises(F.FdscError) as e:
+        F.pool2x2_sum(P, x, out=x.view(-1)[: 2 * 16].view(2, 4, 4))  # output inside the input
+    assert e.value.code == -1
+    xin = torch.zeros((1, 3, 8, 8), dtype=torch.int32, device="cuda")
+    yout = torch.zeros((1, 2, 8, 8), dtype=torch.int32, device="cuda")
+    with pytest.raises(F.FdscError) as e:  # a plan layer whose flooding breaks the bound
+        F.Plan([dict(params=P, layer=F.LayerSpec(1, 3, 2, 8, 8, 0, 0),
+                     w=dev(np.ones((2, 3, 3, 3), np.int8), np.int8), t_hat=F.keygen(P, 1), enc_seed=1, mask_seed=2,
+                     xA=xin, xB=xin, yA=yout, yB=yout.clone(), flood_bits=60)])
+    assert e.value.code == -2
+    P.close()
