@@ -4,10 +4,12 @@
 // server with HBM-budget admission.  Host C++ only; all arithmetic stays in the
 // kernels of the other translation units.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -397,6 +399,84 @@ struct ServerType {
     int variant;
 };
 
+// Host copies of one batch (request inputs into the lane's pinned staging,
+// results out to the callers' buffers), split into chunks and shared by a
+// few persistent threads and the calling (worker) thread.  run() returns when
+// every chunk is copied and every pool thread has left the generation, so the
+// chunk list can be refilled.
+class CopyPool {
+  public:
+    struct Job {
+        void* dst;
+        const void* src;
+        size_t bytes;
+    };
+    explicit CopyPool(unsigned threads) {
+        for (unsigned i = 0; i < threads; i++) th_.emplace_back([this] { loop(); });
+    }
+    ~CopyPool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& t : th_) t.join();
+    }
+    void run(const std::vector<Job>& jobs) {
+        size_t total = 0;
+        for (const Job& j : jobs) total += j.bytes;
+        if (total <= kInline) {  // small batches: waking the pool costs more than it saves
+            for (const Job& j : jobs) memcpy(j.dst, j.src, j.bytes);
+            return;
+        }
+        chunks_.clear();
+        for (const Job& j : jobs)
+            for (size_t off = 0; off < j.bytes; off += kChunk)
+                chunks_.push_back({static_cast<char*>(j.dst) + off, static_cast<const char*>(j.src) + off,
+                                   std::min(kChunk, j.bytes - off)});
+        if (chunks_.empty()) return;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            next_.store(0);
+            left_ = th_.size();
+            gen_++;
+        }
+        cv_.notify_all();
+        work();
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_done_.wait(lk, [&] { return left_ == 0; });
+    }
+
+  private:
+    static constexpr size_t kChunk = 256 << 10, kInline = 1 << 20;
+    void work() {
+        for (size_t i = next_.fetch_add(1); i < chunks_.size(); i = next_.fetch_add(1))
+            memcpy(chunks_[i].dst, chunks_[i].src, chunks_[i].bytes);
+    }
+    void loop() {
+        uint64_t seen = 0;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+                if (stop_) return;
+                seen = gen_;
+            }
+            work();
+            std::lock_guard<std::mutex> lk(mu_);
+            if (--left_ == 0) cv_done_.notify_all();
+        }
+    }
+    std::vector<std::thread> th_;
+    std::vector<Job> chunks_;
+    std::atomic<size_t> next_{0};
+    std::mutex mu_;
+    std::condition_variable cv_, cv_done_;
+    uint64_t gen_ = 0;
+    size_t left_ = 0;
+    bool stop_ = false;
+};
+
 struct Req {
     fdsc_request r;
     uint64_t ticket;
@@ -436,6 +516,7 @@ struct fdsc_server {
     int error = FDSC_OK;
     bool started = false, stop = false;
     std::thread worker;
+    std::unique_ptr<CopyPool> copies;
     // largest per-request sizes over the types (elements)
     uint64_t max_in = 0, max_out = 0, max_ct_in = 0, max_add = 0, max_ct_out = 0, max_mask = 0, max_n = 0;
 };
@@ -462,13 +543,15 @@ int launch_batch(fdsc_server* S, Lane& ln) {
     int rc = fdsc_make_layer(t.P->info, &LG, &D, &lay);
     if (rc) return rc;
     const uint64_t in_img = t.lay1.in_spectra_words, out_img = t.lay1.out_spectra_words, n = t.P->info.n;
+    std::vector<CopyPool::Job> jobs;
     for (uint32_t b = 0; b < G; b++) {
         const fdsc_request& r = ln.batch[b].r;
-        memcpy(ln.h_xA + b * in_img, r.xA, in_img * 4);
-        memcpy(ln.h_xB + b * in_img, r.xB, in_img * 4);
+        jobs.push_back({ln.h_xA + b * in_img, r.xA, in_img * 4});
+        jobs.push_back({ln.h_xB + b * in_img, r.xB, in_img * 4});
         ln.h_seeds[b] = r.enc_seed;
         ln.h_seeds[G + b] = r.mask_seed;
     }
+    S->copies->run(jobs);
     cudaStream_t s = ln.stream;
     RT_TRY(cudaMemcpyAsync(ln.xA, ln.h_xA, G * in_img * 4, cudaMemcpyHostToDevice, s));
     RT_TRY(cudaMemcpyAsync(ln.xB, ln.h_xB, G * in_img * 4, cudaMemcpyHostToDevice, s));
@@ -493,14 +576,16 @@ int launch_batch(fdsc_server* S, Lane& ln) {
 void finish_batch(fdsc_server* S, Lane& ln, bool ok) {
     const ServerType& t = S->types[ln.type];
     const uint64_t out_img = t.lay1.out_spectra_words;
-    const auto now = Clock::now();
-    for (size_t b = 0; b < ln.batch.size(); b++) {
-        const fdsc_request& r = ln.batch[b].r;
-        if (ok) {
-            memcpy(r.yA, ln.h_yA + b * out_img, out_img * 4);
-            memcpy(r.yB, ln.h_yB + b * out_img, out_img * 4);
+    if (ok) {
+        std::vector<CopyPool::Job> jobs;
+        for (size_t b = 0; b < ln.batch.size(); b++) {
+            const fdsc_request& r = ln.batch[b].r;
+            jobs.push_back({r.yA, ln.h_yA + b * out_img, out_img * 4});
+            jobs.push_back({r.yB, ln.h_yB + b * out_img, out_img * 4});
         }
+        S->copies->run(jobs);
     }
+    const auto now = Clock::now();
     std::lock_guard<std::mutex> lk(S->mu);
     for (auto& q : ln.batch) {
         const double us = std::chrono::duration<double, std::micro>(now - q.t_submit).count();
@@ -586,7 +671,9 @@ void worker_loop(fdsc_server* S) {
             continue;
         }
         lk.unlock();
-        std::this_thread::sleep_for(std::chrono::microseconds(any_busy ? 5 : 0));
+        // batches in flight: poll again at once (a timed sleep would add tens of
+        // microseconds to every request's latency); only yield the core
+        std::this_thread::yield();
     }
 }
 
@@ -664,6 +751,9 @@ extern "C" int fdsc_server_start(fdsc_server* S) {
             cudaMallocHost((void**)&ln.h_seeds, 2 * B * 8) != cudaSuccess)
             return fdsc_set_error(FDSC_ERR_CUDA, "lane setup failed");
     }
+    // host copies: a quarter of the host's threads (2 to 8) besides the worker
+    const unsigned hw = std::thread::hardware_concurrency();
+    S->copies.reset(new CopyPool(std::min(8u, std::max(2u, hw / 4))));
     S->started = true;
     S->worker = std::thread(worker_loop, S);
     return FDSC_OK;
@@ -736,6 +826,7 @@ extern "C" int fdsc_server_destroy(fdsc_server* S) {
         S->cv_work.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
+    S->copies.reset();
     for (auto& ln : S->lanes) {
         if (ln.stream) {
             cudaStreamSynchronize(ln.stream);
