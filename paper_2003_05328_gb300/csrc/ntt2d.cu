@@ -79,8 +79,9 @@ __global__ void __launch_bounds__(512) ntt2d_kernel(DevParams P, u32 logH, u32 l
 // ---------------------------------------------------------------- square planes up to 32 x 32
 // One warp owns 32/N planes of N x N (N = 8, 16, 32); lane j of a plane
 // holds column j in registers, read with coalesced row loads.  Columns, then
-// rows, run unrolled radix-2 DIF (Gentleman-Sande) butterflies with Harvey's
-// lazy reduction (values kept in [0, 2p)); the twiddles w_32^k, k < 16, and
+// rows, run unrolled radix-2 DIF (Gentleman-Sande) butterflies with lazy
+// reduction (only the Shoup products reduce; a final Shoup product by 1 makes
+// the words canonical; needs p 2^(2 LOG) < 2^32); the twiddles w_32^k, k < 16, and
 // their Shoup companions are kernel parameters, so every multiply takes its
 // twiddle straight from the constant bank.  The bit-reversed order the DIF
 // leaves is a fixed register permutation, undone while the plane is
@@ -105,21 +106,26 @@ __device__ __forceinline__ u32 sub_if_ge(u32 x, u32 m) {  // x < 2m -> [0, m)
     return min(x, x - m);
 }
 
+// Unrolled DIF on N = 2^LOG registers whose values are below p 2^s0.  Sums
+// and twiddle-1 differences are not reduced (a level doubles the bound, so
+// after both directions of a 32 x 32 plane it is p 2^10 < 2^27); every other
+// difference is offset by the level's bound and leaves a lazy Shoup product
+// in [0, 2p).  The result is below p 2^(s0 + LOG).
 template <int LOG>
-__device__ __forceinline__ void dif_regs(u32 (&a)[1 << LOG], u32 p, const Tw32& tw) {
+__device__ __forceinline__ void dif_regs(u32 (&a)[1 << LOG], u32 p, u32 s0, const Tw32& tw) {
     constexpr int N = 1 << LOG;
-    const u32 p2 = 2 * p;
 #pragma unroll
-    for (int len = N / 2; len >= 1; len >>= 1) {
+    for (int len = N / 2, lvl = 0; len >= 1; len >>= 1, lvl++) {
+        const u32 bound = p << (s0 + lvl);  // every input of this level is below it
 #pragma unroll
         for (int st = 0; st < N; st += 2 * len) {
 #pragma unroll
             for (int j = 0; j < len; j++) {
                 const u32 u = a[st + j], v = a[st + j + len];
-                a[st + j] = sub_if_ge(u + v, p2);
-                const u32 d = u - v + p2;
+                a[st + j] = u + v;
+                const u32 d = u - v + bound;
                 const int k = j * (16 / len);  // w_{2 len}^j = w_32^(j 32 / (2 len))
-                a[st + j + len] = j == 0 ? sub_if_ge(d, p2) : lazy_mul(d, tw.w[k], tw.ws[k], p);
+                a[st + j + len] = j == 0 ? d : lazy_mul(d, tw.w[k], tw.ws[k], p);
             }
         }
     }
@@ -135,6 +141,7 @@ __global__ void __launch_bounds__(256, 4) ntt2d_reg_kernel(u32 p, Tw32 tw, u32 s
     griddep_wait();
     const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const u32 sub = lane / N, col = lane % N;
+    const u32 one_s = (u32)(0x100000000ull / p);  // Shoup companion of 1
     u32* tr = sm[wid] + sub * N * STR;
     const u64 nwarps = (u64)gridDim.x * 8;
     for (u64 g = (u64)blockIdx.x * 8 + wid; g * PPW < planes; g += nwarps) {
@@ -144,14 +151,14 @@ __global__ void __launch_bounds__(256, 4) ntt2d_reg_kernel(u32 p, Tw32 tw, u32 s
         u32 a[N];
 #pragma unroll
         for (int r = 0; r < N; r++) a[r] = valid ? src[r * N] : 0u;
-        dif_regs<LOG>(a, p, tw);  // column col: a[i] = spectrum at row frequency brv(i)
+        dif_regs<LOG>(a, p, 0, tw);  // column col: a[i] = spectrum at row frequency brv(i), below p 2^LOG
 #pragma unroll
         for (int i = 0; i < N; i++) tr[brv_c<LOG>(i) * STR + col] = a[i];
         __syncwarp();
 #pragma unroll
         for (int c = 0; c < N; c++) a[c] = tr[col * STR + c];  // row col
         __syncwarp();
-        dif_regs<LOG>(a, p, tw);  // a[i] = X[col][brv(i)]
+        dif_regs<LOG>(a, p, LOG, tw);  // a[i] = X[col][brv(i)], below p 2^(2 LOG)
 #pragma unroll
         for (int i = 0; i < N; i++) tr[col * STR + brv_c<LOG>(i)] = a[i];
         __syncwarp();
@@ -159,7 +166,7 @@ __global__ void __launch_bounds__(256, 4) ntt2d_reg_kernel(u32 p, Tw32 tw, u32 s
 #pragma unroll
         for (int r = 0; r < N; r++) {
             u32 v = tr[r * STR + col];
-            if (kInv) v = lazy_mul(v, scale, scale_s, p);
+            v = kInv ? lazy_mul(v, scale, scale_s, p) : lazy_mul(v, 1, one_s, p);  // [0, 2p)
             v = sub_if_ge(v, p);
             if (valid) dst[r * N] = v;
         }
@@ -196,7 +203,7 @@ cudaError_t launch_ntt2d(const DevParams& P, u32 H, u32 W, const u32* x, u32* X,
         scale = fdsc_powmod32(HW % P.p, P.p - 2, P.p);
         scale_s = fdsc_shoup32(scale, P.p);
     }
-    if (logH == logW && logH >= 3 && logH <= 5 && (P.p - 1) % 32 == 0) {
+    if (logH == logW && logH >= 3 && logH <= 5 && (P.p - 1) % 32 == 0 && (u64)P.p << (2 * logH) < (1ull << 32)) {
         Tw32 tw;
         const u32 w32 = fdsc_powmod32(P.g_p, (P.p - 1) / 32, P.p);
         const u32 w = inverse ? fdsc_powmod32(w32, P.p - 2, P.p) : w32;

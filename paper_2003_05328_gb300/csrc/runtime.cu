@@ -196,8 +196,10 @@ void plan_free(fdsc_plan* p) {
     if (!p) return;
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
-    for (auto s : p->streams) cudaStreamDestroy(s);
-    for (auto e : p->events) cudaEventDestroy(e);
+    for (auto s : p->streams)
+        if (s) cudaStreamDestroy(s);  // never the default stream
+    for (auto e : p->events)
+        if (e) cudaEventDestroy(e);
     p->arena.release();
     delete p;
 }
