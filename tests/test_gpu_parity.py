@@ -65,8 +65,8 @@ def _check_layer(F, n, p, B, Ci, Co, H, W, fh, fw=None, g_c=None, g_b=1, seed=0,
 
 # ---------------------------------------------------------------- transforms
 @pytest.mark.parametrize("p", [65537, 12289])
-@pytest.mark.parametrize("H,W,planes", [(2, 2, 3), (4, 64, 5), (64, 4, 2), (8, 8, 7), (16, 16, 64), (32, 32, 64),
-                                        (64, 64, 9), (2, 2048, 2), (32, 32, 2500)])
+@pytest.mark.parametrize("H,W,planes", [(2, 2, 3), (4, 64, 5), (64, 4, 2), (8, 8, 7), (16, 16, 64), (16, 16, 5),
+                                        (32, 32, 1), (32, 32, 64), (64, 64, 9), (2, 2048, 2), (32, 32, 2500)])
 def test_ntt2d_intt2d_match_oracle(F, p, H, W, planes):
     P = F.Params(1024, p)
     x = np.random.default_rng(H * 131 + W + planes).integers(0, p, (planes, H, W)).astype(np.uint32)
@@ -83,6 +83,10 @@ def test_ntt2d_intt2d_match_oracle(F, p, H, W, planes):
     d[0, 0, 0] = 1
     assert np.all(u32(F.ntt2d(P, dev(d, np.int32))) == 1)
     assert np.array_equal(u32(F.intt2d(P, dev(O.ntt2d(x, p), np.int32))).reshape(x.shape), x)
+    # the largest inputs (every word p - 1), where unreduced sums grow the most
+    m = np.full((2, H, W), p - 1, np.uint32)
+    assert np.array_equal(u32(F.ntt2d(P, dev(m, np.int32))).reshape(m.shape), O.ntt2d(m, p))
+    assert np.array_equal(u32(F.intt2d(P, dev(m, np.int32))).reshape(m.shape), O.ntt2d(m, p, inverse=True))
     P.close()
 
 
