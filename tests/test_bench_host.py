@@ -49,3 +49,23 @@ def test_homconv_counts():
     byts, macs = bench.layer_counts(ls, 32, 1, 1, 2048, addends=0)
     assert macs == 2 * 64 * 64 * 32 * 32  # equals the useful MACs: g_c H W = S
     assert byts == 8 * 64 * 32 * 2048 + 8 * (2 * 32 * 2048 + 3 * 64 * 2048)
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference times the oracle on the host and prints one
+    JSON line with the contract's keys (no GPU involved)."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "3", "--warmup", "3"],
+                         cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "layers/s" and d["steps"] == 3 and d["warmup"] == 3
+    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
