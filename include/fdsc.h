@@ -233,6 +233,32 @@ int fdsc_homconv_sum(const fdsc_params* P, const fdsc_layer* L, const uint64_t* 
                      const uint64_t* A2, const uint64_t* P_hat, const uint64_t* M_hat, uint64_t* ct_out,
                      void* stream);
 
+/* HomConv on the tensor cores (the same words as fdsc_homconv_sum).  For
+ * every evaluation index the contraction over the T input ciphertexts is a
+ * matrix product of 60-bit words; each word is split into eight balanced
+ * base-256 digits (held exactly in fp16), the digit products are summed by
+ * tcgen05 MMAs in fp32 into the 15 weight classes 256^kappa (exact: every
+ * partial sum stays below 2^24 for T <= 128), and the classes are combined
+ * into the 128-bit sum and reduced mod q once.
+ * fdsc_filter_tc_words: the size in uint64 words of the digit-ready filter
+ * for layer L at (n, p) (host only); FDSC_ERR_UNSUPPORTED if T > 128.
+ * fdsc_filter_tc: P_hat uint64 [Co][T][beta][n] (fdsc_filter_prepare) ->
+ * P_tc uint64 [beta n][ceil(T/16)][Co][16], each word biased by 0x80..80
+ * (ciphertexts past T hold the bias alone); setup, once per filter.
+ * fdsc_homconv_tc: as fdsc_homconv_sum with P_tc in place of P_hat; ct_out
+ * must not overlap any input.  Launches one persistent CTA per SM.
+ * fdsc_homconv_tc_status: after synchronizing, 0 in *code if no CTA of the
+ * tensor-core kernel gave up a bounded wait since the last call; otherwise
+ * the role that did (1 producer, 2 MMA, 3 epilogue) and FDSC_ERR_TIMEOUT
+ * (that launch's output is not valid).  Resets the flag. */
+int fdsc_filter_tc_words(uint32_t n, uint32_t p, const fdsc_layer* L, uint64_t* words);
+int fdsc_filter_tc(const fdsc_params* P, const fdsc_layer* L, const uint64_t* P_hat, uint64_t* P_tc,
+                   void* stream);
+int fdsc_homconv_tc(const fdsc_params* P, const fdsc_layer* L, const uint64_t* ct_in, const uint64_t* A1,
+                    const uint64_t* A2, const uint64_t* P_tc, const uint64_t* M_hat, uint64_t* ct_out,
+                    void* stream);
+int fdsc_homconv_tc_status(uint32_t* code);
+
 /* Seeded ciphertexts.  In Eq. 1 `a` is uniform and public, so a fresh
  * ciphertext can travel as its encryption seed and c1 alone: half the
  * client-to-server bytes, and half the input words HomConv reads.

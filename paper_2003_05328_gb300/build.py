@@ -20,7 +20,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfdsc.so")
-SOURCES = ["params.cu", "ntt2d.cu", "crypt.cu", "homconv.cu", "pipeline.cu", "runtime.cu", "noalloc.cu", "api.cu"]
+SOURCES = ["params.cu", "ntt2d.cu", "crypt.cu", "homconv.cu", "homconv_tc.cu", "pipeline.cu", "runtime.cu", "noalloc.cu", "api.cu"]
 HEADERS = ["fdsc_internal.h", "modarith.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]

@@ -250,6 +250,68 @@ extern "C" int fdsc_homconv_sum(const fdsc_params* P, const fdsc_layer* L, const
                     "homconv_sum");
 }
 
+// ---------------------------------------------------------------- tensor-core HomConv
+extern "C" int fdsc_filter_tc_words(uint32_t n, uint32_t p, const fdsc_layer* L, uint64_t* words) {
+    if (!L || !words) return fdsc_set_error(FDSC_ERR_ARG, "layer or words is NULL");
+    fdsc_params_info I;
+    int rc = fdsc_derive(n, p, &I);
+    if (rc) return rc;
+    DevLayer D;
+    if ((rc = fdsc_make_layer(I, L, &D, nullptr))) return rc;
+    if (!homconv_tc_supported(n, D))
+        return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "the tensor-core HomConv needs T <= 128 (T = %u)", D.T);
+    *words = filter_tc_words(n, D);
+    return FDSC_OK;
+}
+
+extern "C" int fdsc_filter_tc(const fdsc_params* P, const fdsc_layer* L, const uint64_t* P_hat, uint64_t* P_tc,
+                              void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    fdsc_layout lay;
+    if ((rc = fdsc_make_layer(P->info, L, &D, &lay))) return rc;
+    if (!homconv_tc_supported(P->info.n, D))
+        return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "the tensor-core HomConv needs T <= 128 (T = %u)", D.T);
+    if ((rc = check_ptr(P_hat, "P_hat")) || (rc = check_ptr(P_tc, "P_tc"))) return rc;
+    if (overlap(P_hat, lay.filter_words * 8, P_tc, filter_tc_words(P->info.n, D) * 8))
+        return fdsc_set_error(FDSC_ERR_ARG, "P_tc overlaps P_hat");
+    return launched(launch_filter_tc(P->dev, D, P_hat, P_tc, (cudaStream_t)stream), "filter_tc");
+}
+
+extern "C" int fdsc_homconv_tc(const fdsc_params* P, const fdsc_layer* L, const uint64_t* ct_in, const uint64_t* A1,
+                               const uint64_t* A2, const uint64_t* P_tc, const uint64_t* M_hat, uint64_t* ct_out,
+                               void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    fdsc_layout lay;
+    if ((rc = fdsc_make_layer(P->info, L, &D, &lay))) return rc;
+    if (D.T > P->max_T)
+        return fdsc_set_error(FDSC_ERR_NOISE, "T = %u input ciphertexts exceed the params' noise budget (max_T = %u)",
+                              D.T, P->max_T);
+    if (!homconv_tc_supported(P->info.n, D))
+        return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "the tensor-core HomConv needs T <= 128 (T = %u)", D.T);
+    if ((rc = check_ptr(ct_in, "ct_in")) || (rc = check_ptr(P_tc, "P_tc")) || (rc = check_ptr(ct_out, "ct_out")))
+        return rc;
+    if ((A1 && (rc = check_ptr(A1, "A1"))) || (A2 && (rc = check_ptr(A2, "A2"))) ||
+        (M_hat && (rc = check_ptr(M_hat, "M_hat"))))
+        return rc;
+    const u64 ob = lay.ct_out_words * 8, ab = (u64)D.n_in * P->info.n * 8;
+    if (overlap(ct_in, lay.ct_in_words * 8, ct_out, ob) || (A1 && overlap(A1, ab, ct_out, ob)) ||
+        (A2 && overlap(A2, ab, ct_out, ob)) || overlap(P_tc, filter_tc_words(P->info.n, D) * 8, ct_out, ob))
+        return fdsc_set_error(FDSC_ERR_ARG, "ct_out overlaps an input");
+    return launched(launch_homconv_tc(P->dev, D, ct_in, A1, A2, P_tc, M_hat, ct_out, (cudaStream_t)stream),
+                    "homconv_tc");
+}
+
+extern "C" int fdsc_homconv_tc_status(uint32_t* code) {
+    if (!code) return fdsc_set_error(FDSC_ERR_ARG, "code is NULL");
+    *code = homconv_tc_error(true);
+    if (*code) return fdsc_set_error(FDSC_ERR_TIMEOUT, "a tensor-core HomConv CTA gave up waiting (role %u)", *code);
+    return FDSC_OK;
+}
+
 extern "C" int fdsc_encrypt_constants_seeded(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat,
                                              uint64_t seed, uint64_t* c1, void* stream) {
     int rc = check_params(P);

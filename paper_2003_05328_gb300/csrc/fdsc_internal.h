@@ -114,6 +114,13 @@ cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_
 cudaError_t launch_homconv_v(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
                              const u64* Phat, const u64* Mhat, u64* ct_out, int variant, cudaStream_t s);
 int homconv_default_variant(const DevLayer& L);
+// tensor-core HomConv (homconv_tc.cu)
+bool homconv_tc_supported(u32 n, const DevLayer& L);
+u64 filter_tc_words(u32 n, const DevLayer& L);
+cudaError_t launch_filter_tc(const DevParams& P, const DevLayer& L, const u64* Phat, u64* Ptc, cudaStream_t s);
+cudaError_t launch_homconv_tc(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                              const u64* Ptc, const u64* Mhat, u64* ct_out, cudaStream_t s);
+u32 homconv_tc_error(bool reset);
 cudaError_t launch_pool2x2(const DevParams& P, u32 H, u32 W, const u32* x, u32* y, u64 planes, cudaStream_t s);
 cudaError_t launch_constants(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, u64 seed,
                              const u64* seeds, u64* ct, cudaStream_t s, bool c1_only = false);

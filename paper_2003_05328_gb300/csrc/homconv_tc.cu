@@ -1,0 +1,590 @@
+// homconv_tc.cu -- HomConv + HomShare (Fig. 2 lines 3-4, Eq. 2) on the
+// tensor cores, exact.
+//
+// For every evaluation index J = (h, j) of the NTT_q domain the layer is a
+// modular matrix product over the input ciphertexts k,
+//   out[co][col] = sum_k P[co][k] X[k][col]  (mod q),   col = (bb, c),
+// of 60-bit words.  A word w < 2^60 is written in balanced base-256 digits,
+//   w = sum_{a<8} d_a 256^a,   d_a = byte_a(w + 0x8080808080808080) - 128,
+// so d_a lies in [-128, 127] (the top digit in [0, 16]) and is held exactly
+// by fp16.  Then
+//   sum_k P X = sum_{kappa<15} 256^kappa D_kappa,
+//   D_kappa[co][col] = sum_{a+b=kappa} sum_k P_a[co][k] X_b[k][col],
+// and every partial sum of D_kappa is an integer of magnitude at most
+// T * 7 * 2^14 < 2^24 for T <= 128, so the fp32 accumulation of the tensor
+// cores is exact.  The epilogue converts the 15 diagonals to integers,
+// combines them into the 128-bit value of the sum and reduces it mod q once.
+//
+// MMA mapping (tcgen05.mma kind::f16, M = 128 output channels in the TMEM
+// lanes, K = 16 input ciphertexts per instruction): the B operand stacks the
+// eight digit planes of X along N (rows (b, col), N = 8 NB), and the MMA of
+// filter digit plane a accumulates into the TMEM column window
+// [a NB, a NB + 8 NB): column block kappa then receives exactly the products
+// with a + b = kappa.  One MMA with a zero A operand clears the upper window
+// before the first accumulation.
+//
+// Roles in a persistent CTA of 16 warps (one CTA per SM):
+//   warps 0-7   epilogue: TMEM -> diagonals -> 128-bit sum -> mod q -> HomShare
+//   warp 8      TMEM allocation; lane 0 issues the MMAs
+//   warps 9-15  producers: a bulk copy stages each unit's filter digit words,
+//               cp.async the input words; both are converted to fp16 digit
+//               planes in the canonical no-swizzle K-major layout.
+// A unit is (item, 16 input ciphertexts); an item is (J, 128 output channels,
+// up to 8 image groups).  Two TMEM accumulators let the MMAs of one item run
+// while the epilogue drains the previous one.  Every wait is bounded: on a
+// timeout the CTA records an error, stops, lets its copies and MMAs finish,
+// frees its TMEM and returns.
+#include <cuda_fp16.h>
+
+#include "modarith.cuh"
+
+namespace {
+
+constexpr u32 kThreadsTC = 512;
+constexpr u32 kEpiWarps = 8;
+constexpr u32 kMmaWarp = 8;
+constexpr u32 kProdWarp0 = 9;
+constexpr u32 kProdThreads = (16 - kProdWarp0) * 32;  // 224
+constexpr u32 kFS = 2;                                // fp16 operand slots
+constexpr u32 kMaxRS = 16;                            // staging slots at most
+constexpr u64 kDigitBias = 0x8080808080808080ull;
+constexpr u64 kWaitNs = 2000000000ull;  // a wait gives up after 2 s
+
+struct TcGeom {
+    u32 NB;        // B columns (bb, c) per item: 2 x image groups per pass
+    u32 KB;        // 16-ciphertext blocks: ceil(T / 16)
+    u32 n_ct;      // 128-channel tiles
+    u32 n_gbg;     // image-group passes
+    u32 gbt;       // image groups per pass (NB / 2)
+    u32 n_items;   // nJ * n_ct * n_gbg
+    u32 RS;        // staging slots
+    u32 off_f16, fsz, off_ra, raz, off_rx, rxz;
+};
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ u64 sdesc(u32 addr, u32 lbo, u32 sbo) {
+    // no-swizzle K-major: LBO = byte stride between the two 8-element K halves,
+    // SBO = byte stride between 8-row groups; bit 46 = descriptor version 1
+    return (u64)((addr & 0x3FFFF) >> 4) | ((u64)(lbo >> 4) << 16) | ((u64)(sbo >> 4) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ u32 idesc_f16(u32 M, u32 N) {
+    // D f32 (bits 4-5 = 1), A and B f16 (0), both K-major, N >> 3 at 17, M >> 4 at 24
+    return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(u32 d, u64 a, u64 b, u32 idesc, u32 acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(u32 bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(u32 bar, u32 count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(u32 bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(u32 bar, u32 bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(u32 bar, u32 parity) {
+    u32 ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ u64 gtime_ns() {
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: false after kWaitNs or once *abort is set.
+__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity, const volatile u32* abort) {
+    if (mbar_try(bar, parity)) return true;
+    const u64 t0 = gtime_ns();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort || gtime_ns() - t0 > kWaitNs) return false;
+    }
+}
+// Bounded wait that ignores the abort flag (used to drain copies in flight).
+__device__ __forceinline__ void mbar_drain(u32 bar, u32 parity) {
+    const u64 t0 = gtime_ns();
+    while (!mbar_try(bar, parity) && gtime_ns() - t0 <= kWaitNs) {
+    }
+}
+__device__ __forceinline__ void bulk_g2s(u32 dst, const void* src, u32 bytes, u32 bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(u32 dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+// arrives on bar once this thread's earlier cp.async copies have landed
+__device__ __forceinline__ void cp_async_arrive(u32 bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+// named barrier over the producer warps returning the OR of `pred`
+__device__ __forceinline__ bool producers_sync_or(bool pred) {
+    u32 r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((u32)pred), "r"(kProdThreads)
+        : "memory");
+    return r != 0;
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(u32 addr, u32 (&r)[N]);
+template <>
+__device__ __forceinline__ void tmem_ld<1>(u32 addr, u32 (&r)[1]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[0]) : "r"(addr));
+}
+template <>
+__device__ __forceinline__ void tmem_ld<2>(u32 addr, u32 (&r)[2]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(addr));
+}
+template <>
+__device__ __forceinline__ void tmem_ld<4>(u32 addr, u32 (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+template <>
+__device__ __forceinline__ void tmem_ld<8>(u32 addr, u32 (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------- digit planes
+// Eight biased words (w + 0x80..80) -> for each digit a, the eight fp16 values
+// d_a(w_0..w_7) in word order (one 16-byte row of a core matrix).  A byte u
+// becomes the fp16 with bit pattern 0x64uu = 1024 + u; subtracting 1152
+// leaves u - 128 = d_a exactly.
+__device__ __forceinline__ u32 hsub1152(u32 h2) {
+    __half2 v = *reinterpret_cast<__half2*>(&h2);
+    v = __hsub2(v, __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480)));  // 1152
+    return *reinterpret_cast<u32*>(&v);
+}
+__device__ __forceinline__ void digit_rows(const u64 (&w)[8], uint4 (&row)[8]) {
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+        u32 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = half ? (u32)(w[k] >> 32) : (u32)w[k];
+        u32 o[4][4];  // [digit within half][word pair]
+#pragma unroll
+        for (int kp = 0; kp < 4; kp++) {
+            const u32 t01 = __byte_perm(v[2 * kp], v[2 * kp + 1], 0x5140);  // x0 y0 x1 y1
+            const u32 t23 = __byte_perm(v[2 * kp], v[2 * kp + 1], 0x7362);  // x2 y2 x3 y3
+            o[0][kp] = hsub1152(__byte_perm(t01, 0x64646464u, 0x4140));
+            o[1][kp] = hsub1152(__byte_perm(t01, 0x64646464u, 0x4342));
+            o[2][kp] = hsub1152(__byte_perm(t23, 0x64646464u, 0x4140));
+            o[3][kp] = hsub1152(__byte_perm(t23, 0x64646464u, 0x4342));
+        }
+#pragma unroll
+        for (int a = 0; a < 4; a++) row[4 * half + a] = make_uint4(o[a][0], o[a][1], o[a][2], o[a][3]);
+    }
+}
+
+// ---------------------------------------------------------------- the kernel
+template <int NBH>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    homconv_tc_kernel(DevParams P, DevLayer L, TcGeom G, const u64* __restrict__ ct_in, const u64* __restrict__ A1,
+                      const u64* __restrict__ A2, const u64* __restrict__ Ptc, const u64* __restrict__ Mhat,
+                      u64* __restrict__ ct_out, u32* __restrict__ err) {
+    constexpr u32 NB = 2 * NBH;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    u64* bars = reinterpret_cast<u64*>(sm);
+    // barrier slots: raw_full[16], f16_full[2], f16_empty[2], tfull[2], tempty[2], drain
+    const u32 b_raw = smem_u32(bars), b_ffull = b_raw + 8 * kMaxRS, b_fempty = b_ffull + 16, b_tfull = b_fempty + 16,
+              b_tempty = b_tfull + 16, b_drain = b_tempty + 16;
+    volatile u32* tmem_slot = reinterpret_cast<volatile u32*>(sm + 240);
+    volatile u32* abort = reinterpret_cast<volatile u32*>(sm + 248);
+    unsigned char* zero_blk = sm + 1024;
+    const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const u32 nJ = L.beta * P.n;
+    const u32 my_items = blockIdx.x < G.n_items ? (G.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const u32 total_units = my_items * G.KB;
+    const u32 tm_cols = 64 * NBH;  // two accumulators of 16 NB columns
+
+    // ---- setup: zero the operand slots (unused A rows and the zero block stay 0), barriers, TMEM
+    for (u32 e = tid; e < (G.off_f16 + kFS * G.fsz - 1024) / 16; e += kThreadsTC)
+        reinterpret_cast<uint4*>(sm + 1024)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (u32 s = 0; s < kMaxRS; s++) mbar_init(b_raw + 8 * s, 1 + kProdThreads);
+        for (u32 s = 0; s < kFS; s++) {
+            mbar_init(b_ffull + 8 * s, kProdThreads / 32);
+            mbar_init(b_fempty + 8 * s, 1);
+        }
+        for (u32 s = 0; s < 2; s++) {
+            mbar_init(b_tfull + 8 * s, 1);
+            mbar_init(b_tempty + 8 * s, kEpiWarps);
+        }
+        mbar_init(b_drain, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(
+                         (const void*)tmem_slot)),
+                     "r"(tm_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const u32 tmem = *tmem_slot;
+
+    if (warp >= kProdWarp0) {
+        // ================================================================ producers
+        const u32 pt = tid - kProdWarp0 * 32;
+        auto unit_item = [&](u32 u, u32& J, u32& ct, u32& gbg, u32& kb) {
+            const u32 item = blockIdx.x + (u / G.KB) * gridDim.x;
+            kb = u % G.KB;
+            J = item % nJ;
+            const u32 rest = item / nJ;
+            ct = rest % G.n_ct;
+            gbg = rest / G.n_ct;
+        };
+        // stage unit u: the filter digit words by one bulk copy, the input words by cp.async
+        auto issue = [&](u32 u) {
+            u32 J, ct, gbg, kb;
+            unit_item(u, J, ct, gbg, kb);
+            const u32 s = u % G.RS, bar = b_raw + 8 * s;
+            const u32 co0 = ct * 128, R = min(128u, L.Co - co0);
+            if (pt == 0) {
+                const u32 bytes = R * 128;
+                fence_async_smem();  // the slot's earlier generic reads come before the copy's writes
+                mbar_expect_tx(bar, bytes);
+                bulk_g2s(smem_u32(sm + G.off_ra + s * G.raz), Ptc + ((u64)(J * G.KB + kb) * L.Co + co0) * 16, bytes,
+                         bar);
+            }
+            const u32 h = J >> P.logn, j = J & (P.n - 1);
+            u64* xr = reinterpret_cast<u64*>(sm + G.off_rx + s * G.rxz);  // [3][16][NB]
+            const u32 bb0 = gbg * G.gbt;
+            for (u32 e = pt; e < 3 * 16 * NB; e += kProdThreads) {
+                const u32 plane = e / (16 * NB), kk = (e / NB) % 16, col = e % NB;
+                const u32 bbl = col >> 1, c = col & 1, k = kb * 16 + kk, bb = bb0 + bbl;
+                const u64* src = nullptr;
+                if (k < L.T && bb < L.GB) {
+                    const u64 uin = ((u64)bb * L.T + k) * L.beta + h;
+                    if (plane == 0)
+                        src = ct_in + (uin * 2 + c) * P.n + j;
+                    else if (c == 1)
+                        src = (plane == 1 ? A1 : A2) ? (plane == 1 ? A1 : A2) + uin * P.n + j : nullptr;
+                }
+                if (src)
+                    cp_async8(smem_u32(xr + e), src);
+                else
+                    xr[e] = 0;
+            }
+            cp_async_arrive(bar);
+        };
+        bool bad = false;
+        u32 issued = 0;
+        for (; issued < min(G.RS - 1, total_units); issued++) issue(issued);
+        u32 u = 0;
+        for (; u < total_units; u++) {
+            // every producer is done with unit u - 1, so its staging slot may be refilled
+            if (producers_sync_or(bad || *abort)) break;
+            if (issued < total_units && issued < u + G.RS) issue(issued++);
+            const u32 s = u % G.RS, fs = u % kFS;
+            bool ok = mbar_wait(b_raw + 8 * s, (u / G.RS) & 1, abort);
+            ok = ok && mbar_wait(b_fempty + 8 * fs, ((u / kFS) & 1) ^ 1, abort);
+            if (!__all_sync(0xffffffffu, ok)) {
+                bad = true;
+                continue;
+            }
+            u32 J, ct, gbg, kb;
+            unit_item(u, J, ct, gbg, kb);
+            const u32 R = min(128u, L.Co - ct * 128);
+            unsigned char* fA = sm + G.off_f16 + fs * G.fsz;
+            unsigned char* fX = fA + 32768;
+            const u64* ra = reinterpret_cast<const u64*>(sm + G.off_ra + s * G.raz);
+            const u64* xr = reinterpret_cast<const u64*>(sm + G.off_rx + s * G.rxz);
+            for (u32 t = pt; t < 2 * R + 2 * NB; t += kProdThreads) {
+                u64 w[8];
+                uint4 row[8];
+                if (t < 2 * R) {
+                    // filter: row co, input ciphertexts k8*8 .. k8*8+7 (already biased)
+                    const u32 co = t >> 1, k8 = t & 1;
+                    const uint4* src = reinterpret_cast<const uint4*>(ra + co * 16 + k8 * 8);
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const uint4 v = src[i];
+                        w[2 * i] = ((u64)v.y << 32) | v.x;
+                        w[2 * i + 1] = ((u64)v.w << 32) | v.z;
+                    }
+                    digit_rows(w, row);
+                    const u32 off = (co >> 3) * 256 + k8 * 128 + (co & 7) * 16;
+#pragma unroll
+                    for (int a = 0; a < 8; a++) *reinterpret_cast<uint4*>(fA + a * 4096 + off) = row[a];
+                } else {
+                    // input: column col, k8*8 .. k8*8+7; c1 gets the addends mod q, then the bias
+                    const u32 col = (t - 2 * R) >> 1, k8 = (t - 2 * R) & 1;
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        const u32 kk = k8 * 8 + i;
+                        u64 x = xr[kk * NB + col];
+                        if (col & 1) {
+                            x = addmod_q(x, xr[16 * NB + kk * NB + col], P.q);
+                            x = addmod_q(x, xr[32 * NB + kk * NB + col], P.q);
+                        }
+                        w[i] = x + kDigitBias;
+                    }
+                    digit_rows(w, row);
+#pragma unroll
+                    for (int b = 0; b < 8; b++)
+                        *reinterpret_cast<uint4*>(fX + k8 * (8 * NB * 16) + (b * NB + col) * 16) = row[b];
+                }
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_ffull + 8 * fs);
+        }
+        if (u < total_units) {
+            *abort = 1;
+            atomicExch(err, 1u);
+            // let the copies already issued land before the CTA may exit: at most
+            // the last RS units issued can still be in flight, one per slot
+            for (u32 v = issued > G.RS ? issued - G.RS : 0; v < issued; v++)
+                mbar_drain(b_raw + 8 * (v % G.RS), (v / G.RS) & 1);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp == kMmaWarp) {
+        // ================================================================ MMA issue
+        if (lane == 0) {
+            const u32 idesc = idesc_f16(128, 8 * NB);
+            const u64 zdesc = sdesc(smem_u32(zero_blk), 128, 256);
+            u32 u = 0;
+            bool ok = true;
+            for (u32 li = 0; li < my_items && ok; li++) {
+                const u32 b = li & 1;
+                if (!mbar_wait(b_tempty + 8 * b, ((li >> 1) & 1) ^ 1, abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const u32 dcol = tmem + b * 16 * NB;
+                for (u32 kb = 0; kb < G.KB; kb++, u++) {
+                    const u32 fs = u % kFS;
+                    if (!mbar_wait(b_ffull + 8 * fs, (u / kFS) & 1, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const u32 fA = smem_u32(sm + G.off_f16 + fs * G.fsz);
+                    const u64 xdesc = sdesc(fA + 32768, 8 * NB * 16, 128);
+#pragma unroll
+                    for (u32 a = 0; a < 8; a++) {
+                        mma_f16(dcol + a * NB, sdesc(fA + a * 4096, 128, 256), xdesc, idesc, (kb | a) ? 1u : 0u);
+                        if (kb == 0 && a == 0) mma_f16(dcol + 8 * NB, zdesc, xdesc, idesc, 0u);
+                    }
+                    mma_commit(b_fempty + 8 * fs);
+                }
+                if (ok) mma_commit(b_tfull + 8 * b);
+            }
+            if (!ok) {
+                *abort = 1;
+                atomicExch(err, 2u);
+            }
+            // every MMA issued has completed before the TMEM may be freed
+            mma_commit(b_drain);
+            mbar_drain(b_drain, 0);
+        }
+        __syncwarp();
+    } else {
+        // ================================================================ epilogue
+        const u32 quarter = warp & 3, hc = warp >> 2;
+        const u32 r = quarter * 32 + lane;
+        const u32 lane_addr = (quarter * 32) << 16;
+        for (u32 li = 0; li < my_items; li++) {
+            const u32 b = li & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(b_tfull + 8 * b, (li >> 1) & 1, abort))) {
+                *abort = 1;
+                atomicExch(err, 3u);
+                break;
+            }
+            tc_fence_after();
+            const u32 item = blockIdx.x + li * gridDim.x;
+            const u32 J = item % nJ, rest = item / nJ, ct = rest % G.n_ct, gbg = rest / G.n_ct;
+            const u32 h = J >> P.logn, j = J & (P.n - 1);
+            const u32 co = ct * 128 + r;
+            const u32 col0 = hc * NBH;
+            const u32 base = tmem + lane_addr + b * 16 * NB + col0;
+            unsigned __int128 V[NBH];  // the sum mod 2^128: exact, since it lies in [0, 2^127)
+#pragma unroll
+            for (int i = 0; i < NBH; i++) V[i] = 0;
+#pragma unroll
+            for (u32 m = 0; m < 4; m++) {
+                u32 d[4][NBH];
+#pragma unroll
+                for (u32 rr = 0; rr < 4; rr++)
+                    if (4 * m + rr < 15) tmem_ld<NBH>(base + (4 * m + rr) * NB, d[rr]);
+                tmem_wait_ld();
+                // the loaded registers are used only after the wait
+#pragma unroll
+                for (u32 rr = 0; rr < 4; rr++)
+#pragma unroll
+                    for (int i = 0; i < NBH; i++)
+                        if (4 * m + rr < 15) asm volatile("" : "+r"(d[rr][i]));
+#pragma unroll
+                for (int i = 0; i < NBH; i++) {
+                    long long cm = 0;
+#pragma unroll
+                    for (u32 rr = 0; rr < 4; rr++)
+                        if (4 * m + rr < 15) cm += (long long)__float2int_rn(__uint_as_float(d[rr][i])) * (1ll << (8 * rr));
+                    V[i] += (unsigned __int128)(__int128)cm << (32 * m);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_tempty + 8 * b);
+            if (co < L.Co) {
+#pragma unroll
+                for (int i = 0; i < NBH; i++) {
+                    const u32 col = col0 + i, bb = gbg * G.gbt + (col >> 1), c = col & 1;
+                    if (bb >= L.GB) continue;
+                    const unsigned __int128 v = V[i];
+                    u64 res = reduce128((u64)(v >> 64), (u64)v, P);
+                    const u64 vo = ((u64)bb * L.Co + co) * L.beta + h;
+                    if (c == 1 && Mhat) res = submod_q(res, __ldg(Mhat + vo * P.n + j), P.q);
+                    ct_out[(vo * 2 + c) * P.n + j] = res;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tm_cols));
+    }
+}
+
+// Phat [Co][T][beta][n] -> Ptc [J][KB][Co][16]: the words of 16 consecutive
+// input ciphertexts of one output channel contiguous per J, biased by
+// 0x80..80; ciphertexts past T hold the bias alone (digits 0).
+__global__ void filter_tc_kernel(const DevParams P, const DevLayer L, u32 KB, const u64* __restrict__ Phat,
+                                 u64* __restrict__ Ptc) {
+    __shared__ u64 tile[16][65];
+    const u32 nJ = L.beta * P.n;
+    const u32 J0 = blockIdx.x * 64, kb = blockIdx.y, co = blockIdx.z;
+    for (u32 e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
+        const u32 kk = e / 64, jj = e % 64, k = kb * 16 + kk, J = J0 + jj;
+        u64 v = kDigitBias;
+        if (k < L.T && J < nJ) v = Phat[((u64)co * L.T + k) * nJ + J] + kDigitBias;
+        tile[kk][jj] = v;
+    }
+    __syncthreads();
+    for (u32 e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
+        const u32 jj = e / 16, kk = e % 16, J = J0 + jj;
+        if (J < nJ) Ptc[(((u64)J * KB + kb) * L.Co + co) * 16 + kk] = tile[kk][jj];
+    }
+}
+
+__device__ u32 g_tc_err;  // nonzero after a CTA gave up waiting (1 producer, 2 MMA, 3 epilogue)
+
+}  // namespace
+
+// Geometry of the tensor-core path for a layer of ring degree n; false if
+// it does not apply (T > 128 would let a diagonal reach 2^24).
+static bool tc_geom(u32 n, const DevLayer& L, TcGeom& G, size_t& smem) {
+    if (L.T == 0 || L.T > 128 || L.GB == 0 || L.Co == 0) return false;
+    const u32 gbt = L.GB >= 8 ? 8 : (L.GB >= 4 ? 4 : (L.GB >= 2 ? 2 : 1));
+    G.gbt = gbt;
+    G.NB = 2 * gbt;
+    G.KB = (L.T + 15) / 16;
+    G.n_ct = (L.Co + 127) / 128;
+    G.n_gbg = (L.GB + gbt - 1) / gbt;
+    const u64 items = (u64)L.beta * n * G.n_ct * G.n_gbg;
+    if (items > 0x7FFFFFFFull) return false;
+    G.n_items = (u32)items;
+    const u32 rmax = L.Co < 128 ? L.Co : 128;
+    G.raz = rmax * 128;
+    G.RS = 65536 / G.raz;
+    G.RS = G.RS < 2 ? 2 : (G.RS > kMaxRS ? kMaxRS : G.RS);
+    G.fsz = 32768 + 256 * G.NB;
+    G.off_f16 = 1024 + 4096;
+    G.off_ra = G.off_f16 + kFS * G.fsz;
+    G.rxz = 3 * 16 * G.NB * 8;
+    G.off_rx = G.off_ra + G.RS * G.raz;
+    smem = G.off_rx + G.RS * G.rxz;
+    return true;
+}
+
+bool homconv_tc_supported(u32 n, const DevLayer& L) {
+    TcGeom G;
+    size_t smem;
+    return tc_geom(n, L, G, smem) && smem <= 227 * 1024;
+}
+
+u64 filter_tc_words(u32 n, const DevLayer& L) { return (u64)L.beta * n * ((L.T + 15) / 16) * L.Co * 16; }
+
+cudaError_t launch_filter_tc(const DevParams& P, const DevLayer& L, const u64* Phat, u64* Ptc, cudaStream_t s) {
+    const u32 nJ = L.beta * P.n, KB = (L.T + 15) / 16;
+    dim3 grid((nJ + 63) / 64, KB, L.Co);
+    filter_tc_kernel<<<grid, 256, 0, s>>>(P, L, KB, Phat, Ptc);
+    return cudaGetLastError();
+}
+
+template <int NBH>
+static cudaError_t launch_tc(const DevParams& P, const DevLayer& L, const TcGeom& G, size_t smem, const u64* ct_in,
+                             const u64* A1, const u64* A2, const u64* Ptc, const u64* Mhat, u64* ct_out,
+                             cudaStream_t s) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    cudaError_t e = cudaFuncSetAttribute(homconv_tc_kernel<NBH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    u32* errp = nullptr;
+    e = cudaGetSymbolAddress((void**)&errp, g_tc_err);
+    if (e != cudaSuccess) return e;
+    const u32 grid = G.n_items < (u32)sms ? G.n_items : (u32)sms;
+    homconv_tc_kernel<NBH><<<grid, kThreadsTC, smem, s>>>(P, L, G, ct_in, A1, A2, Ptc, Mhat, ct_out, errp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_homconv_tc(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                              const u64* Ptc, const u64* Mhat, u64* ct_out, cudaStream_t s) {
+    TcGeom G;
+    size_t smem;
+    if (!tc_geom(P.n, L, G, smem) || smem > 227 * 1024) return cudaErrorInvalidValue;
+    switch (G.gbt) {
+        case 1: return launch_tc<1>(P, L, G, smem, ct_in, A1, A2, Ptc, Mhat, ct_out, s);
+        case 2: return launch_tc<2>(P, L, G, smem, ct_in, A1, A2, Ptc, Mhat, ct_out, s);
+        case 4: return launch_tc<4>(P, L, G, smem, ct_in, A1, A2, Ptc, Mhat, ct_out, s);
+        default: return launch_tc<8>(P, L, G, smem, ct_in, A1, A2, Ptc, Mhat, ct_out, s);
+    }
+}
+
+// The error word of the tensor-core kernel (0: no CTA gave up waiting).
+u32 homconv_tc_error(bool reset) {
+    u32 v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_err, sizeof(u32)) != cudaSuccess) return 0;
+    if (reset && v) {
+        const u32 z = 0;
+        cudaMemcpyToSymbol(g_tc_err, &z, sizeof(u32));
+    }
+    return v;
+}

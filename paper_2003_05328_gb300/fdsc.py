@@ -79,6 +79,10 @@ _SIGS = {
     "fdsc_encode_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
     "fdsc_homrec_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
     "fdsc_homconv_sum": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fdsc_filter_tc_words": (C.c_int, [C.c_uint32, C.c_uint32, _PL, C.POINTER(C.c_uint64)]),
+    "fdsc_filter_tc": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
+    "fdsc_homconv_tc": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fdsc_homconv_tc_status": (C.c_int, [C.POINTER(C.c_uint32)]),
     "fdsc_encrypt_constants_seeded": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp]),
     "fdsc_homconv_seeded": (C.c_int, [_vp, _PL, C.c_uint64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fdsc_decrypt_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
@@ -392,6 +396,46 @@ def homconv_sum(P: Params, L: LayerSpec, ct_in, A1, A2, P_hat, M_hat=None, out=N
           _ptr(P_hat, torch.int64, lay.filter_words, "P_hat"), m, _ptr(out, torch.int64, lay.ct_out_words, "ct_out"),
           _stream(stream))
     return out
+
+
+def filter_tc_words(n: int, p: int, L: LayerSpec) -> int:
+    """Words of the digit-ready filter of the tensor-core HomConv (host only)."""
+    out = C.c_uint64()
+    _call("fdsc_filter_tc_words", n, p, C.byref(L.c()), C.byref(out))
+    return out.value
+
+
+def filter_tc(P: Params, L: LayerSpec, P_hat, out=None, stream=None) -> torch.Tensor:
+    """P_hat [Co][T][beta][n] -> the tensor-core layout [beta n][ceil(T/16)][Co][16] (biased words)."""
+    lay = layout(P, L)
+    words = filter_tc_words(P.n, P.p, L)
+    if out is None:
+        out = torch.empty(words, dtype=torch.int64, device="cuda")
+    _call("fdsc_filter_tc", P.handle, C.byref(L.c()), _ptr(P_hat, torch.int64, lay.filter_words, "P_hat"),
+          _ptr(out, torch.int64, words, "P_tc"), _stream(stream))
+    return out
+
+
+def homconv_tc(P: Params, L: LayerSpec, ct_in, A1, A2, P_tc, M_hat=None, out=None, stream=None) -> torch.Tensor:
+    """homconv_sum on the tensor cores (exact digit products, fp32 accumulation below 2^24)."""
+    lay = layout(P, L)
+    if out is None:
+        out = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
+    na = lay.n_in * P.n
+    a1 = None if A1 is None else _ptr(A1, torch.int64, na, "A1")
+    a2 = None if A2 is None else _ptr(A2, torch.int64, na, "A2")
+    m = None if M_hat is None else _ptr(M_hat, torch.int64, lay.mask_words, "M_hat")
+    _call("fdsc_homconv_tc", P.handle, C.byref(L.c()), _ptr(ct_in, torch.int64, lay.ct_in_words, "ct_in"), a1, a2,
+          _ptr(P_tc, torch.int64, filter_tc_words(P.n, P.p, L), "P_tc"), m,
+          _ptr(out, torch.int64, lay.ct_out_words, "ct_out"), _stream(stream))
+    return out
+
+
+def homconv_tc_status() -> int:
+    """0 if no tensor-core HomConv CTA gave up a bounded wait since the last call (raises otherwise)."""
+    code = C.c_uint32()
+    _call("fdsc_homconv_tc_status", C.byref(code))
+    return code.value
 
 
 def encrypt_constants_seeded(P: Params, L: LayerSpec, t_hat, seed: int, out=None, stream=None) -> torch.Tensor:

@@ -333,3 +333,118 @@ def test_seeded_ciphertexts(F, shape):
     ref = O.homconv(OP, OL, full.astype(np.uint64), Ph, Mh)
     assert np.array_equal(u64(out).reshape(ref.shape), ref)
     P.close()
+
+
+# ---------------------------------------------------------------- tensor-core HomConv
+def _worst_digit_word(q):
+    """The largest word below q whose balanced base-256 digits 0..6 are all
+    -128: (w + 0x80..80) has bytes 0..6 equal to zero."""
+    low = (1 << 56) - 0x80808080808080  # w = low mod 2^56
+    t = (q - 1 - low) >> 56
+    return low + (t << 56)
+
+
+@pytest.mark.parametrize("shape", [
+    (2048, 1, 64, 64, 32, 32, 2, 1),    # the 32x32x64 layer at batch 1: T = 32, Co = 64 (half an M tile)
+    (1024, 3, 5, 7, 16, 16, 2, 2),      # T = 3: one ragged block of 16 input ciphertexts; 2 image groups
+    (1024, 2, 12, 12, 64, 64, 1, 1),    # beta = 4 ciphertexts per spectrum, Co not a multiple of 8
+    (2048, 16, 50, 8, 32, 32, 2, 1),    # 16 image groups: two passes of 8; T = 25
+    (256, 5, 34, 130, 8, 8, 1, 1),      # Co = 130: a full and a 2-channel tile; T = 34: 3 blocks; 5 groups: 4 + 1
+    (1024, 1, 128, 128, 32, 32, 1, 1),  # T = 128, the largest the fp32 bound admits
+])
+def test_homconv_tc_matches_oracle(F, shape):
+    """The tensor-core HomConv (digit planes in fp16, exact fp32 sums of the
+    15 weight classes) gives the oracle's words, with and without the fused
+    c1 addends and the HomShare mask."""
+    n, B, Ci, Co, H, W, g_c, g_b = shape
+    OP = O.params(n, 65537)
+    OL = O.layer(OP, B, Ci, Co, H, W, g_c, g_b)
+    P = F.Params(n, 65537, max_T=max(OL.T, 1))
+    L = F.LayerSpec(B, Ci, Co, H, W, g_c, g_b)
+    g = np.random.default_rng(n + Ci + Co)
+    ct = np.array(g.integers(0, OP.q, (OL.n_in, 2, n), dtype=np.uint64))
+    A1 = np.array(g.integers(0, OP.q, (OL.n_in, n), dtype=np.uint64))
+    A2 = np.array(g.integers(0, OP.q, (OL.n_in, n), dtype=np.uint64))
+    Ph = np.array(g.integers(0, OP.q, (Co * OL.T * OL.beta, n), dtype=np.uint64))
+    Mh = np.array(g.integers(0, OP.q, (OL.n_out, n), dtype=np.uint64))
+    ct[:, :, :4] = OP.q - 1
+    Ph[:, :4] = OP.q - 1
+    ct[:, :, 4:8] = 0
+    summed = ct.astype(object)
+    summed[:, 1] = (summed[:, 1] + A1.astype(object) + A2.astype(object)) % OP.q
+    ref = O.homconv(OP, OL, summed.astype(np.uint64), Ph, Mh)
+    d = lambda a: dev(a.view(np.int64), np.int64)
+    Ptc = F.filter_tc(P, L, d(Ph))
+    assert Ptc.numel() == F.filter_tc_words(n, 65537, L)
+    out = F.homconv_tc(P, L, d(ct), d(A1), d(A2), Ptc, d(Mh))
+    torch.cuda.synchronize()
+    assert F.homconv_tc_status() == 0
+    assert np.array_equal(u64(out).reshape(ref.shape), ref)
+    out = F.homconv_tc(P, L, d(ct), None, None, Ptc, None)
+    assert np.array_equal(u64(out).reshape(ref.shape), O.homconv(OP, OL, ct, Ph, None))
+    # identical to the CUDA-core kernel on the same inputs
+    assert torch.equal(F.homconv_tc(P, L, d(ct), d(A1), d(A2), Ptc, d(Mh)),
+                       F.homconv_sum(P, L, d(ct), d(A1), d(A2), d(Ph), d(Mh)))
+    torch.cuda.synchronize()
+    assert F.homconv_tc_status() == 0
+    P.close()
+
+
+def test_homconv_tc_worst_case_digits(F):
+    """T = 128 words whose low seven digits are all -128 on both sides: the
+    weight class 256^6 then sums 128 x 7 products of +2^14 (14.7 M, the
+    largest partial sum the bound allows below 2^24), and q - 1 / 0 words
+    exercise the top digit and the zero digits."""
+    n, B, Ci, Co, H, W = 1024, 2, 128, 128, 32, 32
+    OP = O.params(n, 65537)
+    OL = O.layer(OP, B, Ci, Co, H, W, 1, 1)
+    P = F.Params(n, 65537, max_T=128)
+    L = F.LayerSpec(B, Ci, Co, H, W, 1, 1)
+    wbad = _worst_digit_word(OP.q)
+    assert wbad < OP.q and all(((wbad + 0x8080808080808080) >> (8 * a)) & 255 == 0 for a in range(7))
+    ct = np.full((OL.n_in, 2, n), wbad, np.uint64)
+    Ph = np.full((Co * OL.T, n), wbad, np.uint64)
+    ct[:, :, 1::3] = OP.q - 1
+    Ph[:, 2::5] = 0
+    ref = O.homconv(OP, OL, ct, Ph, None)
+    d = lambda a: dev(a.view(np.int64), np.int64)
+    out = F.homconv_tc(P, L, d(ct), None, None, F.filter_tc(P, L, d(Ph)), None)
+    torch.cuda.synchronize()
+    assert F.homconv_tc_status() == 0
+    assert np.array_equal(u64(out).reshape(ref.shape), ref)
+    P.close()
+
+
+def test_homconv_tc_full_size_binarized_layer(F):
+    """The binarized 64x64x128 layer at batch 8 (n = 4096, p = 12289, two
+    ciphertexts per spectrum): the tensor-core words equal the CUDA-core
+    kernel's at full size, and sampled output words equal the oracle's
+    per-word sum."""
+    ls = FI.CONFIGS["cfg4"].layers[0]
+    OP = O.params(ls.n, ls.p)
+    OL = O.layer(OP, ls.B, ls.Ci, ls.Co, ls.H, ls.W, 1, 1)
+    P = F.Params(ls.n, ls.p, max_T=OL.T)
+    L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, 1, 1)
+    gen = torch.Generator(device="cuda").manual_seed(44)
+    q = OP.q
+    ct = torch.randint(0, q, (OL.n_in * 2 * ls.n,), dtype=torch.int64, device="cuda", generator=gen)
+    Ph = torch.randint(0, q, (ls.Co * OL.T * OL.beta * ls.n,), dtype=torch.int64, device="cuda", generator=gen)
+    Mh = torch.randint(0, q, (OL.n_out * ls.n,), dtype=torch.int64, device="cuda", generator=gen)
+    a = F.homconv_tc(P, L, ct, None, None, F.filter_tc(P, L, Ph), Mh)
+    b = F.homconv_sum(P, L, ct, None, None, Ph, Mh)
+    torch.cuda.synchronize()
+    assert F.homconv_tc_status() == 0
+    assert torch.equal(a, b)
+    ctn, Phn, Mhn, outn = (u64(t) for t in (ct, Ph, Mh, a))
+    ctn = ctn.reshape(OL.GB, OL.T, OL.beta, 2, ls.n)
+    Phn = Phn.reshape(ls.Co, OL.T, OL.beta, ls.n)
+    outn = outn.reshape(OL.GB, ls.Co, OL.beta, 2, ls.n)
+    Mhn = Mhn.reshape(OL.GB, ls.Co, OL.beta, ls.n)
+    rng = np.random.default_rng(4)
+    for _ in range(64):
+        bb, co, h, c, j = (int(rng.integers(m)) for m in (OL.GB, ls.Co, OL.beta, 2, ls.n))
+        s = sum(int(ctn[bb, k, h, c, j]) * int(Phn[co, k, h, j]) for k in range(OL.T)) % q
+        if c == 1:
+            s = (s - int(Mhn[bb, co, h, j])) % q
+        assert int(outn[bb, co, h, c, j]) == s, (bb, co, h, c, j)
+    P.close()

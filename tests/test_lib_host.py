@@ -99,3 +99,22 @@ def test_flood_bits_max_matches_oracle_bound(F, n, p, T):
     P = O.params(n, p)
     f = F.flood_bits_max(n, p, T)
     assert O.noise_ok(P, T, f) and not O.noise_ok(P, T, f + 1)
+
+
+@pytest.mark.parametrize("n,p,shape", [
+    (2048, 65537, (1, 64, 64, 32, 32, 2, 1)),
+    (4096, 12289, (8, 128, 128, 64, 64, 1, 1)),
+    (256, 65537, (5, 34, 130, 8, 8, 1, 1)),
+])
+def test_filter_tc_words(F, n, p, shape):
+    """Size of the tensor-core filter layout: [beta n][ceil(T/16)][Co][16]."""
+    B, Ci, Co, H, W, g_c, g_b = shape
+    L = F.LayerSpec(B, Ci, Co, H, W, g_c, g_b)
+    ref = O.layer(O.params(n, p), B, Ci, Co, H, W, g_c, g_b)
+    assert F.filter_tc_words(n, p, L) == ref.beta * n * (-(-ref.T // 16)) * Co * 16
+
+
+def test_filter_tc_rejects_large_T(F):
+    with pytest.raises(F.FdscError) as e:  # T = 129 > 128: a diagonal could reach 2^24
+        F.filter_tc_words(256, 65537, F.LayerSpec(1, 129, 4, 8, 8, 1, 1))
+    assert e.value.code == -5
