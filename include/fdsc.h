@@ -331,7 +331,8 @@ typedef struct {
 
 typedef struct {
     uint32_t g_c, g_b;          /* packing used                                */
-    uint32_t homconv_variant;   /* as in fdsc_set_homconv_variant              */
+    uint32_t homconv_variant;   /* as in fdsc_set_homconv_variant, or 7: the
+                                   tensor-core kernel (fdsc_homconv_tc)        */
     uint32_t fused;             /* 1: fused online kernels; 0: step by step    */
     uint32_t candidates;        /* candidates the tuner timed (0: not tuned)   */
     uint32_t pad0;
@@ -339,11 +340,14 @@ typedef struct {
 } fdsc_plan_layer_info;
 
 enum {
-    FDSC_PLAN_TUNE = 1,         /* time packings x HomConv variants, keep the fastest */
-    FDSC_PLAN_CHAIN = 2         /* layer i starts once layer i-1 (and its pooling) has
+    FDSC_PLAN_TUNE = 1,         /* time packings x HomConv variants (the tensor-core
+                                   kernel among them where T <= 128), keep the fastest */
+    FDSC_PLAN_CHAIN = 2,        /* layer i starts once layer i-1 (and its pooling) has
                                    finished, so it may read the shares layer i-1 wrote:
                                    a network's convolution stack (Fig. 2 lines 7-13,
                                    with the activation protocol left to the caller) */
+    FDSC_PLAN_TENSOR = 4        /* untuned layers with T <= 128 use the tensor-core
+                                   HomConv (the words do not change) */
 };
 
 typedef struct fdsc_plan fdsc_plan;

@@ -18,22 +18,34 @@
 // MMA mapping (tcgen05.mma kind::f16, M = 128 output channels in the TMEM
 // lanes, K = 16 input ciphertexts per instruction): the B operand stacks the
 // eight digit planes of X along N (rows (b, col), N = 8 NB), and the MMA of
-// filter digit plane a accumulates into the TMEM column window
-// [a NB, a NB + 8 NB): column block kappa then receives exactly the products
-// with a + b = kappa.  One MMA with a zero A operand clears the upper window
-// before the first accumulation.
+// filter digit plane a accumulates into a TMEM column window shifted by a NB
+// blocks: column block kappa then receives exactly the products with
+// a + b = kappa.  The eight digit planes of A are spread over S independent
+// accumulator sets (S = 8 / (NB / 2): all of TMEM for two items in flight),
+// plane a in set a mod S, so consecutive MMAs never wait for each other's
+// accumulator; the epilogue adds the sets (exact in fp32, same bound).  In a
+// set holding several planes, one MMA with a zero A operand clears the upper
+// part of its window before the first accumulation.
 //
 // Roles in a persistent CTA of 16 warps (one CTA per SM):
 //   warps 0-7   epilogue: TMEM -> diagonals -> 128-bit sum -> mod q -> HomShare
 //   warp 8      TMEM allocation; lane 0 issues the MMAs
-//   warps 9-15  producers: a bulk copy stages each unit's filter digit words,
-//               cp.async the input words; both are converted to fp16 digit
-//               planes in the canonical no-swizzle K-major layout.
+//   warp 9      loader: one bulk copy per unit for the filter digit words
+//               (lane 0)
+//   warps 10-15 converters: NC of them (as many as operand slots fit), each
+//               converting whole units into fp16 digit planes in the canonical
+//               no-swizzle K-major layout; a converter stages the input
+//               words (and the fused c1 addends) of its next unit with
+//               cp.async while it converts the current one.
+// Unit u goes to converter u mod NC and to that converter's own staging and
+// operand slots, so every slot is filled, converted and consumed in unit
+// order and no waiter can run two phases ahead of the mbarrier it polls
+// (a parity wait cannot tell phase k from phase k - 2).
 // A unit is (item, 16 input ciphertexts); an item is (J, 128 output channels,
-// up to 8 image groups).  Two TMEM accumulators let the MMAs of one item run
-// while the epilogue drains the previous one.  Every wait is bounded: on a
-// timeout the CTA records an error, stops, lets its copies and MMAs finish,
-// frees its TMEM and returns.
+// up to 8 image groups).  Staging and operand slots form mbarrier rings; two
+// TMEM accumulators let the MMAs of one item run while the epilogue drains
+// the previous one.  Every wait is bounded: on a timeout the CTA records an
+// error, stops, lets its copies and MMAs finish, frees its TMEM and returns.
 #include <cuda_fp16.h>
 
 #include "modarith.cuh"
@@ -43,21 +55,21 @@ namespace {
 constexpr u32 kThreadsTC = 512;
 constexpr u32 kEpiWarps = 8;
 constexpr u32 kMmaWarp = 8;
-constexpr u32 kProdWarp0 = 9;
-constexpr u32 kProdThreads = (16 - kProdWarp0) * 32;  // 224
-constexpr u32 kFS = 2;                                // fp16 operand slots
-constexpr u32 kMaxRS = 16;                            // staging slots at most
+constexpr u32 kLoadWarp = 9;
+constexpr u32 kConvWarp0 = 10;
+constexpr u32 kMaxConv = 6;   // converter warps at most
+constexpr u32 kMaxSlots = 8;  // barrier slots reserved per ring
 constexpr u64 kDigitBias = 0x8080808080808080ull;
 constexpr u64 kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 
 struct TcGeom {
-    u32 NB;        // B columns (bb, c) per item: 2 x image groups per pass
-    u32 KB;        // 16-ciphertext blocks: ceil(T / 16)
-    u32 n_ct;      // 128-channel tiles
-    u32 n_gbg;     // image-group passes
-    u32 gbt;       // image groups per pass (NB / 2)
-    u32 n_items;   // nJ * n_ct * n_gbg
-    u32 RS;        // staging slots
+    u32 NB;       // B columns (bb, c) per item: 2 x image groups per pass
+    u32 KB;       // 16-ciphertext blocks: ceil(T / 16)
+    u32 n_ct;     // 128-channel tiles
+    u32 n_gbg;    // image-group passes
+    u32 gbt;      // image groups per pass (NB / 2)
+    u32 n_items;  // nJ * n_ct * n_gbg
+    u32 NC;       // converter warps = staging slots = operand slots
     u32 off_f16, fsz, off_ra, raz, off_rx, rxz;
 };
 
@@ -95,12 +107,14 @@ __device__ __forceinline__ void mbar_arrive(u32 bar) {
 __device__ __forceinline__ void mbar_expect_tx(u32 bar, u32 bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+// try_wait with a suspend-time hint: a waiting warp sleeps in hardware until
+// the phase completes (or about 20 us pass) instead of spinning on issue slots
 __device__ __forceinline__ bool mbar_try(u32 bar, u32 parity) {
     u32 ok;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -136,17 +150,6 @@ __device__ __forceinline__ void cp_async8(u32 dst, const void* src) {
 __device__ __forceinline__ void cp_async_arrive(u32 bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
-// named barrier over the producer warps returning the OR of `pred`
-__device__ __forceinline__ bool producers_sync_or(bool pred) {
-    u32 r;
-    asm volatile(
-        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"((u32)pred), "r"(kProdThreads)
-        : "memory");
-    return r != 0;
-}
-
 template <int N>
 __device__ __forceinline__ void tmem_ld(u32 addr, u32 (&r)[N]);
 template <>
@@ -202,6 +205,37 @@ __device__ __forceinline__ void digit_rows(const u64 (&w)[8], uint4 (&row)[8]) {
     }
 }
 
+// Walks the units of one CTA: unit u -> item blockIdx.x + (u / KB) * grid,
+// ciphertext block u % KB; item -> (J fastest, channel tile, image-group
+// pass).  Advancing by d units costs a few adds (no divisions).
+struct UnitIter {
+    u32 grid, nJ, n_ct, KB;
+    u32 kb, J, ct, gbg;
+    __device__ UnitIter(u32 cta, u32 grid_, u32 nJ_, u32 n_ct_, u32 KB_, u32 u0)
+        : grid(grid_), nJ(nJ_), n_ct(n_ct_), KB(KB_) {
+        const u32 item = cta + (u0 / KB) * grid;
+        kb = u0 % KB;
+        J = item % nJ;
+        const u32 rest = item / nJ;
+        ct = rest % n_ct;
+        gbg = rest / n_ct;
+    }
+    __device__ void next(u32 d) {
+        kb += d;
+        while (kb >= KB) {
+            kb -= KB;
+            J += grid;
+            while (J >= nJ) {
+                J -= nJ;
+                if (++ct == n_ct) {
+                    ct = 0;
+                    gbg++;
+                }
+            }
+        }
+    }
+};
+
 // ---------------------------------------------------------------- the kernel
 template <int NBH>
 __global__ void __launch_bounds__(kThreadsTC, 1)
@@ -209,27 +243,29 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                       const u64* __restrict__ A2, const u64* __restrict__ Ptc, const u64* __restrict__ Mhat,
                       u64* __restrict__ ct_out, u32* __restrict__ err) {
     constexpr u32 NB = 2 * NBH;
+    constexpr u32 S = 8 / NBH;       // accumulator sets
+    constexpr u32 SETC = 16 * NB;    // columns of one set: 16 blocks of NB
+    constexpr u32 BUFC = S * SETC;   // columns of one accumulator (256)
     extern __shared__ __align__(1024) unsigned char sm[];
-    u64* bars = reinterpret_cast<u64*>(sm);
-    // barrier slots: raw_full[16], f16_full[2], f16_empty[2], tfull[2], tempty[2], drain
-    const u32 b_raw = smem_u32(bars), b_ffull = b_raw + 8 * kMaxRS, b_fempty = b_ffull + 16, b_tfull = b_fempty + 16,
-              b_tempty = b_tfull + 16, b_drain = b_tempty + 16;
-    volatile u32* tmem_slot = reinterpret_cast<volatile u32*>(sm + 240);
-    volatile u32* abort = reinterpret_cast<volatile u32*>(sm + 248);
+    // barriers: raw_full[8] raw_empty[8] f16_full[8] f16_empty[8] tfull[2] tempty[2] drain
+    const u32 b_rfull = smem_u32(sm), b_rempty = b_rfull + 64, b_ffull = b_rempty + 64, b_fempty = b_ffull + 64,
+              b_tfull = b_fempty + 64, b_tempty = b_tfull + 16, b_drain = b_tempty + 16;
+    volatile u32* tmem_slot = reinterpret_cast<volatile u32*>(sm + 400);
+    volatile u32* abort = reinterpret_cast<volatile u32*>(sm + 408);
     unsigned char* zero_blk = sm + 1024;
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const u32 nJ = L.beta * P.n;
     const u32 my_items = blockIdx.x < G.n_items ? (G.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const u32 total_units = my_items * G.KB;
-    const u32 tm_cols = 64 * NBH;  // two accumulators of 16 NB columns
 
-    // ---- setup: zero the operand slots (unused A rows and the zero block stay 0), barriers, TMEM
-    for (u32 e = tid; e < (G.off_f16 + kFS * G.fsz - 1024) / 16; e += kThreadsTC)
+    // ---- setup: zero block and operand slots (unused A rows stay 0), barriers, TMEM
+    for (u32 e = tid; e < (G.off_f16 + G.NC * G.fsz - 1024) / 16; e += kThreadsTC)
         reinterpret_cast<uint4*>(sm + 1024)[e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        for (u32 s = 0; s < kMaxRS; s++) mbar_init(b_raw + 8 * s, 1 + kProdThreads);
-        for (u32 s = 0; s < kFS; s++) {
-            mbar_init(b_ffull + 8 * s, kProdThreads / 32);
+        for (u32 s = 0; s < kMaxSlots; s++) {
+            mbar_init(b_rfull + 8 * s, 1);  // the loader's expect_tx; the bulk copy completes the bytes
+            mbar_init(b_rempty + 8 * s, 1);
+            mbar_init(b_ffull + 8 * s, 1);
             mbar_init(b_fempty + 8 * s, 1);
         }
         for (u32 s = 0; s < 2; s++) {
@@ -243,7 +279,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(
                          (const void*)tmem_slot)),
-                     "r"(tm_cols));
+                     "r"(2 * BUFC));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_async_smem();
@@ -252,100 +288,123 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     tc_fence_after();
     const u32 tmem = *tmem_slot;
 
-    if (warp >= kProdWarp0) {
-        // ================================================================ producers
-        const u32 pt = tid - kProdWarp0 * 32;
-        auto unit_item = [&](u32 u, u32& J, u32& ct, u32& gbg, u32& kb) {
-            const u32 item = blockIdx.x + (u / G.KB) * gridDim.x;
-            kb = u % G.KB;
-            J = item % nJ;
-            const u32 rest = item / nJ;
-            ct = rest % G.n_ct;
-            gbg = rest / G.n_ct;
-        };
-        // stage unit u: the filter digit words by one bulk copy, the input words by cp.async
-        auto issue = [&](u32 u) {
-            u32 J, ct, gbg, kb;
-            unit_item(u, J, ct, gbg, kb);
-            const u32 s = u % G.RS, bar = b_raw + 8 * s;
-            const u32 co0 = ct * 128, R = min(128u, L.Co - co0);
-            if (pt == 0) {
-                const u32 bytes = R * 128;
-                fence_async_smem();  // the slot's earlier generic reads come before the copy's writes
-                mbar_expect_tx(bar, bytes);
-                bulk_g2s(smem_u32(sm + G.off_ra + s * G.raz), Ptc + ((u64)(J * G.KB + kb) * L.Co + co0) * 16, bytes,
-                         bar);
+
+    if (warp == kLoadWarp) {
+        // ================================================================ loader (lane 0)
+        if (lane == 0) {
+            UnitIter it(blockIdx.x, gridDim.x, nJ, G.n_ct, G.KB, 0);
+            u32 u = 0;
+            for (; u < total_units; u++, it.next(1)) {
+                const u32 s = u % G.NC, bar = b_rfull + 8 * s;
+                if (!mbar_wait(b_rempty + 8 * s, ((u / G.NC) & 1) ^ 1, abort)) break;
+                const u32 co0 = it.ct * 128, R = min(128u, L.Co - co0);
+                mbar_expect_tx(bar, R * 128);
+                bulk_g2s(smem_u32(sm + G.off_ra + s * G.raz), Ptc + ((u64)(it.J * G.KB + it.kb) * L.Co + co0) * 16,
+                         R * 128, bar);
             }
-            const u32 h = J >> P.logn, j = J & (P.n - 1);
-            u64* xr = reinterpret_cast<u64*>(sm + G.off_rx + s * G.rxz);  // [3][16][NB]
-            const u32 bb0 = gbg * G.gbt;
-            for (u32 e = pt; e < 3 * 16 * NB; e += kProdThreads) {
-                const u32 plane = e / (16 * NB), kk = (e / NB) % 16, col = e % NB;
-                const u32 bbl = col >> 1, c = col & 1, k = kb * 16 + kk, bb = bb0 + bbl;
-                const u64* src = nullptr;
-                if (k < L.T && bb < L.GB) {
-                    const u64 uin = ((u64)bb * L.T + k) * L.beta + h;
-                    if (plane == 0)
-                        src = ct_in + (uin * 2 + c) * P.n + j;
-                    else if (c == 1)
-                        src = (plane == 1 ? A1 : A2) ? (plane == 1 ? A1 : A2) + uin * P.n + j : nullptr;
-                }
-                if (src)
-                    cp_async8(smem_u32(xr + e), src);
-                else
-                    xr[e] = 0;
+            if (u < total_units) {
+                *abort = 1;
+                atomicExch(err, 1u);
             }
-            cp_async_arrive(bar);
-        };
-        bool bad = false;
-        u32 issued = 0;
-        for (; issued < min(G.RS - 1, total_units); issued++) issue(issued);
-        u32 u = 0;
-        for (; u < total_units; u++) {
-            // every producer is done with unit u - 1, so its staging slot may be refilled
-            if (producers_sync_or(bad || *abort)) break;
-            if (issued < total_units && issued < u + G.RS) issue(issued++);
-            const u32 s = u % G.RS, fs = u % kFS;
-            bool ok = mbar_wait(b_raw + 8 * s, (u / G.RS) & 1, abort);
-            ok = ok && mbar_wait(b_fempty + 8 * fs, ((u / kFS) & 1) ^ 1, abort);
-            if (!__all_sync(0xffffffffu, ok)) {
-                bad = true;
-                continue;
-            }
-            u32 J, ct, gbg, kb;
-            unit_item(u, J, ct, gbg, kb);
-            const u32 R = min(128u, L.Co - ct * 128);
-            unsigned char* fA = sm + G.off_f16 + fs * G.fsz;
-            unsigned char* fX = fA + 32768;
-            const u64* ra = reinterpret_cast<const u64*>(sm + G.off_ra + s * G.raz);
-            const u64* xr = reinterpret_cast<const u64*>(sm + G.off_rx + s * G.rxz);
-            for (u32 t = pt; t < 2 * R + 2 * NB; t += kProdThreads) {
-                u64 w[8];
-                uint4 row[8];
-                if (t < 2 * R) {
-                    // filter: row co, input ciphertexts k8*8 .. k8*8+7 (already biased)
-                    const u32 co = t >> 1, k8 = t & 1;
-                    const uint4* src = reinterpret_cast<const uint4*>(ra + co * 16 + k8 * 8);
-#pragma unroll
-                    for (int i = 0; i < 4; i++) {
-                        const uint4 v = src[i];
-                        w[2 * i] = ((u64)v.y << 32) | v.x;
-                        w[2 * i + 1] = ((u64)v.w << 32) | v.z;
+            // copies still in flight land before the CTA may exit (the last NC units at most)
+            for (u32 v = u > G.NC ? u - G.NC : 0; v < u; v++) mbar_drain(b_rfull + 8 * (v % G.NC), (v / G.NC) & 1);
+        }
+        __syncwarp();
+    } else if (warp >= kConvWarp0) {
+        // ================================================================ converters
+        const u32 cw = warp - kConvWarp0, s = cw, fs = cw;  // this converter's own slots
+        if (cw < G.NC && cw < total_units) {
+            // input words of a unit, staged by this warp's lanes with cp.async:
+            // [16][NB] ciphertext words, then [16][NB/2] A1 and [16][NB/2] A2 words of
+            // the c1 columns; double-buffered so the next unit's copies fly while
+            // this one is converted
+            u64* xbuf = reinterpret_cast<u64*>(sm + G.off_rx + cw * G.rxz);
+            auto stage_x = [&](const UnitIter& t, u64* xr) {
+                const u32 h = t.J >> P.logn, j = t.J & (P.n - 1), bb0 = t.gbg * G.gbt;
+#pragma unroll 2
+                for (u32 e = lane; e < 32 * NB; e += 32) {
+                    u32 plane, kk, col;
+                    if (e < 16 * NB) {
+                        plane = 0, kk = e / NB, col = e % NB;
+                    } else {
+                        const u32 r = (e - 16 * NB) % (8 * NB);
+                        plane = 1 + (e - 16 * NB) / (8 * NB), kk = r / NBH, col = 2 * (r % NBH) + 1;
                     }
-                    digit_rows(w, row);
-                    const u32 off = (co >> 3) * 256 + k8 * 128 + (co & 7) * 16;
+                    const u32 c = col & 1, k = t.kb * 16 + kk, bb = bb0 + (col >> 1);
+                    const u64* base = plane == 0 ? ct_in : (plane == 1 ? A1 : A2);
+                    if (k < L.T && bb < L.GB && base) {
+                        const u64 uin = ((u64)bb * L.T + k) * L.beta + h;
+                        cp_async8(smem_u32(xr + e), base + (plane == 0 ? uin * 2 + c : uin) * P.n + j);
+                    } else {
+                        xr[e] = 0;
+                    }
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            };
+            UnitIter it(blockIdx.x, gridDim.x, nJ, G.n_ct, G.KB, cw);
+            stage_x(it, xbuf);
+            u32 par = 0;
+            for (u32 u = cw; u < total_units; u += G.NC, par ^= 1) {
+                UnitIter nx = it;
+                nx.next(G.NC);
+                if (u + G.NC < total_units)
+                    stage_x(nx, xbuf + (par ^ 1) * 32 * NB);
+                else
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                bool ok = mbar_wait(b_rfull + 8 * s, (u / G.NC) & 1, abort);
+                ok = ok && mbar_wait(b_fempty + 8 * fs, ((u / G.NC) & 1) ^ 1, abort);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    *abort = 1;
+                    atomicExch(err, 4u);
+                    break;
+                }
+                asm volatile("cp.async.wait_group 1;" ::: "memory");  // this unit's input words
+                __syncwarp();
+                const u32 R = min(128u, L.Co - it.ct * 128);
+                unsigned char* fA = sm + G.off_f16 + fs * G.fsz;
+                unsigned char* fX = fA + 32768;
+                const uint4* ra = reinterpret_cast<const uint4*>(sm + G.off_ra + s * G.raz);  // [4][2R] x 16 B
+                const u64* xr = xbuf + par * 32 * NB;
+                // filter task t = (co, k8): words k8*8 .. k8*8+7 of row co, stored as 4
+                // chunks of 2 words at stride 2R chunks (conflict-free reads); two tasks
+                // per round for instruction-level parallelism
+                for (u32 t0 = lane; t0 < 2 * R; t0 += 64) {
+                    u64 w[2][8];
+                    uint4 row[2][8];
 #pragma unroll
-                    for (int a = 0; a < 8; a++) *reinterpret_cast<uint4*>(fA + a * 4096 + off) = row[a];
-                } else {
-                    // input: column col, k8*8 .. k8*8+7; c1 gets the addends mod q, then the bias
-                    const u32 col = (t - 2 * R) >> 1, k8 = (t - 2 * R) & 1;
+                    for (int q = 0; q < 2; q++) {
+                        const u32 t = t0 + 32 * q < 2 * R ? t0 + 32 * q : t0;
+#pragma unroll
+                        for (int i = 0; i < 4; i++) {
+                            const uint4 v = ra[i * 2 * R + t];
+                            w[q][2 * i] = ((u64)v.y << 32) | v.x;
+                            w[q][2 * i + 1] = ((u64)v.w << 32) | v.z;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 2; q++) digit_rows(w[q], row[q]);
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const u32 t = t0 + 32 * q;
+                        if (t >= 2 * R) continue;
+                        const u32 co = t >> 1, k8 = t & 1;
+                        const u32 off = (co >> 3) * 256 + k8 * 128 + (co & 7) * 16;
+#pragma unroll
+                        for (int a = 0; a < 8; a++) *reinterpret_cast<uint4*>(fA + a * 4096 + off) = row[q][a];
+                    }
+                }
+                // input task (col, k8): ciphertexts k8*8 .. k8*8+7; c1 gets the addends mod q
+                for (u32 t = lane; t < 2 * NB; t += 32) {
+                    u64 w[8];
+                    uint4 row[8];
+                    const u32 col = t >> 1, k8 = t & 1;
 #pragma unroll
                     for (int i = 0; i < 8; i++) {
                         const u32 kk = k8 * 8 + i;
                         u64 x = xr[kk * NB + col];
                         if (col & 1) {
-                            x = addmod_q(x, xr[16 * NB + kk * NB + col], P.q);
-                            x = addmod_q(x, xr[32 * NB + kk * NB + col], P.q);
+                            x = addmod_q(x, xr[16 * NB + kk * NBH + (col >> 1)], P.q);
+                            x = addmod_q(x, xr[24 * NB + kk * NBH + (col >> 1)], P.q);
                         }
                         w[i] = x + kDigitBias;
                     }
@@ -354,20 +413,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     for (int b = 0; b < 8; b++)
                         *reinterpret_cast<uint4*>(fX + k8 * (8 * NB * 16) + (b * NB + col) * 16) = row[b];
                 }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(b_rempty + 8 * s);
+                    mbar_arrive(b_ffull + 8 * fs);
+                }
+                it = nx;
             }
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(b_ffull + 8 * fs);
+            asm volatile("cp.async.wait_all;" ::: "memory");
         }
-        if (u < total_units) {
-            *abort = 1;
-            atomicExch(err, 1u);
-            // let the copies already issued land before the CTA may exit: at most
-            // the last RS units issued can still be in flight, one per slot
-            for (u32 v = issued > G.RS ? issued - G.RS : 0; v < issued; v++)
-                mbar_drain(b_raw + 8 * (v % G.RS), (v / G.RS) & 1);
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == kMmaWarp) {
         // ================================================================ MMA issue
         if (lane == 0) {
@@ -382,10 +437,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     break;
                 }
                 tc_fence_after();
-                const u32 dcol = tmem + b * 16 * NB;
+                const u32 dbuf = tmem + b * BUFC;
                 for (u32 kb = 0; kb < G.KB; kb++, u++) {
-                    const u32 fs = u % kFS;
-                    if (!mbar_wait(b_ffull + 8 * fs, (u / kFS) & 1, abort)) {
+                    const u32 fs = u % G.NC;
+                    if (!mbar_wait(b_ffull + 8 * fs, (u / G.NC) & 1, abort)) {
                         ok = false;
                         break;
                     }
@@ -394,8 +449,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     const u64 xdesc = sdesc(fA + 32768, 8 * NB * 16, 128);
 #pragma unroll
                     for (u32 a = 0; a < 8; a++) {
-                        mma_f16(dcol + a * NB, sdesc(fA + a * 4096, 128, 256), xdesc, idesc, (kb | a) ? 1u : 0u);
-                        if (kb == 0 && a == 0) mma_f16(dcol + 8 * NB, zdesc, xdesc, idesc, 0u);
+                        const u32 set = a % S, rel = a - set;  // plane a: set a mod S, window shifted by rel blocks
+                        const u32 d = dbuf + set * SETC + rel * NB;
+                        mma_f16(d, sdesc(fA + a * 4096, 128, 256), xdesc, idesc, (kb != 0 || rel != 0) ? 1u : 0u);
+                        if (S < 8 && kb == 0 && rel == 0) mma_f16(dbuf + set * SETC + 8 * NB, zdesc, xdesc, idesc, 0u);
                     }
                     mma_commit(b_fempty + 8 * fs);
                 }
@@ -417,40 +474,65 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const u32 lane_addr = (quarter * 32) << 16;
         for (u32 li = 0; li < my_items; li++) {
             const u32 b = li & 1;
+            const u32 item = blockIdx.x + li * gridDim.x;
+            const u32 J = item % nJ, rest = item / nJ, ct = rest % G.n_ct, gbg = rest / G.n_ct;
+            const u32 h = J >> P.logn, j = J & (P.n - 1);
+            const u32 co = ct * 128 + r;
+            const u32 col0 = hc * NBH;
+            // the HomShare mask words of this thread's c1 outputs, fetched while the MMAs run
+            u64 mk[NBH];
+#pragma unroll
+            for (int i = 0; i < NBH; i++) {
+                const u32 col = col0 + i, bb = gbg * G.gbt + (col >> 1);
+                mk[i] = 0;
+                if ((col & 1) && Mhat && co < L.Co && bb < L.GB)
+                    mk[i] = __ldg(Mhat + (((u64)bb * L.Co + co) * L.beta + h) * P.n + j);
+            }
             if (!__all_sync(0xffffffffu, mbar_wait(b_tfull + 8 * b, (li >> 1) & 1, abort))) {
                 *abort = 1;
                 atomicExch(err, 3u);
                 break;
             }
             tc_fence_after();
-            const u32 item = blockIdx.x + li * gridDim.x;
-            const u32 J = item % nJ, rest = item / nJ, ct = rest % G.n_ct, gbg = rest / G.n_ct;
-            const u32 h = J >> P.logn, j = J & (P.n - 1);
-            const u32 co = ct * 128 + r;
-            const u32 col0 = hc * NBH;
-            const u32 base = tmem + lane_addr + b * 16 * NB + col0;
+            const u32 base = tmem + lane_addr + b * BUFC + col0;
             unsigned __int128 V[NBH];  // the sum mod 2^128: exact, since it lies in [0, 2^127)
 #pragma unroll
             for (int i = 0; i < NBH; i++) V[i] = 0;
 #pragma unroll
             for (u32 m = 0; m < 4; m++) {
-                u32 d[4][NBH];
+                // diagonals 4m .. 4m+3, each the sum of its sets
+                u32 d[4][S][NBH];
 #pragma unroll
                 for (u32 rr = 0; rr < 4; rr++)
-                    if (4 * m + rr < 15) tmem_ld<NBH>(base + (4 * m + rr) * NB, d[rr]);
+#pragma unroll
+                    for (u32 st = 0; st < S; st++) {
+                        const u32 kap = 4 * m + rr;
+                        if (kap < 15 && kap >= st && kap - st < 16 - S)
+                            tmem_ld<NBH>(base + st * SETC + (kap - st) * NB, d[rr][st]);
+                    }
                 tmem_wait_ld();
-                // the loaded registers are used only after the wait
 #pragma unroll
                 for (u32 rr = 0; rr < 4; rr++)
 #pragma unroll
-                    for (int i = 0; i < NBH; i++)
-                        if (4 * m + rr < 15) asm volatile("" : "+r"(d[rr][i]));
+                    for (u32 st = 0; st < S; st++)
+#pragma unroll
+                        for (int i = 0; i < NBH; i++) {
+                            const u32 kap = 4 * m + rr;
+                            if (kap < 15 && kap >= st && kap - st < 16 - S) asm volatile("" : "+r"(d[rr][st][i]));
+                        }
 #pragma unroll
                 for (int i = 0; i < NBH; i++) {
                     long long cm = 0;
 #pragma unroll
-                    for (u32 rr = 0; rr < 4; rr++)
-                        if (4 * m + rr < 15) cm += (long long)__float2int_rn(__uint_as_float(d[rr][i])) * (1ll << (8 * rr));
+                    for (u32 rr = 0; rr < 4; rr++) {
+                        const u32 kap = 4 * m + rr;
+                        if (kap >= 15) continue;
+                        float f = 0.f;  // exact: every partial sum is an integer below 2^24
+#pragma unroll
+                        for (u32 st = 0; st < S; st++)
+                            if (kap >= st && kap - st < 16 - S) f += __uint_as_float(d[rr][st][i]);
+                        cm += (long long)__float2int_rn(f) * (1ll << (8 * rr));
+                    }
                     V[i] += (unsigned __int128)(__int128)cm << (32 * m);
                 }
             }
@@ -464,9 +546,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     if (bb >= L.GB) continue;
                     const unsigned __int128 v = V[i];
                     u64 res = reduce128((u64)(v >> 64), (u64)v, P);
-                    const u64 vo = ((u64)bb * L.Co + co) * L.beta + h;
-                    if (c == 1 && Mhat) res = submod_q(res, __ldg(Mhat + vo * P.n + j), P.q);
-                    ct_out[(vo * 2 + c) * P.n + j] = res;
+                    if (c == 1) res = submod_q(res, mk[i], P.q);
+                    ct_out[((((u64)bb * L.Co + co) * L.beta + h) * 2 + c) * P.n + j] = res;
                 }
             }
         }
@@ -475,18 +556,22 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     __syncthreads();
     if (warp == kMmaWarp) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tm_cols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BUFC));
     }
 }
 
-// Phat [Co][T][beta][n] -> Ptc [J][KB][Co][16]: the words of 16 consecutive
-// input ciphertexts of one output channel contiguous per J, biased by
-// 0x80..80; ciphertexts past T hold the bias alone (digits 0).
+// Phat [Co][T][beta][n] -> Ptc: per (J, 16-ciphertext block kb, 128-channel
+// tile of R rows) one contiguous unit of R x 16 words, biased by 0x80..80
+// (ciphertexts past T hold the bias alone).  Within a unit, word (co, k) with
+// k = 8 k8 + 2 i + e sits in 16-byte chunk i * 2R + (2 co + k8), half e, so
+// that a converter lane reading its four chunks of task (co, k8) hits
+// consecutive chunks across the warp.
 __global__ void filter_tc_kernel(const DevParams P, const DevLayer L, u32 KB, const u64* __restrict__ Phat,
                                  u64* __restrict__ Ptc) {
     __shared__ u64 tile[16][65];
     const u32 nJ = L.beta * P.n;
     const u32 J0 = blockIdx.x * 64, kb = blockIdx.y, co = blockIdx.z;
+    const u32 co0 = co & ~127u, R = min(128u, L.Co - co0), cl = co - co0;
     for (u32 e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
         const u32 kk = e / 64, jj = e % 64, k = kb * 16 + kk, J = J0 + jj;
         u64 v = kDigitBias;
@@ -496,11 +581,14 @@ __global__ void filter_tc_kernel(const DevParams P, const DevLayer L, u32 KB, co
     __syncthreads();
     for (u32 e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
         const u32 jj = e / 16, kk = e % 16, J = J0 + jj;
-        if (J < nJ) Ptc[(((u64)J * KB + kb) * L.Co + co) * 16 + kk] = tile[kk][jj];
+        const u32 k8 = kk >> 3, i = (kk >> 1) & 3, half = kk & 1;
+        if (J < nJ)
+            Ptc[((u64)J * KB + kb) * L.Co * 16 + (u64)co0 * 16 + ((u64)i * 2 * R + 2 * cl + k8) * 2 + half] =
+                tile[kk][jj];
     }
 }
 
-__device__ u32 g_tc_err;  // nonzero after a CTA gave up waiting (1 producer, 2 MMA, 3 epilogue)
+__device__ u32 g_tc_err;  // nonzero after a CTA gave up waiting (1 loader, 2 MMA, 3 epilogue, 4 converter)
 
 }  // namespace
 
@@ -519,21 +607,23 @@ static bool tc_geom(u32 n, const DevLayer& L, TcGeom& G, size_t& smem) {
     G.n_items = (u32)items;
     const u32 rmax = L.Co < 128 ? L.Co : 128;
     G.raz = rmax * 128;
-    G.RS = 65536 / G.raz;
-    G.RS = G.RS < 2 ? 2 : (G.RS > kMaxRS ? kMaxRS : G.RS);
+    G.rxz = 2 * 32 * G.NB * 8;  // a converter's two input-word buffers
     G.fsz = 32768 + 256 * G.NB;
     G.off_f16 = 1024 + 4096;
-    G.off_ra = G.off_f16 + kFS * G.fsz;
-    G.rxz = 3 * 16 * G.NB * 8;
-    G.off_rx = G.off_ra + G.RS * G.raz;
-    smem = G.off_rx + G.RS * G.rxz;
-    return true;
+    const size_t budget = 227 * 1024;
+    const size_t nc = (budget - G.off_f16) / ((size_t)G.fsz + G.raz + G.rxz);  // one slot of each per converter
+    if (nc < 2) return false;
+    G.NC = (u32)(nc > kMaxConv ? kMaxConv : nc);
+    G.off_ra = G.off_f16 + G.NC * G.fsz;
+    G.off_rx = G.off_ra + G.NC * G.raz;
+    smem = G.off_rx + G.NC * G.rxz;
+    return smem <= budget;
 }
 
 bool homconv_tc_supported(u32 n, const DevLayer& L) {
     TcGeom G;
     size_t smem;
-    return tc_geom(n, L, G, smem) && smem <= 227 * 1024;
+    return tc_geom(n, L, G, smem);
 }
 
 u64 filter_tc_words(u32 n, const DevLayer& L) { return (u64)L.beta * n * ((L.T + 15) / 16) * L.Co * 16; }
@@ -555,11 +645,18 @@ static cudaError_t launch_tc(const DevParams& P, const DevLayer& L, const TcGeom
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    cudaError_t e = cudaFuncSetAttribute(homconv_tc_kernel<NBH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    u32* errp = nullptr;
-    e = cudaGetSymbolAddress((void**)&errp, g_tc_err);
-    if (e != cudaSuccess) return e;
+    static size_t smem_set = 0;
+    cudaError_t e = cudaSuccess;
+    if (smem > smem_set) {
+        e = cudaFuncSetAttribute(homconv_tc_kernel<NBH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
+    static u32* errp = nullptr;
+    if (!errp) {
+        e = cudaGetSymbolAddress((void**)&errp, g_tc_err);
+        if (e != cudaSuccess) return e;
+    }
     const u32 grid = G.n_items < (u32)sms ? G.n_items : (u32)sms;
     homconv_tc_kernel<NBH><<<grid, kThreadsTC, smem, s>>>(P, L, G, ct_in, A1, A2, Ptc, Mhat, ct_out, errp);
     return cudaGetLastError();
@@ -569,7 +666,7 @@ cudaError_t launch_homconv_tc(const DevParams& P, const DevLayer& L, const u64* 
                               const u64* Ptc, const u64* Mhat, u64* ct_out, cudaStream_t s) {
     TcGeom G;
     size_t smem;
-    if (!tc_geom(P.n, L, G, smem) || smem > 227 * 1024) return cudaErrorInvalidValue;
+    if (!tc_geom(P.n, L, G, smem)) return cudaErrorInvalidValue;
     switch (G.gbt) {
         case 1: return launch_tc<1>(P, L, G, smem, ct_in, A1, A2, Ptc, Mhat, ct_out, s);
         case 2: return launch_tc<2>(P, L, G, smem, ct_in, A1, A2, Ptc, Mhat, ct_out, s);

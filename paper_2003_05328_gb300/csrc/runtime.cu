@@ -76,6 +76,7 @@ struct PlanLayer {
     uint32_t candidates = 0;
     double tuned_us = 0;
     u64 *Phat = nullptr, *Mhat = nullptr, *ct = nullptr, *A = nullptr, *R = nullptr, *ct_out = nullptr;
+    u64* Ptc = nullptr;  // the filter in the tensor-core layout (variant kTensorVariant only)
     u32 *sB = nullptr, *X = nullptr, *XB = nullptr, *SA = nullptr;
 };
 
@@ -91,11 +92,22 @@ struct fdsc_plan {
 
 namespace {
 
+// HomConv variant number of the tensor-core kernel (homconv_tc.cu) in a plan.
+constexpr int kTensorVariant = 7;
+
+// The HomConv of a layer with its chosen variant.
+cudaError_t plan_homconv(const DevParams& P, const PlanLayer& pl, const u64* A1, const u64* A2, cudaStream_t s) {
+    if (pl.variant == kTensorVariant)
+        return launch_homconv_tc(P, pl.D, pl.ct, A1, A2, pl.Ptc, pl.Mhat, pl.ct_out, s);
+    return launch_homconv_v(P, pl.D, pl.ct, A1, A2, pl.Phat, pl.Mhat, pl.ct_out, pl.variant, s);
+}
+
 // Buffers of one layer for one packing (the filter plaintexts and masks
 // depend on the packing).
 int plan_alloc_layer(PlanLayer& pl, Arena& ar, fdsc_layout& lay) {
     const fdsc_params_info& I = pl.spec.params->info;
     int rc;
+    if (pl.variant == kTensorVariant && (rc = ar.alloc((void**)&pl.Ptc, filter_tc_words(I.n, pl.D) * 8))) return rc;
     if ((rc = ar.alloc((void**)&pl.Phat, lay.filter_words * 8)) || (rc = ar.alloc((void**)&pl.Mhat, lay.mask_words * 8)) ||
         (rc = ar.alloc((void**)&pl.sB, lay.out_spectra_words * 4)) || (rc = ar.alloc((void**)&pl.ct, lay.ct_in_words * 8)) ||
         (rc = ar.alloc((void**)&pl.ct_out, lay.ct_out_words * 8)))
@@ -114,6 +126,7 @@ int plan_alloc_layer(PlanLayer& pl, Arena& ar, fdsc_layout& lay) {
 int plan_setup_layer(PlanLayer& pl, cudaStream_t s) {
     const DevParams& P = pl.spec.params->dev;
     RT_TRY(launch_filter_prepare(P, pl.D, pl.spec.w, pl.spec.fh, pl.spec.fw, pl.Phat, s));
+    if (pl.variant == kTensorVariant) RT_TRY(launch_filter_tc(P, pl.D, pl.Phat, pl.Ptc, s));
     RT_TRY(launch_mask_prepare(P, pl.D, pl.spec.mask_seed, nullptr, pl.spec.flood_bits, pl.Mhat, pl.sB, s));
     return FDSC_OK;
 }
@@ -137,7 +150,7 @@ int plan_record_layer(PlanLayer& pl, cudaStream_t* st, cudaEvent_t* ev) {
         RT_TRY(cudaEventRecord(ev[2], st[2]));
         RT_TRY(cudaStreamWaitEvent(st[0], ev[1], 0));
         RT_TRY(cudaStreamWaitEvent(st[0], ev[2], 0));
-        RT_TRY(launch_homconv_v(P, D, pl.ct, pl.A, pl.R, pl.Phat, pl.Mhat, pl.ct_out, pl.variant, st[0]));
+        RT_TRY(plan_homconv(P, pl, pl.A, pl.R, st[0]));
         RT_TRY(launch_decrypt_share(P, D, sp.t_hat, 0, pl.ct_out, sp.yA, st[0]));
     } else {
         const u64 planes_in = (u64)D.B * D.Ci;
@@ -149,7 +162,7 @@ int plan_record_layer(PlanLayer& pl, cudaStream_t* st, cudaEvent_t* ev) {
         RT_TRY(cudaEventRecord(ev[1], st[1]));
         RT_TRY(cudaStreamWaitEvent(st[0], ev[1], 0));
         RT_TRY(launch_homrec(P, D, pl.XB, pl.ct, st[0]));
-        RT_TRY(launch_homconv_v(P, D, pl.ct, nullptr, nullptr, pl.Phat, pl.Mhat, pl.ct_out, pl.variant, st[0]));
+        RT_TRY(plan_homconv(P, pl, nullptr, nullptr, st[0]));
         RT_TRY(launch_decrypt(P, D, sp.t_hat, pl.ct_out, pl.SA, st[0]));
         RT_TRY(launch_ntt2d(P, D.H, D.W, pl.SA, sp.yA, planes_out, true, st[0]));
     }
@@ -254,6 +267,7 @@ extern "C" int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, u
             return fail(fdsc_set_error(FDSC_ERR_ARG, "layer %u: filter does not fit the plane", i));
         pl.fused = fused_ok(pl.D);
         pl.variant = homconv_default_variant(pl.D);
+        if ((flags & FDSC_PLAN_TENSOR) && homconv_tc_supported(I.n, pl.D)) pl.variant = kTensorVariant;
         cudaStream_t* st = &plan->streams[4 * (size_t)i];
         cudaEvent_t* ev = &plan->events[4 * (size_t)i];
         if ((flags & FDSC_PLAN_TUNE) && pl.fused) {
@@ -266,7 +280,7 @@ extern "C" int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, u
                 packs.push_back({std::min(gc, sp.layer.Ci), gb});
             }
             if (packs.empty()) packs.push_back({pl.L.g_c, pl.L.g_b});
-            const int variants[] = {3, 4, 2};
+            const int variants[] = {3, 4, 2, kTensorVariant};
             double best = 1e30;
             fdsc_layer bestL = pl.L;
             int bestV = pl.variant;
@@ -281,6 +295,7 @@ extern "C" int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, u
                         !fdsc_noise_ok_flood(I, Dt.T, sp.flood_bits))
                         continue;
                     if (v == 2 && Dt.GB < 2) continue;
+                    if (v == kTensorVariant && !homconv_tc_supported(I.n, Dt)) continue;
                     double us = 0;
                     if ((rc = plan_time_candidate(cand, st, ev, &us))) return fail(rc);
                     pl.candidates++;

@@ -528,6 +528,7 @@ class PlanLayerInfo(C.Structure):
 
 PLAN_TUNE = 1
 PLAN_CHAIN = 2
+PLAN_TENSOR = 4
 
 
 class Plan:
@@ -537,7 +538,7 @@ class Plan:
     choose), w (int8 [Co][Ci][fh][fw]), t_hat, enc_seed, mask_seed, xA, xB, yA,
     yB (device tensors)."""
 
-    def __init__(self, layers, tune=False, stream=None, chain=False):
+    def __init__(self, layers, tune=False, stream=None, chain=False, tensor=False):
         arr = (PlanLayerC * len(layers))()
         self._keep = layers
         for i, d in enumerate(layers):
@@ -550,7 +551,7 @@ class Plan:
                                 d["pB"].data_ptr() if d.get("pB") is not None else None,
                                 d.get("flood_bits", 0), 0)
         h = _vp()
-        flags = (PLAN_TUNE if tune else 0) | (PLAN_CHAIN if chain else 0)
+        flags = (PLAN_TUNE if tune else 0) | (PLAN_CHAIN if chain else 0) | (PLAN_TENSOR if tensor else 0)
         _call("fdsc_plan_create", C.addressof(arr), len(layers), flags, _stream(stream), C.byref(h))
         self.handle = h
 

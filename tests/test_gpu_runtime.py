@@ -55,10 +55,11 @@ def _make_layers(F, seed):
     return specs, refs, params
 
 
-@pytest.mark.parametrize("tune", [False, True])
-def test_plan_of_uneven_layers_matches_oracle(F, tune):
+@pytest.mark.parametrize("tune,tensor", [(False, False), (True, False), (False, True)])
+def test_plan_of_uneven_layers_matches_oracle(F, tune, tensor):
+    """tensor: every layer's HomConv on the tensor cores (all have T <= 128)."""
     specs, refs, params = _make_layers(F, 5 + tune)
-    plan = F.Plan(specs, tune=tune)
+    plan = F.Plan(specs, tune=tune, tensor=tensor)
     for rep in range(2):
         for d in specs:
             d["yA"].zero_()
@@ -72,6 +73,9 @@ def test_plan_of_uneven_layers_matches_oracle(F, tune):
     assert [x.fused for x in infos] == [1, 1, 1, 0, 1]
     if tune:
         assert all(x.candidates > 0 for x, f in zip(infos, [1, 1, 1, 0, 1]) if f)
+    if tensor:
+        assert [x.homconv_variant for x in infos] == [7] * len(LAYERS)
+        assert F.homconv_tc_status() == 0
     plan.close()
     for P in params:
         P.close()
