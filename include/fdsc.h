@@ -240,17 +240,20 @@ int fdsc_homconv_sum(const fdsc_params* P, const fdsc_layer* L, const uint64_t* 
  * tcgen05 MMAs in fp32 into the 15 weight classes 256^kappa (exact: every
  * partial sum stays below 2^24 for T <= 128), and the classes are combined
  * into the 128-bit sum and reduced mod q once.
- * fdsc_filter_tc_words: the size in uint64 words of the digit-ready filter
+ * fdsc_filter_tc_words: the size in uint64 words of the digit-plane filter
  * for layer L at (n, p) (host only); FDSC_ERR_UNSUPPORTED if T > 128.
  * fdsc_filter_tc: P_hat uint64 [Co][T][beta][n] (fdsc_filter_prepare) ->
- * P_tc uint64 [beta n][ceil(T/16)][Co][16], each word biased by 0x80..80
- * (ciphertexts past T hold the bias alone); setup, once per filter.
+ * P_tc: per evaluation index J < beta n, block of 16 input ciphertexts and
+ * tile of up to 128 output channels (rows rounded up to a multiple of 8),
+ * the eight fp16 digit planes of the filter words in the canonical layout of
+ * a tcgen05 A operand (256 bytes per row); twice the bytes of P_hat.  Setup,
+ * once per filter.
  * fdsc_homconv_tc: as fdsc_homconv_sum with P_tc in place of P_hat; ct_out
  * must not overlap any input.  Launches one persistent CTA per SM.
  * fdsc_homconv_tc_status: after synchronizing, 0 in *code if no CTA of the
  * tensor-core kernel gave up a bounded wait since the last call; otherwise
- * the role that did (1 producer, 2 MMA, 3 epilogue) and FDSC_ERR_TIMEOUT
- * (that launch's output is not valid).  Resets the flag. */
+ * the role that did (1 loader, 2 MMA, 3 epilogue, 4 converter) and
+ * FDSC_ERR_TIMEOUT (that launch's output is not valid).  Resets the flag. */
 int fdsc_filter_tc_words(uint32_t n, uint32_t p, const fdsc_layer* L, uint64_t* words);
 int fdsc_filter_tc(const fdsc_params* P, const fdsc_layer* L, const uint64_t* P_hat, uint64_t* P_tc,
                    void* stream);

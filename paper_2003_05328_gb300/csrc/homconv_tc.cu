@@ -69,9 +69,18 @@ struct TcGeom {
     u32 n_gbg;    // image-group passes
     u32 gbt;      // image groups per pass (NB / 2)
     u32 n_items;  // nJ * n_ct * n_gbg
-    u32 NC;       // converter warps = staging slots = operand slots
-    u32 off_f16, fsz, off_ra, raz, off_rx, rxz;
+    u32 NC;       // converter warps = operand slots
+    u32 co_pad;   // filter rows stored per unit group: tiles of 128, the last rounded up to 8
+    u32 az;       // bytes of a slot's A operand region
+    u32 ssz;      // bytes of one slot (A, input digit planes, input-word buffers)
+    u32 off_slot; // first slot
 };
+
+// Rows of 128-channel tile ct, rounded up to a multiple of 8.
+__host__ __device__ inline u32 tile_rows8(u32 Co, u32 ct) {
+    const u32 r = Co - 128 * ct < 128 ? Co - 128 * ct : 128;
+    return (r + 7) & ~7u;
+}
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
@@ -145,10 +154,6 @@ __device__ __forceinline__ void bulk_g2s(u32 dst, const void* src, u32 bytes, u3
 }
 __device__ __forceinline__ void cp_async8(u32 dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
-}
-// arrives on bar once this thread's earlier cp.async copies have landed
-__device__ __forceinline__ void cp_async_arrive(u32 bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 template <int N>
 __device__ __forceinline__ void tmem_ld(u32 addr, u32 (&r)[N]);
@@ -240,16 +245,15 @@ struct UnitIter {
 template <int NBH>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     homconv_tc_kernel(DevParams P, DevLayer L, TcGeom G, const u64* __restrict__ ct_in, const u64* __restrict__ A1,
-                      const u64* __restrict__ A2, const u64* __restrict__ Ptc, const u64* __restrict__ Mhat,
-                      u64* __restrict__ ct_out, u32* __restrict__ err) {
+                      const u64* __restrict__ A2, const unsigned char* __restrict__ Ptc,
+                      const u64* __restrict__ Mhat, u64* __restrict__ ct_out, u32* __restrict__ err) {
     constexpr u32 NB = 2 * NBH;
-    constexpr u32 S = 8 / NBH;       // accumulator sets
-    constexpr u32 SETC = 16 * NB;    // columns of one set: 16 blocks of NB
-    constexpr u32 BUFC = S * SETC;   // columns of one accumulator (256)
+    constexpr u32 BUFC = 16 * NB;               // TMEM columns of one accumulator: 16 blocks of NB
+    constexpr u32 NBUF = 512 / BUFC > 8 ? 8 : 512 / BUFC;  // accumulators in flight
     extern __shared__ __align__(1024) unsigned char sm[];
-    // barriers: raw_full[8] raw_empty[8] f16_full[8] f16_empty[8] tfull[2] tempty[2] drain
-    const u32 b_rfull = smem_u32(sm), b_rempty = b_rfull + 64, b_ffull = b_rempty + 64, b_fempty = b_ffull + 64,
-              b_tfull = b_fempty + 64, b_tempty = b_tfull + 16, b_drain = b_tempty + 16;
+    // barriers: a_full[8] x_full[8] s_empty[8] tfull[8] tempty[8] drain
+    const u32 b_afull = smem_u32(sm), b_xfull = b_afull + 64, b_sempty = b_xfull + 64, b_tfull = b_sempty + 64,
+              b_tempty = b_tfull + 64, b_drain = b_tempty + 64;
     volatile u32* tmem_slot = reinterpret_cast<volatile u32*>(sm + 400);
     volatile u32* abort = reinterpret_cast<volatile u32*>(sm + 408);
     unsigned char* zero_blk = sm + 1024;
@@ -258,17 +262,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const u32 my_items = blockIdx.x < G.n_items ? (G.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const u32 total_units = my_items * G.KB;
 
-    // ---- setup: zero block and operand slots (unused A rows stay 0), barriers, TMEM
-    for (u32 e = tid; e < (G.off_f16 + G.NC * G.fsz - 1024) / 16; e += kThreadsTC)
+    // ---- setup: zero block and operand slots, barriers, TMEM
+    for (u32 e = tid; e < (G.off_slot + G.NC * G.ssz - 1024) / 16; e += kThreadsTC)
         reinterpret_cast<uint4*>(sm + 1024)[e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         for (u32 s = 0; s < kMaxSlots; s++) {
-            mbar_init(b_rfull + 8 * s, 1);  // the loader's expect_tx; the bulk copy completes the bytes
-            mbar_init(b_rempty + 8 * s, 1);
-            mbar_init(b_ffull + 8 * s, 1);
-            mbar_init(b_fempty + 8 * s, 1);
-        }
-        for (u32 s = 0; s < 2; s++) {
+            mbar_init(b_afull + 8 * s, 1);   // the loader's expect_tx; the bulk copy completes the bytes
+            mbar_init(b_xfull + 8 * s, 1);   // the slot's converter
+            mbar_init(b_sempty + 8 * s, 1);  // tcgen05.commit after the slot's MMAs
             mbar_init(b_tfull + 8 * s, 1);
             mbar_init(b_tempty + 8 * s, kEpiWarps);
         }
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(
                          (const void*)tmem_slot)),
-                     "r"(2 * BUFC));
+                     "r"(NBUF * BUFC));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_async_smem();
@@ -288,37 +289,36 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     tc_fence_after();
     const u32 tmem = *tmem_slot;
 
-
     if (warp == kLoadWarp) {
         // ================================================================ loader (lane 0)
         if (lane == 0) {
             UnitIter it(blockIdx.x, gridDim.x, nJ, G.n_ct, G.KB, 0);
             u32 u = 0;
             for (; u < total_units; u++, it.next(1)) {
-                const u32 s = u % G.NC, bar = b_rfull + 8 * s;
-                if (!mbar_wait(b_rempty + 8 * s, ((u / G.NC) & 1) ^ 1, abort)) break;
-                const u32 co0 = it.ct * 128, R = min(128u, L.Co - co0);
-                mbar_expect_tx(bar, R * 128);
-                bulk_g2s(smem_u32(sm + G.off_ra + s * G.raz), Ptc + ((u64)(it.J * G.KB + it.kb) * L.Co + co0) * 16,
-                         R * 128, bar);
+                const u32 s = u % G.NC, bar = b_afull + 8 * s;
+                if (!mbar_wait(b_sempty + 8 * s, ((u / G.NC) & 1) ^ 1, abort)) break;
+                const u32 rp = tile_rows8(L.Co, it.ct), bytes = 256 * rp;
+                mbar_expect_tx(bar, bytes);
+                bulk_g2s(smem_u32(sm + G.off_slot + s * G.ssz),
+                         Ptc + ((u64)(it.J * G.KB + it.kb) * G.co_pad + it.ct * 128) * 256, bytes, bar);
             }
             if (u < total_units) {
                 *abort = 1;
                 atomicExch(err, 1u);
             }
             // copies still in flight land before the CTA may exit (the last NC units at most)
-            for (u32 v = u > G.NC ? u - G.NC : 0; v < u; v++) mbar_drain(b_rfull + 8 * (v % G.NC), (v / G.NC) & 1);
+            for (u32 v = u > G.NC ? u - G.NC : 0; v < u; v++) mbar_drain(b_afull + 8 * (v % G.NC), (v / G.NC) & 1);
         }
         __syncwarp();
     } else if (warp >= kConvWarp0) {
-        // ================================================================ converters
-        const u32 cw = warp - kConvWarp0, s = cw, fs = cw;  // this converter's own slots
+        // ================================================================ converters (input words)
+        const u32 cw = warp - kConvWarp0, s = cw;  // this converter's own slot
         if (cw < G.NC && cw < total_units) {
             // input words of a unit, staged by this warp's lanes with cp.async:
             // [16][NB] ciphertext words, then [16][NB/2] A1 and [16][NB/2] A2 words of
             // the c1 columns; double-buffered so the next unit's copies fly while
             // this one is converted
-            u64* xbuf = reinterpret_cast<u64*>(sm + G.off_rx + cw * G.rxz);
+            u64* xbuf = reinterpret_cast<u64*>(sm + G.off_slot + s * G.ssz + G.az + 256 * NB);
             auto stage_x = [&](const UnitIter& t, u64* xr) {
                 const u32 h = t.J >> P.logn, j = t.J & (P.n - 1), bb0 = t.gbg * G.gbt;
 #pragma unroll 2
@@ -351,49 +351,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     stage_x(nx, xbuf + (par ^ 1) * 32 * NB);
                 else
                     asm volatile("cp.async.commit_group;" ::: "memory");
-                bool ok = mbar_wait(b_rfull + 8 * s, (u / G.NC) & 1, abort);
-                ok = ok && mbar_wait(b_fempty + 8 * fs, ((u / G.NC) & 1) ^ 1, abort);
-                if (!__all_sync(0xffffffffu, ok)) {
+                if (!__all_sync(0xffffffffu, mbar_wait(b_sempty + 8 * s, ((u / G.NC) & 1) ^ 1, abort))) {
                     *abort = 1;
                     atomicExch(err, 4u);
                     break;
                 }
                 asm volatile("cp.async.wait_group 1;" ::: "memory");  // this unit's input words
                 __syncwarp();
-                const u32 R = min(128u, L.Co - it.ct * 128);
-                unsigned char* fA = sm + G.off_f16 + fs * G.fsz;
-                unsigned char* fX = fA + 32768;
-                const uint4* ra = reinterpret_cast<const uint4*>(sm + G.off_ra + s * G.raz);  // [4][2R] x 16 B
+                unsigned char* fX = sm + G.off_slot + s * G.ssz + G.az;
                 const u64* xr = xbuf + par * 32 * NB;
-                // filter task t = (co, k8): words k8*8 .. k8*8+7 of row co, stored as 4
-                // chunks of 2 words at stride 2R chunks (conflict-free reads); two tasks
-                // per round for instruction-level parallelism
-                for (u32 t0 = lane; t0 < 2 * R; t0 += 64) {
-                    u64 w[2][8];
-                    uint4 row[2][8];
-#pragma unroll
-                    for (int q = 0; q < 2; q++) {
-                        const u32 t = t0 + 32 * q < 2 * R ? t0 + 32 * q : t0;
-#pragma unroll
-                        for (int i = 0; i < 4; i++) {
-                            const uint4 v = ra[i * 2 * R + t];
-                            w[q][2 * i] = ((u64)v.y << 32) | v.x;
-                            w[q][2 * i + 1] = ((u64)v.w << 32) | v.z;
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < 2; q++) digit_rows(w[q], row[q]);
-#pragma unroll
-                    for (int q = 0; q < 2; q++) {
-                        const u32 t = t0 + 32 * q;
-                        if (t >= 2 * R) continue;
-                        const u32 co = t >> 1, k8 = t & 1;
-                        const u32 off = (co >> 3) * 256 + k8 * 128 + (co & 7) * 16;
-#pragma unroll
-                        for (int a = 0; a < 8; a++) *reinterpret_cast<uint4*>(fA + a * 4096 + off) = row[q][a];
-                    }
-                }
-                // input task (col, k8): ciphertexts k8*8 .. k8*8+7; c1 gets the addends mod q
+                // task (col, k8): ciphertexts k8*8 .. k8*8+7 of column col; c1 gets the addends mod q
                 for (u32 t = lane; t < 2 * NB; t += 32) {
                     u64 w[8];
                     uint4 row[8];
@@ -415,10 +382,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 }
                 fence_async_smem();
                 __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(b_rempty + 8 * s);
-                    mbar_arrive(b_ffull + 8 * fs);
-                }
+                if (lane == 0) mbar_arrive(b_xfull + 8 * s);
                 it = nx;
             }
             asm volatile("cp.async.wait_all;" ::: "memory");
@@ -428,33 +392,33 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         if (lane == 0) {
             const u32 idesc = idesc_f16(128, 8 * NB);
             const u64 zdesc = sdesc(smem_u32(zero_blk), 128, 256);
+            UnitIter it(blockIdx.x, gridDim.x, nJ, G.n_ct, G.KB, 0);
             u32 u = 0;
             bool ok = true;
             for (u32 li = 0; li < my_items && ok; li++) {
-                const u32 b = li & 1;
-                if (!mbar_wait(b_tempty + 8 * b, ((li >> 1) & 1) ^ 1, abort)) {
+                const u32 b = li % NBUF;
+                if (!mbar_wait(b_tempty + 8 * b, ((li / NBUF) & 1) ^ 1, abort)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const u32 dbuf = tmem + b * BUFC;
-                for (u32 kb = 0; kb < G.KB; kb++, u++) {
-                    const u32 fs = u % G.NC;
-                    if (!mbar_wait(b_ffull + 8 * fs, (u / G.NC) & 1, abort)) {
+                for (u32 kb = 0; kb < G.KB; kb++, u++, it.next(1)) {
+                    const u32 s = u % G.NC, par = (u / G.NC) & 1;
+                    if (!mbar_wait(b_afull + 8 * s, par, abort) || !mbar_wait(b_xfull + 8 * s, par, abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const u32 fA = smem_u32(sm + G.off_f16 + fs * G.fsz);
-                    const u64 xdesc = sdesc(fA + 32768, 8 * NB * 16, 128);
+                    const u32 fA = smem_u32(sm + G.off_slot + s * G.ssz), ablk = 32 * tile_rows8(L.Co, it.ct);
+                    const u64 xdesc = sdesc(fA + G.az, 8 * NB * 16, 128);
 #pragma unroll
                     for (u32 a = 0; a < 8; a++) {
-                        const u32 set = a % S, rel = a - set;  // plane a: set a mod S, window shifted by rel blocks
-                        const u32 d = dbuf + set * SETC + rel * NB;
-                        mma_f16(d, sdesc(fA + a * 4096, 128, 256), xdesc, idesc, (kb != 0 || rel != 0) ? 1u : 0u);
-                        if (S < 8 && kb == 0 && rel == 0) mma_f16(dbuf + set * SETC + 8 * NB, zdesc, xdesc, idesc, 0u);
+                        // digit plane a of the filter accumulates into the window shifted by a blocks
+                        mma_f16(dbuf + a * NB, sdesc(fA + a * ablk, 128, 256), xdesc, idesc, (kb | a) ? 1u : 0u);
+                        if (kb == 0 && a == 0) mma_f16(dbuf + 8 * NB, zdesc, xdesc, idesc, 0u);
                     }
-                    mma_commit(b_fempty + 8 * fs);
+                    mma_commit(b_sempty + 8 * s);
                 }
                 if (ok) mma_commit(b_tfull + 8 * b);
             }
@@ -472,68 +436,72 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const u32 quarter = warp & 3, hc = warp >> 2;
         const u32 r = quarter * 32 + lane;
         const u32 lane_addr = (quarter * 32) << 16;
-        for (u32 li = 0; li < my_items; li++) {
-            const u32 b = li & 1;
-            const u32 item = blockIdx.x + li * gridDim.x;
-            const u32 J = item % nJ, rest = item / nJ, ct = rest % G.n_ct, gbg = rest / G.n_ct;
-            const u32 h = J >> P.logn, j = J & (P.n - 1);
-            const u32 co = ct * 128 + r;
-            const u32 col0 = hc * NBH;
+        const u32 col0 = hc * NBH;
+        // diagonals are read as biased integers B = D + 0x4B400000 (positive, below 2^31):
+        // for T <= 32 every |D| < 2^22 and the bits of D + 1.5 * 2^23 (one fp32 add) are B;
+        // otherwise B = rint(D) + 0x4B400000.  The bias of all 15 diagonals is removed once.
+        const bool magic = L.T <= 32;
+        unsigned __int128 bias = 0;
+#pragma unroll
+        for (int k = 0; k < 15; k++) bias += (unsigned __int128)0x4B400000u << (8 * k);
+        const u64 out_bb = (u64)L.Co * L.beta * 2 * P.n;  // output stride of one image group
+        const u64 msk_bb = (u64)L.Co * L.beta * P.n;      // mask stride of one image group
+        UnitIter it(blockIdx.x, gridDim.x, nJ, G.n_ct, G.KB, 0);
+        for (u32 li = 0; li < my_items; li++, it.next(G.KB)) {
+            const u32 b = li % NBUF;
+            const u32 h = it.J >> P.logn, j = it.J & (P.n - 1);
+            const u32 co = it.ct * 128 + r, bb0 = it.gbg * G.gbt;
+            const u64 vbase = ((u64)bb0 * L.Co + co) * L.beta + h;
+            const u64 obase = vbase * 2 * P.n + j, mbase = vbase * P.n + j;
             // the HomShare mask words of this thread's c1 outputs, fetched while the MMAs run
             u64 mk[NBH];
 #pragma unroll
             for (int i = 0; i < NBH; i++) {
-                const u32 col = col0 + i, bb = gbg * G.gbt + (col >> 1);
+                const u32 col = col0 + i, bb = bb0 + (col >> 1);
                 mk[i] = 0;
-                if ((col & 1) && Mhat && co < L.Co && bb < L.GB)
-                    mk[i] = __ldg(Mhat + (((u64)bb * L.Co + co) * L.beta + h) * P.n + j);
+                if ((col & 1) && Mhat && co < L.Co && bb < L.GB) mk[i] = __ldg(Mhat + mbase + (u64)(col >> 1) * msk_bb);
             }
-            if (!__all_sync(0xffffffffu, mbar_wait(b_tfull + 8 * b, (li >> 1) & 1, abort))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(b_tfull + 8 * b, (li / NBUF) & 1, abort))) {
                 *abort = 1;
                 atomicExch(err, 3u);
                 break;
             }
             tc_fence_after();
+            if (quarter * 32 >= L.Co - it.ct * 128) {
+                // this warp's lanes hold only the padding rows of a narrower tile
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(b_tempty + 8 * b);
+                continue;
+            }
             const u32 base = tmem + lane_addr + b * BUFC + col0;
-            unsigned __int128 V[NBH];  // the sum mod 2^128: exact, since it lies in [0, 2^127)
+            unsigned __int128 V[NBH];  // the biased sum mod 2^128
 #pragma unroll
             for (int i = 0; i < NBH; i++) V[i] = 0;
 #pragma unroll
             for (u32 m = 0; m < 4; m++) {
-                // diagonals 4m .. 4m+3, each the sum of its sets
-                u32 d[4][S][NBH];
+                u32 d[4][NBH];
 #pragma unroll
                 for (u32 rr = 0; rr < 4; rr++)
-#pragma unroll
-                    for (u32 st = 0; st < S; st++) {
-                        const u32 kap = 4 * m + rr;
-                        if (kap < 15 && kap >= st && kap - st < 16 - S)
-                            tmem_ld<NBH>(base + st * SETC + (kap - st) * NB, d[rr][st]);
-                    }
+                    if (4 * m + rr < 15) tmem_ld<NBH>(base + (4 * m + rr) * NB, d[rr]);
                 tmem_wait_ld();
 #pragma unroll
                 for (u32 rr = 0; rr < 4; rr++)
 #pragma unroll
-                    for (u32 st = 0; st < S; st++)
-#pragma unroll
-                        for (int i = 0; i < NBH; i++) {
-                            const u32 kap = 4 * m + rr;
-                            if (kap < 15 && kap >= st && kap - st < 16 - S) asm volatile("" : "+r"(d[rr][st][i]));
-                        }
+                    for (int i = 0; i < NBH; i++)
+                        if (4 * m + rr < 15) asm volatile("" : "+r"(d[rr][i]));
 #pragma unroll
                 for (int i = 0; i < NBH; i++) {
-                    long long cm = 0;
+                    u64 cm = 0;  // sum of B 2^(8 rr): below 2^56
 #pragma unroll
                     for (u32 rr = 0; rr < 4; rr++) {
-                        const u32 kap = 4 * m + rr;
-                        if (kap >= 15) continue;
-                        float f = 0.f;  // exact: every partial sum is an integer below 2^24
-#pragma unroll
-                        for (u32 st = 0; st < S; st++)
-                            if (kap >= st && kap - st < 16 - S) f += __uint_as_float(d[rr][st][i]);
-                        cm += (long long)__float2int_rn(f) * (1ll << (8 * rr));
+                        if (4 * m + rr >= 15) continue;
+                        const float f = __uint_as_float(d[rr][i]);
+                        const u32 bv = magic ? __float_as_uint(f + 12582912.0f)
+                                             : (u32)(__float2int_rn(f) + 0x4B400000);
+                        cm += (u64)bv << (8 * rr);
                     }
-                    V[i] += (unsigned __int128)(__int128)cm << (32 * m);
+                    V[i] += (unsigned __int128)cm << (32 * m);
                 }
             }
             tc_fence_before();
@@ -542,12 +510,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             if (co < L.Co) {
 #pragma unroll
                 for (int i = 0; i < NBH; i++) {
-                    const u32 col = col0 + i, bb = gbg * G.gbt + (col >> 1), c = col & 1;
-                    if (bb >= L.GB) continue;
-                    const unsigned __int128 v = V[i];
+                    const u32 col = col0 + i, c = col & 1;
+                    if (bb0 + (col >> 1) >= L.GB) continue;
+                    const unsigned __int128 v = V[i] - bias;  // the exact sum, in [0, 2^127)
                     u64 res = reduce128((u64)(v >> 64), (u64)v, P);
                     if (c == 1) res = submod_q(res, mk[i], P.q);
-                    ct_out[((((u64)bb * L.Co + co) * L.beta + h) * 2 + c) * P.n + j] = res;
+                    ct_out[obase + (u64)(col >> 1) * out_bb + c * P.n] = res;
                 }
             }
         }
@@ -556,22 +524,22 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     __syncthreads();
     if (warp == kMmaWarp) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BUFC));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NBUF * BUFC));
     }
 }
 
 // Phat [Co][T][beta][n] -> Ptc: per (J, 16-ciphertext block kb, 128-channel
-// tile of R rows) one contiguous unit of R x 16 words, biased by 0x80..80
-// (ciphertexts past T hold the bias alone).  Within a unit, word (co, k) with
-// k = 8 k8 + 2 i + e sits in 16-byte chunk i * 2R + (2 co + k8), half e, so
-// that a converter lane reading its four chunks of task (co, k8) hits
-// consecutive chunks across the warp.
-__global__ void filter_tc_kernel(const DevParams P, const DevLayer L, u32 KB, const u64* __restrict__ Phat,
-                                 u64* __restrict__ Ptc) {
+// tile of R rows, R rounded up to rp, a multiple of 8) one contiguous unit of
+// 256 rp bytes holding the eight fp16 digit planes of the filter words in the
+// canonical no-swizzle K-major layout of a tcgen05 A operand: plane a at
+// 32 rp a bytes, row r / k in the plane at (r / 8) 256 + (k / 8) 128 +
+// (r mod 8) 16 + (k mod 8) 2.  Ciphertexts past T and rows past R are zero.
+__global__ void filter_tc_kernel(const DevParams P, const DevLayer L, u32 KB, u32 co_pad,
+                                 const u64* __restrict__ Phat, unsigned char* __restrict__ Ptc) {
     __shared__ u64 tile[16][65];
     const u32 nJ = L.beta * P.n;
     const u32 J0 = blockIdx.x * 64, kb = blockIdx.y, co = blockIdx.z;
-    const u32 co0 = co & ~127u, R = min(128u, L.Co - co0), cl = co - co0;
+    const u32 ct = co / 128, rl = co % 128, rp = tile_rows8(L.Co, ct);
     for (u32 e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
         const u32 kk = e / 64, jj = e % 64, k = kb * 16 + kk, J = J0 + jj;
         u64 v = kDigitBias;
@@ -579,12 +547,18 @@ __global__ void filter_tc_kernel(const DevParams P, const DevLayer L, u32 KB, co
         tile[kk][jj] = v;
     }
     __syncthreads();
-    for (u32 e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
-        const u32 jj = e / 16, kk = e % 16, J = J0 + jj;
-        const u32 k8 = kk >> 3, i = (kk >> 1) & 3, half = kk & 1;
-        if (J < nJ)
-            Ptc[((u64)J * KB + kb) * L.Co * 16 + (u64)co0 * 16 + ((u64)i * 2 * R + 2 * cl + k8) * 2 + half] =
-                tile[kk][jj];
+    for (u32 e = threadIdx.x; e < 2 * 64; e += blockDim.x) {
+        const u32 jj = e / 2, k8 = e % 2, J = J0 + jj;
+        if (J >= nJ) continue;
+        u64 w[8];
+        uint4 row[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) w[i] = tile[k8 * 8 + i][jj];
+        digit_rows(w, row);
+        unsigned char* unit = Ptc + ((u64)(J * KB + kb) * co_pad + ct * 128) * 256;
+        const u32 off = (rl >> 3) * 256 + k8 * 128 + (rl & 7) * 16;
+#pragma unroll
+        for (int a = 0; a < 8; a++) *reinterpret_cast<uint4*>(unit + a * 32 * rp + off) = row[a];
     }
 }
 
@@ -602,21 +576,20 @@ static bool tc_geom(u32 n, const DevLayer& L, TcGeom& G, size_t& smem) {
     G.KB = (L.T + 15) / 16;
     G.n_ct = (L.Co + 127) / 128;
     G.n_gbg = (L.GB + gbt - 1) / gbt;
+    G.co_pad = 128 * (G.n_ct - 1) + tile_rows8(L.Co, G.n_ct - 1);
     const u64 items = (u64)L.beta * n * G.n_ct * G.n_gbg;
     if (items > 0x7FFFFFFFull) return false;
     G.n_items = (u32)items;
-    const u32 rmax = L.Co < 128 ? L.Co : 128;
-    G.raz = rmax * 128;
-    G.rxz = 2 * 32 * G.NB * 8;  // a converter's two input-word buffers
-    G.fsz = 32768 + 256 * G.NB;
-    G.off_f16 = 1024 + 4096;
+    const u32 rp = tile_rows8(L.Co, 0);  // the widest tile
+    // the A operand region: the digit planes, and room for the 128-row reads of the last plane
+    G.az = 256 * rp > 7 * 32 * rp + 4096 ? 256 * rp : 7 * 32 * rp + 4096;
+    G.ssz = G.az + 256 * G.NB + 2 * 32 * G.NB * 8;  // A, the input digit planes, two input-word buffers
+    G.off_slot = 1024 + 4096;
     const size_t budget = 227 * 1024;
-    const size_t nc = (budget - G.off_f16) / ((size_t)G.fsz + G.raz + G.rxz);  // one slot of each per converter
+    size_t nc = (budget - G.off_slot) / G.ssz;
     if (nc < 2) return false;
     G.NC = (u32)(nc > kMaxConv ? kMaxConv : nc);
-    G.off_ra = G.off_f16 + G.NC * G.fsz;
-    G.off_rx = G.off_ra + G.NC * G.raz;
-    smem = G.off_rx + G.NC * G.rxz;
+    smem = G.off_slot + (size_t)G.NC * G.ssz;
     return smem <= budget;
 }
 
@@ -626,12 +599,20 @@ bool homconv_tc_supported(u32 n, const DevLayer& L) {
     return tc_geom(n, L, G, smem);
 }
 
-u64 filter_tc_words(u32 n, const DevLayer& L) { return (u64)L.beta * n * ((L.T + 15) / 16) * L.Co * 16; }
+// Words (u64) of the tensor-core filter layout: 256 bytes per row per
+// (J, ciphertext block), rows padded per tile to a multiple of 8.
+u64 filter_tc_words(u32 n, const DevLayer& L) {
+    const u32 n_ct = (L.Co + 127) / 128, co_pad = 128 * (n_ct - 1) + tile_rows8(L.Co, n_ct - 1);
+    return (u64)L.beta * n * ((L.T + 15) / 16) * co_pad * 32;
+}
 
 cudaError_t launch_filter_tc(const DevParams& P, const DevLayer& L, const u64* Phat, u64* Ptc, cudaStream_t s) {
     const u32 nJ = L.beta * P.n, KB = (L.T + 15) / 16;
+    const u32 n_ct = (L.Co + 127) / 128, co_pad = 128 * (n_ct - 1) + tile_rows8(L.Co, n_ct - 1);
+    cudaError_t e = cudaMemsetAsync(Ptc, 0, filter_tc_words(P.n, L) * 8, s);  // padding rows stay zero
+    if (e != cudaSuccess) return e;
     dim3 grid((nJ + 63) / 64, KB, L.Co);
-    filter_tc_kernel<<<grid, 256, 0, s>>>(P, L, KB, Phat, Ptc);
+    filter_tc_kernel<<<grid, 128, 0, s>>>(P, L, KB, co_pad, Phat, reinterpret_cast<unsigned char*>(Ptc));
     return cudaGetLastError();
 }
 
@@ -658,7 +639,9 @@ static cudaError_t launch_tc(const DevParams& P, const DevLayer& L, const TcGeom
         if (e != cudaSuccess) return e;
     }
     const u32 grid = G.n_items < (u32)sms ? G.n_items : (u32)sms;
-    homconv_tc_kernel<NBH><<<grid, kThreadsTC, smem, s>>>(P, L, G, ct_in, A1, A2, Ptc, Mhat, ct_out, errp);
+    homconv_tc_kernel<NBH><<<grid, kThreadsTC, smem, s>>>(P, L, G, ct_in, A1, A2,
+                                                         reinterpret_cast<const unsigned char*>(Ptc), Mhat, ct_out,
+                                                         errp);
     return cudaGetLastError();
 }
 

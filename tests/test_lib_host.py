@@ -107,11 +107,14 @@ def test_flood_bits_max_matches_oracle_bound(F, n, p, T):
     (256, 65537, (5, 34, 130, 8, 8, 1, 1)),
 ])
 def test_filter_tc_words(F, n, p, shape):
-    """Size of the tensor-core filter layout: [beta n][ceil(T/16)][Co][16]."""
+    """Size of the tensor-core filter layout: per evaluation index and block of
+    16 input ciphertexts, 8 fp16 digit planes of 16 values for every row, the
+    rows of the last 128-channel tile rounded up to a multiple of 8."""
     B, Ci, Co, H, W, g_c, g_b = shape
     L = F.LayerSpec(B, Ci, Co, H, W, g_c, g_b)
     ref = O.layer(O.params(n, p), B, Ci, Co, H, W, g_c, g_b)
-    assert F.filter_tc_words(n, p, L) == ref.beta * n * (-(-ref.T // 16)) * Co * 16
+    co_pad = 128 * ((Co - 1) // 128) + -(-(Co - 128 * ((Co - 1) // 128)) // 8) * 8
+    assert F.filter_tc_words(n, p, L) * 8 == ref.beta * n * (-(-ref.T // 16)) * co_pad * 8 * 16 * 2
 
 
 def test_filter_tc_rejects_large_T(F):
