@@ -402,6 +402,89 @@ def run_batched(F, flush, sleep_cycles, args):
     return out
 
 
+# HomConv shapes where the contraction is a dense product: the 16-image stack's
+# three layers and the binarized 64x64x128 layer at batch 8
+TENSOR_SHAPES = [("cfg2", 0), ("cfg2", 1), ("cfg2", 2), ("cfg4", 0)]
+
+
+def run_tensor_homconv(F, flush, args):
+    """HomConv + HomShare (+ HomRec addends) of the batched shapes on the
+    tensor cores (fdsc_homconv_tc, digit planes in fp16, exact fp32 sums)
+    against the CUDA-core kernel on the same words: each call recorded in a
+    CUDA graph, L2 flushed before every timed replay, median.  Bytes are those
+    the tensor-core kernel moves (its filter is fp16 digit planes, 16 bytes a
+    word); the tensor work counts the digit MMAs it issues."""
+    import torch
+
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    tpk = peaks.get("bf16_tflops") or 1900.0  # fp16 and bf16 MMAs run at the same rate
+    out = []
+
+    def median_us(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        s0 = torch.cuda.Stream()
+        s0.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s0):
+            with torch.cuda.graph(gr, stream=s0):
+                fn()
+        torch.cuda.current_stream().wait_stream(s0)
+        ts = []
+        for i in range(reps + 2):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            gr.replay()
+            b.record()
+            b.synchronize()
+            if i >= 2:
+                ts.append(a.elapsed_time(b) * 1e3)
+        return float(np.median(ts))
+
+    for cfg, li in TENSOR_SHAPES:
+        ls = FI.CONFIGS[cfg].layers[li]
+        info = F.params_query(ls.n, ls.p)
+        g_c, g_b = FI.default_pack(ls, info.S)
+        L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
+        P = F.Params(ls.n, ls.p, max_T=256)
+        lay = F.layout(P, L)
+        g = torch.Generator(device="cuda").manual_seed(FI.SEED_BASE + li)
+        rnd = lambda k: torch.randint(0, info.q, (k,), dtype=torch.int64, device="cuda", generator=g)
+        ct, Ph, Mh = rnd(lay.ct_in_words), rnd(lay.filter_words), rnd(lay.mask_words)
+        A1, A2 = rnd(lay.n_in * ls.n), rnd(lay.n_in * ls.n)
+        Ptc = F.filter_tc(P, L, Ph)
+        o1 = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
+        o2 = torch.empty_like(o1)
+        reps = 9 if lay.filter_words < (64 << 20) else 5
+        us_tc = median_us(lambda: F.homconv_tc(P, L, ct, A1, A2, Ptc, Mh, out=o1), reps)
+        us_cc = median_us(lambda: F.homconv_sum(P, L, ct, A1, A2, Ph, Mh, out=o2), reps)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(o1, o2))
+        status = F.homconv_tc_status()
+        macs = 2 * ls.Co * lay.T * lay.beta * ls.n * lay.GB
+        gbt = 8 if lay.GB >= 8 else (4 if lay.GB >= 4 else (2 if lay.GB >= 2 else 1))
+        nb = 2 * gbt
+        items = lay.beta * ls.n * (-(-ls.Co // 128)) * (-(-lay.GB // gbt))
+        mmas = items * (8 * (-(-lay.T // 16)) + 1)
+        flops = mmas * 2 * 128 * 8 * nb * 16
+        byts = 8 * (Ptc.numel() + lay.ct_in_words + 2 * lay.n_in * ls.n + lay.ct_out_words + lay.mask_words)
+        out.append({"layer": "%s %dx%dx%d->%d, batch %d, n=%d, p=%d" % (cfg, ls.H, ls.W, ls.Ci, ls.Co, ls.B, ls.n,
+                                                                       ls.p),
+                    "T": lay.T, "image_groups": lay.GB, "tensor_us": us_tc, "cuda_core_us": us_cc,
+                    "speedup": us_cc / us_tc, "words_identical": same, "status": status,
+                    "mod_q_macs_per_s": macs / (us_tc * 1e-6), "bytes": byts,
+                    "GB_per_s": byts / (us_tc * 1e-6) / 1e9, "hbm_frac": byts / (us_tc * 1e-6) / 1e9 / hbm,
+                    "digit_mma_tflops": flops / (us_tc * 1e-6) / 1e12,
+                    "tensor_frac": flops / (us_tc * 1e-6) / 1e12 / tpk})
+        del ct, Ph, Mh, A1, A2, Ptc, o1, o2
+        torch.cuda.empty_cache()
+        P.close()
+    return {"kernel": "homconv_tc_kernel (fdsc_homconv_tc)", "peaks": {"hbm_GB_per_s": hbm, "fp16_tflops": tpk},
+            "l2": "flushed before every timed replay", "shapes": out}
+
+
 # the appendix network (MiniONN's CIFAR-10 network, Fig. 13 there): its six
 # convolution layers, (Ci, Co, H, filter, 2x2 pooling after); the
 # fully-connected layer and the activations are not part of the path
@@ -588,8 +671,10 @@ def ntt2d_sweep(F, P, ls, back_to_back, args):
 def run_kernel_only(args):
     """A few launches of one part of the path, for profiler captures (no
     timing, no JSON line): `homconv` (HomConv + HomShare of the 32x32x64
-    layer on seeded random words), `ntt2d` (forward NTT2D of --planes 32x32
-    planes) or `step` (the fused online step of that layer, eager)."""
+    layer on seeded random words), `homconv_tc` (the tensor-core HomConv of
+    the 16x16x128->128 layer at 16 images), `ntt2d` (forward NTT2D of
+    --planes 32x32 planes) or `step` (the fused online step of that layer,
+    eager)."""
     import torch
 
     torch.cuda.set_device(0)
@@ -609,7 +694,24 @@ def run_kernel_only(args):
     g = torch.Generator(device="cuda")
     g.manual_seed(FI.SEED_BASE)
     rnd = lambda hi, k: torch.randint(0, hi, (k,), dtype=torch.int64, device="cuda", generator=g)
-    if args.kernel_only == "homconv":
+    if args.kernel_only == "homconv_tc":
+        # the tensor-core HomConv on the 16x16x128->128 layer of the 16-image stack
+        ls = FI.CONFIGS["cfg2"].layers[1]
+        info = F.params_query(ls.n, ls.p)
+        g_c, g_b = FI.default_pack(ls, info.S)
+        L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
+        P.close()
+        P = F.Params(ls.n, ls.p, max_T=64)
+        lay = F.layout(P, L)
+        ct, Ph, Mh = rnd(info.q, lay.ct_in_words), rnd(info.q, lay.filter_words), rnd(info.q, lay.mask_words)
+        A1, A2 = rnd(info.q, lay.n_in * ls.n), rnd(info.q, lay.n_in * ls.n)
+        Ptc = F.filter_tc(P, L, Ph)
+        out = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
+        for _ in range(args.steps):
+            F.homconv_tc(P, L, ct, A1, A2, Ptc, Mh, out=out)
+        torch.cuda.synchronize()
+        assert F.homconv_tc_status() == 0
+    elif args.kernel_only == "homconv":
         ct, Ph, Mh = rnd(info.q, lay.ct_in_words), rnd(info.q, lay.filter_words), rnd(info.q, lay.mask_words)
         A1, A2 = rnd(info.q, lay.n_in * ls.n), rnd(info.q, lay.n_in * ls.n)
         out = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
@@ -818,6 +920,7 @@ def run_gpu(args, rank, local_rank, world):
                              xB_h[0], args.e2e_requests)
     flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.int32, device="cuda")
     batched = None if args.skip_batched else run_batched(F, flush, sleep_cycles, args)
+    tensor = None if args.skip_batched else run_tensor_homconv(F, flush, args)
     chain = None if args.skip_batched else run_chain(F, flush, sleep_cycles, args)
     serving = None if args.skip_serving else run_serving(F, args)
 
@@ -893,6 +996,7 @@ def run_gpu(args, rank, local_rank, world):
                 "path": "fdsc_server_submit/wait (C ABI) with host buffers, closed loop of single-image requests; "
                         "copies in and out inside the timed region; host wall clock"},
         "batched": batched,
+        "homconv_tensor": tensor,
         "chain": chain,
         "serving": serving,
         "ntt2d_sweep": sweep,
@@ -922,7 +1026,7 @@ def main():
     ap.add_argument("--serve-keys", type=int, default=64)
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
-    ap.add_argument("--kernel-only", choices=["homconv", "ntt2d", "step"],
+    ap.add_argument("--kernel-only", choices=["homconv", "homconv_tc", "ntt2d", "step"],
                     help="only run --steps launches of one part of the path (for profiler captures)")
     ap.add_argument("--planes", type=int, default=65536, help="planes for --kernel-only ntt2d")
     args = ap.parse_args()
