@@ -48,6 +48,8 @@
 // error, stops, lets its copies and MMAs finish, frees its TMEM and returns.
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "modarith.cuh"
 
 namespace {
@@ -620,24 +622,23 @@ template <int NBH>
 static cudaError_t launch_tc(const DevParams& P, const DevLayer& L, const TcGeom& G, size_t smem, const u64* ct_in,
                              const u64* A1, const u64* A2, const u64* Ptc, const u64* Mhat, u64* ct_out,
                              cudaStream_t s) {
+    // once per instantiation (thread-safe: the server's worker launches too): the
+    // SM count, the shared-memory opt-in at the largest size any layer uses, and
+    // the address of the error word
+    static std::once_flag once;
+    static cudaError_t init = cudaSuccess;
     static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    static size_t smem_set = 0;
-    cudaError_t e = cudaSuccess;
-    if (smem > smem_set) {
-        e = cudaFuncSetAttribute(homconv_tc_kernel<NBH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_set = smem;
-    }
     static u32* errp = nullptr;
-    if (!errp) {
-        e = cudaGetSymbolAddress((void**)&errp, g_tc_err);
-        if (e != cudaSuccess) return e;
-    }
+    std::call_once(once, [] {
+        int dev = 0;
+        init = cudaGetDevice(&dev);
+        if (init == cudaSuccess) init = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (init == cudaSuccess)
+            init = cudaFuncSetAttribute(homconv_tc_kernel<NBH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        227 * 1024);
+        if (init == cudaSuccess) init = cudaGetSymbolAddress((void**)&errp, g_tc_err);
+    });
+    if (init != cudaSuccess) return init;
     const u32 grid = G.n_items < (u32)sms ? G.n_items : (u32)sms;
     homconv_tc_kernel<NBH><<<grid, kThreadsTC, smem, s>>>(P, L, G, ct_in, A1, A2,
                                                          reinterpret_cast<const unsigned char*>(Ptc), Mhat, ct_out,

@@ -448,3 +448,36 @@ def test_homconv_tc_full_size_binarized_layer(F):
             s = (s - int(Mhn[bb, co, h, j])) % q
         assert int(outn[bb, co, h, c, j]) == s, (bb, co, h, c, j)
     P.close()
+
+
+def test_homconv_tc_argument_errors(F):
+    """T > 128 is refused (a weight class could reach 2^24), as are outputs
+    overlapping an input and misaligned buffers; nothing is launched."""
+    P = F.Params(256, 65537, max_T=256)
+    L = F.LayerSpec(1, 129, 4, 8, 8, 1, 1)  # T = 129
+    lay = F.layout(P, L)
+    ct = torch.zeros(lay.ct_in_words, dtype=torch.int64, device="cuda")
+    Ph = torch.zeros(lay.filter_words, dtype=torch.int64, device="cuda")
+    with pytest.raises(F.FdscError) as e:
+        F._call("fdsc_filter_tc", P.handle, F.C.byref(L.c()), Ph.data_ptr(), Ph.data_ptr() + 8 * lay.filter_words, 0)
+    assert e.value.code == -5
+    with pytest.raises(F.FdscError) as e:
+        F._call("fdsc_homconv_tc", P.handle, F.C.byref(L.c()), ct.data_ptr(), None, None, Ph.data_ptr(), None,
+                ct.data_ptr() + 8 * lay.ct_in_words, 0)
+    assert e.value.code == -5
+    L2 = F.LayerSpec(1, 32, 4, 8, 8, 1, 1)
+    lay2 = F.layout(P, L2)
+    Ptc = torch.zeros(F.filter_tc_words(256, 65537, L2), dtype=torch.int64, device="cuda")
+    big = torch.zeros(lay2.ct_in_words + lay2.ct_out_words, dtype=torch.int64, device="cuda")
+    with pytest.raises(F.FdscError) as e:  # output overlapping the input
+        F._call("fdsc_homconv_tc", P.handle, F.C.byref(L2.c()), big.data_ptr(), None, None, Ptc.data_ptr(), None,
+                big.data_ptr() + 8 * 16, 0)
+    assert e.value.code == -1
+    out = torch.zeros(lay2.ct_out_words + 2, dtype=torch.int64, device="cuda")
+    with pytest.raises(F.FdscError) as e:  # misaligned output
+        F._call("fdsc_homconv_tc", P.handle, F.C.byref(L2.c()), big.data_ptr(), None, None, Ptc.data_ptr(), None,
+                out.data_ptr() + 8, 0)
+    assert e.value.code == -1
+    torch.cuda.synchronize()
+    assert F.homconv_tc_status() == 0
+    P.close()
