@@ -19,33 +19,29 @@
 // lanes, K = 16 input ciphertexts per instruction): the B operand stacks the
 // eight digit planes of X along N (rows (b, col), N = 8 NB), and the MMA of
 // filter digit plane a accumulates into a TMEM column window shifted by a NB
-// blocks: column block kappa then receives exactly the products with
-// a + b = kappa.  The eight digit planes of A are spread over S independent
-// accumulator sets (S = 8 / (NB / 2): all of TMEM for two items in flight),
-// plane a in set a mod S, so consecutive MMAs never wait for each other's
-// accumulator; the epilogue adds the sets (exact in fp32, same bound).  In a
-// set holding several planes, one MMA with a zero A operand clears the upper
-// part of its window before the first accumulation.
+// columns: column block kappa then receives exactly the products with
+// a + b = kappa.  One MMA with a zero A operand clears the upper part of the
+// window before the first accumulation.  The filter arrives as fp16 digit
+// planes already in the A operand layout (fdsc_filter_tc, setup).
 //
 // Roles in a persistent CTA of 16 warps (one CTA per SM):
 //   warps 0-7   epilogue: TMEM -> diagonals -> 128-bit sum -> mod q -> HomShare
 //   warp 8      TMEM allocation; lane 0 issues the MMAs
-//   warp 9      loader: one bulk copy per unit for the filter digit words
-//               (lane 0)
-//   warps 10-15 converters: NC of them (as many as operand slots fit), each
-//               converting whole units into fp16 digit planes in the canonical
-//               no-swizzle K-major layout; a converter stages the input
-//               words (and the fused c1 addends) of its next unit with
-//               cp.async while it converts the current one.
-// Unit u goes to converter u mod NC and to that converter's own staging and
-// operand slots, so every slot is filled, converted and consumed in unit
-// order and no waiter can run two phases ahead of the mbarrier it polls
-// (a parity wait cannot tell phase k from phase k - 2).
+//   warp 9      loader: one bulk copy per unit of the filter digit planes into
+//               the unit's operand slot (lane 0)
+//   warps 10-15 converters of the input words, NC of them (as many as operand
+//               slots fit): each stages the ciphertext words (and the fused c1
+//               addends) of its next unit with cp.async while it converts the
+//               current one into fp16 digit planes.
+// Unit u uses operand slot u mod NC and converter u mod NC, so every slot is
+// filled, converted and consumed in unit order and no waiter can run two
+// phases ahead of the mbarrier it polls (a parity wait cannot tell phase k
+// from phase k - 2).
 // A unit is (item, 16 input ciphertexts); an item is (J, 128 output channels,
-// up to 8 image groups).  Staging and operand slots form mbarrier rings; two
-// TMEM accumulators let the MMAs of one item run while the epilogue drains
-// the previous one.  Every wait is bounded: on a timeout the CTA records an
-// error, stops, lets its copies and MMAs finish, frees its TMEM and returns.
+// up to 8 image groups).  Up to 8 TMEM accumulators let the MMAs of later
+// items run while the epilogue drains earlier ones.  Every wait is bounded: on
+// a timeout the CTA records an error, stops, lets its copies and MMAs finish,
+// frees its TMEM and returns.
 #include <cuda_fp16.h>
 
 #include <mutex>
