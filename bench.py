@@ -673,8 +673,9 @@ def run_kernel_only(args):
     timing, no JSON line): `homconv` (HomConv + HomShare of the 32x32x64
     layer on seeded random words), `homconv_tc` (the tensor-core HomConv of
     the 16x16x128->128 layer at 16 images), `ntt2d` (forward NTT2D of
-    --planes 32x32 planes) or `step` (the fused online step of that layer,
-    eager)."""
+    --planes 32x32 planes), `step` (the fused online step of that layer,
+    eager) or `plan` (the 16-image stack as one autotuned plan; under a
+    profiler the tuner's timings, and so its choices, can differ)."""
     import torch
 
     torch.cuda.set_device(0)
@@ -694,6 +695,33 @@ def run_kernel_only(args):
     g = torch.Generator(device="cuda")
     g.manual_seed(FI.SEED_BASE)
     rnd = lambda hi, k: torch.randint(0, hi, (k,), dtype=torch.int64, device="cuda", generator=g)
+    if args.kernel_only == "plan":
+        # the 16-image uneven stack as one autotuned plan, launched --steps times
+        P.close()
+        c2 = FI.CONFIGS["cfg2"]
+        params, specs = {}, []
+        dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
+        for li, ls2 in enumerate(c2.layers):
+            P2 = params.setdefault((ls2.n, ls2.p), F.Params(ls2.n, ls2.p, max_T=256))
+            xA, xB = FI.shares(ls2, c2.cid, li)
+            ks, es, ss = FI.seeds(c2.cid, li)
+            specs.append(dict(params=P2, w=dev(FI.weights(ls2, c2.cid, li), np.int8), t_hat=F.keygen(P2, ks),
+                              enc_seed=es, mask_seed=ss,
+                              layer=F.LayerSpec(ls2.B, ls2.Ci, ls2.Co, ls2.H, ls2.W, 0, 0), xA=dev(xA, np.int32),
+                              xB=dev(xB, np.int32),
+                              yA=torch.empty((ls2.B, ls2.Co, ls2.H, ls2.W), dtype=torch.int32, device="cuda"),
+                              yB=torch.empty((ls2.B, ls2.Co, ls2.H, ls2.W), dtype=torch.int32, device="cuda")))
+        plan = F.Plan(specs, tune=True)
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            plan.launch()
+        torch.cuda.synchronize()
+        print("tuned variants:", [plan.info(i).homconv_variant for i in range(len(specs))])
+        plan.close()
+        for P2 in params.values():
+            P2.close()
+        print("ran %d x plan" % args.steps)
+        return
     if args.kernel_only == "homconv_tc":
         # the tensor-core HomConv on the 16x16x128->128 layer of the 16-image stack
         ls = FI.CONFIGS["cfg2"].layers[1]
@@ -1026,7 +1054,7 @@ def main():
     ap.add_argument("--serve-keys", type=int, default=64)
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
-    ap.add_argument("--kernel-only", choices=["homconv", "homconv_tc", "ntt2d", "step"],
+    ap.add_argument("--kernel-only", choices=["homconv", "homconv_tc", "ntt2d", "step", "plan"],
                     help="only run --steps launches of one part of the path (for profiler captures)")
     ap.add_argument("--planes", type=int, default=65536, help="planes for --kernel-only ntt2d")
     args = ap.parse_args()
