@@ -200,10 +200,12 @@ def test_pool2x2_sum_matches_oracle(F):
     P.close()
 
 
-def test_chained_plan_of_a_network_matches_oracle(F):
+@pytest.mark.parametrize("tensor", [False, True])
+def test_chained_plan_of_a_network_matches_oracle(F, tensor):
     """The appendix network's pattern at reduced width: conv, sum pooling,
     conv, 1x1 conv, run as one chained plan (each layer reads the shares the
-    previous one wrote) and compared with the oracle run layer by layer."""
+    previous one wrote) and compared with the oracle run layer by layer;
+    tensor: every layer's HomConv on the tensor cores."""
     p, n = 65537, 1024
     P = F.Params(n, p, max_T=64)
     OP = O.params(n, p)
@@ -227,7 +229,9 @@ def test_chained_plan_of_a_network_matches_oracle(F):
         specs.append(d)
         ws.append(w)
         seeds.append((ks, es, ss))
-    plan = F.Plan(specs, chain=True)
+    plan = F.Plan(specs, chain=True, tensor=tensor)
+    if tensor:
+        assert [plan.info(i).homconv_variant for i in range(len(shapes))] == [7] * len(shapes)
     for _ in range(2):
         plan.launch()
         torch.cuda.synchronize()
