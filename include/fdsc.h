@@ -399,6 +399,9 @@ typedef struct {
     uint64_t peak_inflight_bytes;
     double mean_batch;
     double p50_us, p99_us, mean_us, max_us; /* submit-to-completion latency   */
+    uint64_t tensor_batches;    /* batches whose HomConv ran on the tensor cores
+                                   (batches of 4 or more requests, when the
+                                   layer admits fdsc_homconv_tc)               */
 } fdsc_server_stats;
 
 typedef struct fdsc_server fdsc_server;

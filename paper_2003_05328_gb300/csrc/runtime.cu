@@ -94,6 +94,9 @@ namespace {
 
 // HomConv variant number of the tensor-core kernel (homconv_tc.cu) in a plan.
 constexpr int kTensorVariant = 7;
+// Smallest server batch (images) whose HomConv runs on the tensor cores: from
+// 4 images on, the tensor-core kernel is the faster one on the served shapes.
+constexpr uint32_t kServerTensorMinImages = 4;
 
 // The HomConv of a layer with its chosen variant.
 cudaError_t plan_homconv(const DevParams& P, const PlanLayer& pl, const u64* A1, const u64* A2, cudaStream_t s) {
@@ -410,6 +413,7 @@ struct ServerType {
     DevLayer D1;
     fdsc_layout lay1;
     u64* Phat = nullptr;
+    u64* Ptc = nullptr;  // the filter in the tensor-core layout (when the layer admits that kernel)
     const uint64_t* keys;
     uint32_t nkeys;
     uint64_t bytes_per_request;
@@ -529,6 +533,7 @@ struct fdsc_server {
     std::map<uint64_t, double> done;  // ticket -> latency (us); -1 = failed
     std::vector<double> latencies;
     uint64_t next_ticket = 1, submitted = 0, completed = 0, batches = 0, batched_requests = 0;
+    std::atomic<uint64_t> tensor_batches{0};  // batches whose HomConv ran on the tensor cores
     uint64_t inflight = 0, peak_inflight = 0;
     int error = FDSC_OK;
     bool started = false, stop = false;
@@ -580,7 +585,12 @@ int launch_batch(fdsc_server* S, Lane& ln) {
     RT_TRY(launch_constants(P, D, ln.keys, n, 0, ln.seeds, ln.ct, s));
     RT_TRY(launch_share(P, D, ln.xA, ln.A, false, s));
     RT_TRY(launch_share(P, D, ln.xB, ln.R, false, s));
-    RT_TRY(launch_homconv_v(P, D, ln.ct, ln.A, ln.R, t.Phat, ln.M, ln.ct_out, t.variant, s));
+    if (t.Ptc && D.GB >= kServerTensorMinImages) {
+        RT_TRY(launch_homconv_tc(P, D, ln.ct, ln.A, ln.R, t.Ptc, ln.M, ln.ct_out, s));
+        S->tensor_batches++;
+    } else {
+        RT_TRY(launch_homconv_v(P, D, ln.ct, ln.A, ln.R, t.Phat, ln.M, ln.ct_out, t.variant, s));
+    }
     RT_TRY(launch_decrypt_share(P, D, ln.keys, n, ln.ct_out, ln.yA, s));
     RT_TRY(launch_ntt2d(P, D.H, D.W, ln.sB, ln.yB, (u64)G * D.Co, true, s));
     RT_TRY(cudaMemcpyAsync(ln.h_yA, ln.yA, G * out_img * 4, cudaMemcpyDeviceToHost, s));
@@ -728,7 +738,17 @@ extern "C" int fdsc_server_add_type(fdsc_server* S, const fdsc_params* P, const 
     t.variant = homconv_default_variant(t.D1);
     t.bytes_per_request = request_bytes(t);
     if ((rc = S->arena.alloc((void**)&t.Phat, t.lay1.filter_words * 8))) return rc;
+    // batches of at least kServerTensorMinImages requests run HomConv on the tensor
+    // cores when the layer admits it at the largest batch
+    fdsc_layer Lmax = t.L;
+    Lmax.B = std::max<uint32_t>(S->cfg.max_batch, 1);
+    DevLayer Dmax;
+    const bool tensor = S->cfg.max_batch >= kServerTensorMinImages &&
+                        fdsc_make_layer(P->info, &Lmax, &Dmax, nullptr) == FDSC_OK &&
+                        homconv_tc_supported(P->info.n, Dmax);
+    if (tensor && (rc = S->arena.alloc((void**)&t.Ptc, filter_tc_words(P->info.n, t.D1) * 8))) return rc;
     cudaError_t e = launch_filter_prepare(P->dev, t.D1, w, fh, fw, t.Phat, 0);
+    if (e == cudaSuccess && tensor) e = launch_filter_tc(P->dev, t.D1, t.Phat, t.Ptc, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fdsc_set_error(FDSC_ERR_CUDA, "filter_prepare: %s", cudaGetErrorString(e));
     const uint64_t n = P->info.n;
@@ -824,6 +844,7 @@ extern "C" int fdsc_server_stats_get(fdsc_server* S, fdsc_server_stats* out) {
     out->submitted = S->submitted;
     out->completed = S->completed;
     out->batches = S->batches;
+    out->tensor_batches = S->tensor_batches.load();
     out->peak_inflight_bytes = S->peak_inflight;
     out->mean_batch = S->batches ? (double)S->batched_requests / S->batches : 0.0;
     out->p50_us = pct(0.50);

@@ -139,6 +139,47 @@ def test_server_results_same_alone_and_in_the_mix(F):
     P.close()
 
 
+def test_server_large_batches_use_the_tensor_cores(F):
+    """Batches of 4 or more requests run HomConv on the tensor cores; every
+    result is still the oracle's shares for that request alone."""
+    g = np.random.default_rng(23)
+    types_def = [(2048, 65537, 64, 8, 32, 32, 3), (2048, 65537, 8, 4, 16, 16, 3)]
+    P = F.Params(2048, 65537, max_T=64)
+    OP = O.params(2048, 65537)
+    key_seeds = [11, 12, 13, 14]
+    keys = torch.stack([F.keygen(P, k) for k in key_seeds]).reshape(-1)
+    types = []
+    for (n, p, Ci, Co, H, W, fh) in types_def:
+        w = g.integers(-8, 8, (Co, Ci, fh, fh)).astype(np.int8)
+        types.append(((n, p, Ci, Co, H, W, fh), w))
+    S = F.Server(hbm_budget_bytes=8 << 30, max_batch=8, lanes=1)
+    ids = [S.add_type(P, F.LayerSpec(1, d[2], d[3], d[4], d[5], 0, 1), dev(w, np.int8), keys) for d, w in types]
+    S.start()
+    reqs = []
+    for t in (0, 1):
+        for _ in range(12):
+            r = _server_case(F, g, None, types, None, None)
+            (n, p, Ci, Co, H, W, fh), _ = types[t]
+            r.update(t=t, xA=g.integers(0, p, (Ci, H, W)).astype(np.uint32),
+                     xB=g.integers(0, p, (Ci, H, W)).astype(np.uint32), yA=np.zeros((Co, H, W), np.uint32),
+                     yB=np.zeros((Co, H, W), np.uint32))
+            reqs.append(r)
+    tickets = [S.submit(ids[r["t"]], r["key"], r["es"], r["ss"], r["xA"], r["xB"], r["yA"], r["yB"]) for r in reqs]
+    for tk in tickets:
+        assert S.wait(tk) > 0
+    st = S.stats()
+    assert st.completed == len(reqs) and st.tensor_batches >= 1, (st.batches, st.tensor_batches)
+    S.close()
+    torch.cuda.synchronize()
+    assert F.homconv_tc_status() == 0
+    for r in reqs:
+        (n, p, Ci, Co, H, W, fh), w = types[r["t"]]
+        ref = O.round_trip(OP, O.layer(OP, 1, Ci, Co, H, W), r["xA"][None], r["xB"][None], w,
+                           key_seeds[r["key"]], r["es"], r["ss"])
+        assert np.array_equal(r["yA"], ref["yA"][0]) and np.array_equal(r["yB"], ref["yB"][0])
+    P.close()
+
+
 def test_server_budget_and_timeouts(F):
     P = F.Params(2048, 65537, max_T=64)
     keys = F.keygen(P, 1)
