@@ -192,37 +192,27 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
     t_hat += (u64)bb * key_stride;
     const u64* c0 = ct + (u64)v * 2 * n;
     const u64* c1 = c0 + n;
-    // v = c0 t + c1, four elements' loads in flight per thread; the first
-    // batch is issued before the twiddle tables, which are copied in the
+    // v = c0 t + c1: all of a thread's words (n / blockDim <= 8 of each) are
+    // requested at once, before the twiddle tables, which are copied in the
     // order they are needed
-    u64 a[4], t[4], b[4];
-    auto load4 = [&](u32 j0) {
+    u64 a[8], t[8], b[8];
 #pragma unroll
-        for (int r = 0; r < 4; r++) {
-            const u32 j = j0 + threadIdx.x + (u32)r * blockDim.x;
-            if (j < n) {
-                a[r] = __ldg(c0 + j);
-                t[r] = __ldg(t_hat + j);
-                b[r] = __ldg(c1 + j);
-            }
+    for (int r = 0; r < 8; r++) {
+        const u32 j = threadIdx.x + (u32)r * blockDim.x;
+        if (j < n) {
+            a[r] = __ldg(c0 + j);
+            t[r] = __ldg(t_hat + j);
+            b[r] = __ldg(c1 + j);
         }
-    };
-    auto mac4 = [&](u32 j0) {
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-            const u32 j = j0 + threadIdx.x + (u32)r * blockDim.x;
-            if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
-        }
-    };
-    load4(0);
+    }
     stage_async(tq, P.qinv2, n * 16);                  // group 3
     stage_async(tp, P.pfw2, S * 8);                    // group 2
     stage_pairs_for_length(tw_row, L.logW, true, P);  // group 1
     stage_pairs_for_length(tw_col, L.logH, true, P);  // group 0
-    mac4(0);
-    for (u32 j0 = 4 * blockDim.x; j0 < n; j0 += 4 * blockDim.x) {
-        load4(j0);
-        mac4(j0);
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        const u32 j = threadIdx.x + (u32)r * blockDim.x;
+        if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
     }
     stage_wait_groups<3>();
     ntt_r8p<false, u64>(c, P.logn, 1, tq, P.ninv, P.ninv_s, P);
@@ -251,6 +241,158 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
         val = shoup_mul32(val, scale, scale_s, P.p);
         y[((u64)b * L.Co + co) * HW + f] = val >= P.p ? val - P.p : val;
     }
+}
+
+// The same decryption + decode + fold + INTT2D split between the two CTAs of
+// a cluster by coefficient parity (one slot set, d = 1).  Rank r computes the
+// coefficients v_{2i+r} only: with the NTT_q words in bit-reversed order,
+// words 2t and 2t+1 are the evaluations at psi^(2k+1) and -psi^(2k+1)
+// (k = brv_{n/2}(t)), so
+//   v_{2i}   = n^-1 INTT_{n/2}(c_{2t} + c_{2t+1})_i,
+//   v_{2i+1} = n^-1 INTT_{n/2}(psi^-(2k+1) (c_{2t} - c_{2t+1}))_i,
+// half-length transforms with psi^2, whose bit-reversed twiddles are the first
+// half of the length-n table (psi^-(2k+1) = psi^-brv_n(t) * psi^-1, psi^-1 =
+// the table's entry n/2).  Rounding is per coefficient.  The rest is linear:
+// the slot vector of the even coefficients is Y[u] at slots 2u and 2u+1 (Y the
+// half-length NTT_p), that of the odd ones psi_p^(2k+1) Z[u] at 2u and its
+// negation at 2u+1; each CTA folds and INTT2Ds its part and the two partial
+// shares are added through distributed shared memory.
+__device__ __forceinline__ u32 cluster_rank() {
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ u32 ld_peer_u32(const u32* local, u32 peer) {
+    u32 a = (u32)__cvta_generic_to_shared(local), ra, v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(peer));
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMaxThreads)
+    decrypt_share_pair_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat, u64 key_stride,
+                              const u64* __restrict__ ct, u32* __restrict__ y, u32 scale, u32 scale_s) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const u32 n = P.n, S = P.S, hn = n >> 1, hS = S >> 1;
+    const u32 np = padded_len(n);
+    ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^-brv, companion)
+    uint2* tp = reinterpret_cast<uint2*>(tq + n);        // [S] (psi_p^brv, companion)
+    uint2* tw_row = tp + S;                              // [W/2]
+    uint2* tw_col = tw_row + (L.W >> 1);                 // [H/2]
+    u64* c = reinterpret_cast<u64*>(tw_col + (L.H >> 1));  // padded [n]
+    u32* slots = reinterpret_cast<u32*>(c + np);         // padded [n]
+    const u32 HW = L.HW, logHW = L.logH + L.logW;
+    const u32 nplanes = L.g_b;
+    u32* planes = slots + np;                            // padded [g_b HW]
+    u32* xs = reinterpret_cast<u32*>(c);                 // the part's slot vector, padded [S] (c is free by then)
+    griddep_release();
+    griddep_wait();
+
+    const u32 rank = cluster_rank();
+    const u32 v = blockIdx.x >> 1, co = v % L.Co, bb = v / L.Co;
+    t_hat += (u64)bb * key_stride;
+    const u64* c0 = ct + (u64)v * 2 * n;
+    const u64* c1 = c0 + n;
+    // all of a thread's words (n / blockDim <= 8 of each) are requested at once,
+    // before the twiddle tables: one memory latency instead of two
+    u64 a[8], t[8], b[8];
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        const u32 j = threadIdx.x + (u32)r * blockDim.x;
+        if (j < n) {
+            a[r] = __ldg(c0 + j);
+            t[r] = __ldg(t_hat + j);
+            b[r] = __ldg(c1 + j);
+        }
+    }
+    stage_async(tq, P.qinv2, n * 16);                  // group 3
+    stage_async(tp, P.pfw2, S * 8);                    // group 2
+    stage_pairs_for_length(tw_row, L.logW, true, P);  // group 1
+    stage_pairs_for_length(tw_col, L.logH, true, P);  // group 0
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        const u32 j = threadIdx.x + (u32)r * blockDim.x;
+        if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
+    }
+    stage_wait_groups<3>();
+    // this part's half-length input: h_t = c_{2t} + c_{2t+1}, or psi^-(2k+1) (c_{2t} - c_{2t+1})
+    {
+        const ulonglong2 pinv1 = tq[hn];  // psi^-1
+        u64 hv[4];  // n/2 words over at least n/8 threads
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const u32 tt = threadIdx.x + (u32)r * blockDim.x;
+            if (tt >= hn) continue;
+            const u64 x0 = c[padx(2 * tt)], x1 = c[padx(2 * tt + 1)];
+            u64 h;
+            if (rank == 0) {
+                h = addmod_q(x0, x1, P.q);
+            } else {
+                h = shoup_mul(submod_q(x0, x1, P.q), tq[tt].x, tq[tt].y, P.q);
+                h = h >= P.q ? h - P.q : h;
+                h = shoup_mul(h, pinv1.x, pinv1.y, P.q);
+                h = h >= P.q ? h - P.q : h;
+            }
+            hv[r] = h;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const u32 tt = threadIdx.x + (u32)r * blockDim.x;
+            if (tt < hn) c[padx(tt)] = hv[r];
+        }
+        __syncthreads();
+    }
+    ntt_r8p<false, u64>(c, P.logn - 1, 1, tq, P.ninv, P.ninv_s, P);  // v_{2i+rank}, i < n/2, times n^-1
+    for (u32 i = threadIdx.x; i < hn; i += blockDim.x) slots[padx(i)] = round_pq2(c[padx(i)], P);
+    stage_wait_groups<2>();
+    ntt_r8p<true, u32>(slots, P.logS - 1, 1, tp, 0, 0, P);  // half-length slot decode
+    {
+        const uint2 psip = tp[hS];  // psi_p
+        for (u32 u = threadIdx.x; u < hS; u += blockDim.x) {
+            u32 w = slots[padx(u)];
+            if (rank == 1) {
+                w = shoup_mul32(w, tp[u].x, tp[u].y, P.p);
+                w = w >= P.p ? w - P.p : w;
+                w = shoup_mul32(w, psip.x, psip.y, P.p);
+                w = w >= P.p ? w - P.p : w;
+            }
+            xs[padx(2 * u)] = w;
+            xs[padx(2 * u + 1)] = rank == 1 ? (w ? P.p - w : 0u) : w;
+        }
+    }
+    __syncthreads();
+    // fold the g_c channel blocks of every image block
+    for (u32 e = threadIdx.x; e < nplanes * HW; e += blockDim.x) {
+        const u32 ib = e >> logHW, f = e & (HW - 1);
+        const u32 src = ib * L.g_c * HW + f;
+        u32 acc = 0;
+        for (u32 ic = 0; ic < L.g_c; ic++) acc = addmod_p(acc, xs[padx(src + ic * HW)], P.p);
+        planes[padx(e)] = acc;
+    }
+    stage_wait_groups<0>();
+    lines_r8p<true>(planes, nplanes, true, L.logH, L.logW, tw_row, P.p);
+    lines_r8p<true>(planes, nplanes, false, L.logH, L.logW, tw_col, P.p);
+    // this part's share in natural order, then the two parts added across the pair
+    u32* part = slots;  // [g_b HW], free after the decode
+    for (u32 e = threadIdx.x; e < nplanes * HW; e += blockDim.x) {
+        const u32 pl = e >> logHW, f = e & (HW - 1);
+        u32 val = planes[padx((pl << logHW) + (brv_bits(f >> L.logW, L.logH) << L.logW) + brv_bits(f & (L.W - 1), L.logW))];
+        val = shoup_mul32(val, scale, scale_s, P.p);
+        part[e] = val >= P.p ? val - P.p : val;
+    }
+    cluster_sync_all();
+    const u32 half = (nplanes * HW) >> 1;
+    for (u32 e = rank * half + threadIdx.x; e < (rank + 1) * half; e += blockDim.x) {
+        const u32 pl = e >> logHW, f = e & (HW - 1);
+        const u32 bi = bb * L.g_b + pl;
+        if (bi >= L.B) continue;
+        y[((u64)bi * L.Co + co) * HW + f] = addmod_p(part[e], ld_peer_u32(part + e, rank ^ 1), P.p);
+    }
+    cluster_sync_all();  // the peer's part stays in place until both halves are read
 }
 
 template <typename K>
@@ -292,9 +434,25 @@ cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u6
 cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, const u64* ct,
                                  u32* y, cudaStream_t s) {
     const size_t sm = decrypt_share_smem_bytes(P, L);
+    const u32 scale = fdsc_powmod32(L.HW % P.p, P.p - 2, P.p);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (P.d == 1 && P.n >= 32 && 2ull * L.n_out <= (u64)sms) {
+        // one slot set and fewer output ciphertexts than half the SMs (a single
+        // image): the two CTAs of a cluster take one parity of the coefficients
+        // each, on SMs that would otherwise idle; batched work keeps one CTA per
+        // ciphertext (the pair repeats the loads and the first products)
+        cudaError_t e = opt_in(decrypt_share_pair_kernel, sm);
+        if (e != cudaSuccess) return e;
+        return launch_online(decrypt_share_pair_kernel, 2 * L.n_out, threads_for(P.n), sm, s, P, L, t_hat, key_stride,
+                             ct, y, scale, fdsc_shoup32(scale, P.p));
+    }
     cudaError_t e = opt_in(decrypt_share_kernel, sm);
     if (e != cudaSuccess) return e;
-    const u32 scale = fdsc_powmod32(L.HW % P.p, P.p - 2, P.p);
     return launch_online(decrypt_share_kernel, L.n_out, threads_for(P.n), sm, s, P, L, t_hat, key_stride, ct, y, scale,
                          fdsc_shoup32(scale, P.p));
 }
