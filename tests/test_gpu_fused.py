@@ -36,6 +36,8 @@ CASES = [
     dict(n=4096, p=12289, B=5, Ci=3, Co=2, H=16, W=16, fh=3, g_c=2, g_b=3),        # two slot sets (d = 2)
     dict(n=256, p=65537, B=3, Ci=5, Co=3, H=8, W=8, fh=3, g_c=2, g_b=2),           # small ring, ragged
     dict(n=1024, p=65537, B=1, Ci=2, Co=2, H=8, W=128, fh=3, fw=5),                # wide plane
+    dict(n=2048, p=147457, B=1, Ci=64, Co=64, H=32, W=32, fh=3),                   # Table 2 "Medium" prime
+    dict(n=1024, p=786433, B=3, Ci=6, Co=3, H=16, W=16, fh=3, g_c=2, g_b=2),       # p = 3 2^18 + 1, near 2^20
 ]
 
 

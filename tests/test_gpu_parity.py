@@ -64,11 +64,11 @@ def _check_layer(F, n, p, B, Ci, Co, H, W, fh, fw=None, g_c=None, g_b=1, seed=0,
 
 
 # ---------------------------------------------------------------- transforms
-@pytest.mark.parametrize("p", [65537, 12289])
+@pytest.mark.parametrize("p", [65537, 12289, 147457, 786433])  # 786433 2^10 < 2^32: lazy sums still fit
 @pytest.mark.parametrize("H,W,planes", [(2, 2, 3), (4, 64, 5), (64, 4, 2), (8, 8, 7), (16, 16, 64), (16, 16, 5),
                                         (32, 32, 1), (32, 32, 64), (64, 64, 9), (2, 2048, 2), (32, 32, 2500)])
 def test_ntt2d_intt2d_match_oracle(F, p, H, W, planes):
-    P = F.Params(1024, p)
+    P = F.Params(1024, p, max_T=8)  # the default T = 256 fails the noise bound at p = 786433
     x = np.random.default_rng(H * 131 + W + planes).integers(0, p, (planes, H, W)).astype(np.uint32)
     X = F.ntt2d(P, dev(x, np.int32))
     assert np.array_equal(u32(X).reshape(x.shape), O.ntt2d(x, p))
@@ -132,6 +132,8 @@ def test_config_layer_bit_exact(F, cfg):
     dict(n=1024, p=65537, B=1, Ci=3, Co=2, H=32, W=32, fh=1),                    # 1x1 filter
     dict(n=1024, p=65537, B=1, Ci=2, Co=2, H=4, W=256, fh=3, fw=5),              # wide plane, fh != fw
     dict(n=2048, p=65537, B=2, Ci=64, Co=8, H=32, W=32, fh=3, homrec=False),     # first round, no HomRec
+    dict(n=2048, p=147457, B=1, Ci=16, Co=4, H=32, W=32, fh=3),                  # Table 2 "Medium" prime
+    dict(n=1024, p=786433, B=3, Ci=6, Co=3, H=16, W=16, fh=3, g_c=2, g_b=2),      # p = 3 2^18 + 1, near 2^20
 ])
 def test_layer_variants_bit_exact(F, args):
     _check_layer(F, **args)

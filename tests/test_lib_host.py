@@ -44,7 +44,7 @@ def test_library_exports_every_declared_entry_point(F):
 
 
 @pytest.mark.parametrize("n,p", [(1024, 65537), (2048, 65537), (4096, 65537), (2048, 12289), (4096, 12289),
-                                 (64, 65537), (256, 12289)])
+                                 (64, 65537), (256, 12289), (2048, 147457), (4096, 786433)])
 def test_params_query_matches_oracle(F, n, p):
     info = F.params_query(n, p)
     ref = O.params(n, p)

@@ -31,6 +31,27 @@ def test_table2_pE_is_minimal_prime_splitting_xn_plus_1():
         assert sympy.isprime(pE)
 
 
+def test_decoupled_moduli_do_not_reconstruct_mod_pN():
+    """Table 2's Binary and High rows pair an NTT modulus p_N with a larger
+    encryption modulus p_E (Sec. 5.2 asks p_E >= p_A >= p_N).  Shares taken
+    mod p_E do not give the result mod p_N: the appendix's step
+    x mod p_A mod p_N = x mod p_N fails as soon as x passes p_A, and one
+    Hadamard product of two spectra below p_N already passes p_E.  Only rows
+    with p_N = p_E (Table 2's Medium row) run as one prime; the library takes
+    any such prime below 2^20."""
+    rows = {r[0]: (int(r[1]), int(r[3])) for r in _rows("table2_moduli.txt")}
+    assert rows["Medium"][0] == rows["Medium"][1]
+    for name in ("Binary", "High"):
+        pN, pE = rows[name]
+        assert pN < pE
+        x = (pN - 1) * (pN - 1)  # one product of two spectra words
+        assert x >= pE and x % pE % pN != x % pN, name
+        # smallest counterexample to the appendix identity: x = p_E
+        assert pE % pE % pN == 0 != pE % pN, name
+    P = O.params(2048, rows["Medium"][0])
+    assert P.S == 2048 and O.noise_ok(P, 32)
+
+
 def test_smallest_prime_splitting_x2048_plus_1_is_12289():
     # Sec. 5.2: "for n = 2048, p_E >= 12289" -- x^n + 1 splits completely mod
     # a prime iff 2n | p - 1.

@@ -126,6 +126,8 @@ def _e2e(n, p, B, Ci, Co, H, W, fh, g_c=None, g_b=1, seed=0, homrec=True, suppor
     dict(n=4096, p=12289, B=3, Ci=2, Co=2, H=64, W=64, fh=3),                      # d = 2 with halves
     dict(n=4096, p=12289, B=5, Ci=3, Co=2, H=16, W=16, fh=3, g_c=2, g_b=3),         # d = 2 with blocks
     dict(n=2048, p=65537, B=1, Ci=1, Co=4, H=32, W=32, fh=5, support=(28, 28)),    # MNIST-shaped
+    dict(n=2048, p=147457, B=1, Ci=6, Co=3, H=32, W=32, fh=3),                     # Table 2 "Medium" prime
+    dict(n=256, p=786433, B=3, Ci=3, Co=2, H=8, W=8, fh=3, g_c=2, g_b=2),           # p = 3 2^18 + 1, near 2^20
 ])
 def test_end_to_end_shares_reconstruct_convolution(args):
     _e2e(**args)
