@@ -1042,7 +1042,7 @@ def run_gpu(args, rank, local_rank, world):
         "serving": serving,
         "ntt2d_sweep": sweep,
         "primitive_rates": {k: {"ops_per_s": v[0], "ops_per_clk_per_sm": v[1]} for k, v in calib.items()},
-        "gpu_launches": LAUNCHES_PER_STEP * (args.steps + len(step_ms)) + 8 * n_unfused + 3 * hc_reps * R
+        "gpu_launches": LAUNCHES_PER_STEP * (args.steps + len(step_ms) + n_one) + 8 * n_unfused + 3 * hc_reps * R
                         + sum(pt["launches"] for pt in sweep["points"]),
         "homconv_variant": args.homconv_variant,
         "clocks": clk,

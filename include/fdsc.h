@@ -4,11 +4,12 @@
  * Shi, Sato, CVPR 2020).
  *
  * One convolution layer, Fig. 2 of the paper, runs as:
- *   Alice  fdsc_ntt2d(x_A) -> fdsc_encrypt                         (lines 1-2)
- *   Bob    fdsc_ntt2d(x_B) -> fdsc_homrec      (between layers, lines 9-11)
+ *   Alice  fdsc_ntt2d(x_A) -> fdsc_encrypt               (transform, encrypt)
+ *   Bob    fdsc_ntt2d(x_B) -> fdsc_homrec               (HomRec, Eq. 3)
  *   Bob    fdsc_homconv (Hadamard product summed over input channels,
- *          fused with HomShare)                                    (lines 3-4)
- *   Alice  fdsc_decrypt -> fdsc_intt2d;  Bob fdsc_intt2d(s_B-hat)  (lines 5-6)
+ *          fused with HomShare)                          (Eq. 2)
+ *   Alice  fdsc_decrypt -> fdsc_intt2d;  Bob fdsc_intt2d(s_B-hat)
+ *                                                        (decrypt, inverse transform)
  * with setup (no user input): fdsc_params_create, fdsc_keygen,
  * fdsc_filter_prepare, fdsc_mask_prepare.
  *
@@ -120,11 +121,11 @@ int fdsc_layout_query(uint32_t n, uint32_t p, const fdsc_layer* L, fdsc_layout* 
 /* Transforms                                                              */
 /* ---------------------------------------------------------------------- */
 /* Eq. 12 in two dimensions (the cyclic NTT over the padded H x W plane,
- * Fig. 2 lines 1 and 9): X[k1][k2] = sum_{i,j} x[i][j] w_H^(i k1) w_W^(j k2)
+ * Fig. 2, both parties' forward transforms): X[k1][k2] = sum_{i,j} x[i][j] w_H^(i k1) w_W^(j k2)
  * mod p, w_L = g_p^((p-1)/L).  x, X: uint32 [planes][H][W]; x may equal X. */
 int fdsc_ntt2d(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_t* x, uint32_t* X,
                uint64_t planes, void* stream);
-/* Fig. 2 line 6: the inverse, x = (HW)^-1 sum X w^-(...). */
+/* Fig. 2's final inverse transform, x = (HW)^-1 sum X w^-(...). */
 int fdsc_intt2d(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_t* X, uint32_t* x,
                 uint64_t planes, void* stream);
 
@@ -144,7 +145,7 @@ int fdsc_pool2x2_sum(const fdsc_params* P, uint32_t H, uint32_t W, const uint32_
  * written as t_hat = NTT_q(t): uint64 [n]. */
 int fdsc_keygen(const fdsc_params* P, uint64_t seed, uint64_t* t_hat, void* stream);
 
-/* Fig. 2 line 3 (Bob): w_hat = flatten(NTT2D(W)) packed into plaintext
+/* Fig. 2, Bob's filter transform: w_hat = flatten(NTT2D(W)) packed into plaintext
  * polynomials and lifted to NTT_q.  w: int8 [Co][Ci][fh][fw] (taps at the
  * top-left of the padded plane, fh <= H, fw <= W); P_hat: uint64
  * [Co][T][beta][n] -- plaintext (co, k, h) holds the spectra of channels
@@ -190,7 +191,7 @@ int fdsc_encrypt(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_ha
 int fdsc_homrec(const fdsc_params* P, const fdsc_layer* L, const uint32_t* XB, uint64_t* ct,
                 void* stream);
 
-/* Fig. 2 lines 3-4: ct_out[bb][co][h][c][j] = sum_k ct_in[bb][k][h][c][j]
+/* Fig. 2, Bob's HomConv and HomShare (Eq. 2): ct_out[bb][co][h][c][j] = sum_k ct_in[bb][k][h][c][j]
  * P_hat[co][k][h][j] mod q, then c1 -= M_hat[bb][co][h] (HomShare; skipped
  * when M_hat is NULL).  ct_out: uint64 [GB][Co][beta][2][n]; must not alias
  * ct_in.  Exact: the sum is formed in 128 bits and reduced once per 256
@@ -198,7 +199,7 @@ int fdsc_homrec(const fdsc_params* P, const fdsc_layer* L, const uint32_t* XB, u
 int fdsc_homconv(const fdsc_params* P, const fdsc_layer* L, const uint64_t* ct_in,
                  const uint64_t* P_hat, const uint64_t* M_hat, uint64_t* ct_out, void* stream);
 
-/* Fig. 2 line 5 (Alice): v = INTT_q(c0_hat o t_hat + c1_hat),
+/* Fig. 2, Alice's decryption (Sec. 3.1): v = INTT_q(c0_hat o t_hat + c1_hat),
  * m = floor((2 p v + q) / (2 q)) mod p, slots = decode(m), and the g_c
  * channel blocks of each image folded: SA_hat: uint32 [B][Co][H W]. */
 int fdsc_decrypt(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat,
@@ -216,7 +217,8 @@ int fdsc_decrypt(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_ha
 int fdsc_encrypt_constants(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, uint64_t seed,
                            uint64_t* ct, void* stream);
 
-/* The message part of Fig. 2 lines 1-2 (and 9-10) from a SPATIAL share
+/* The message part of Alice's encryption in Fig. 2 (and of Bob's HomRec
+ * plaintext) from a SPATIAL share
  * x: uint32 [B][Ci][H][W] -> NTT2D -> flatten and pack -> slot encode ->
  * times Delta -> NTT_q, written to A: uint64 [n_in][n].  Needs H W <= S and
  * H, W >= 8 (FDSC_ERR_UNSUPPORTED otherwise; use fdsc_ntt2d + fdsc_encrypt). */
@@ -277,7 +279,7 @@ int fdsc_homconv_seeded(const fdsc_params* P, const fdsc_layer* L, uint64_t seed
                         const uint64_t* A1, const uint64_t* A2, const uint64_t* P_hat, const uint64_t* M_hat,
                         uint64_t* ct_out, void* stream);
 
-/* Fig. 2 lines 5-6 (Alice) in one kernel: decrypt, decode, fold the channel
+/* Alice's last two steps of Fig. 2 in one kernel: decrypt, decode, fold the channel
  * blocks and INTT2D, giving her SPATIAL share y: uint32 [B][Co][H][W]
  * (= fdsc_intt2d(fdsc_decrypt(...))).  Same restrictions as
  * fdsc_encode_share. */
@@ -308,8 +310,8 @@ int fdsc_decrypt_share_multi(const fdsc_params* P, const fdsc_layer* L, const ui
 /* Not in the paper (a batching runtime around its per-layer protocol).  A
  * plan holds, for every layer, the filter plaintexts and HomShare masks
  * (prepared at creation, i.e. setup) and its intermediate ciphertext buffers,
- * and records the whole online path of every layer (Fig. 2 lines 1-6 with
- * HomRec) as one CUDA graph in which independent layers and the
+ * and records the whole online path of every layer (the one-layer protocol
+ * of Fig. 2 with HomRec) as one CUDA graph in which independent layers and the
  * input-independent steps run concurrently.  The masks and encryption seeds
  * are fixed at creation; a protocol run must not reuse them, so a new plan
  * (or new seeds) is needed per inference. */
@@ -347,7 +349,7 @@ enum {
                                    kernel among them where T <= 128), keep the fastest */
     FDSC_PLAN_CHAIN = 2,        /* layer i starts once layer i-1 (and its pooling) has
                                    finished, so it may read the shares layer i-1 wrote:
-                                   a network's convolution stack (Fig. 2 lines 7-13,
+                                   a network's convolution stack (Fig. 2's layer to layer steps,
                                    with the activation protocol left to the caller) */
     FDSC_PLAN_TENSOR = 4        /* untuned layers with T <= 128 use the tensor-core
                                    HomConv (the words do not change) */

@@ -327,8 +327,8 @@ def pool2x2_sum(p, x):
 
 
 def round_trip(P, L, xA, xB, w, key_seed, enc_seed, srv_seed, with_homrec=True, flood_bits=0):
-    """One FDSC layer (Fig. 2, lines 1-6, with HomRec of Bob's share as in
-    lines 9-11; optionally HomShare noise flooding): returns every stage
+    """One FDSC layer (the one-layer protocol of Fig. 2, with HomRec of Bob's
+    share, Eq. 3; optionally HomShare noise flooding): returns every stage
     boundary for parity checks."""
     H, W = L.H, L.W
     out = {}

@@ -6,7 +6,7 @@
 //   K9 keygen          Eq. 1 secret t, stored as NTT_q(t)
 //   K3 encrypt         Eq. 1 in the NTT_q domain (Sec. 5.1)
 //   K6 homrec          Eq. 3 (HomRec): add Bob's encoded share to c1
-//   K7 filter_prepare  Fig. 2 line 3: w_hat packed, lifted, NTT_q
+//   K7 filter_prepare  Fig. 2, Bob's filter: w_hat packed, lifted, NTT_q
 //   K8 mask_prepare    Eq. 2 (HomShare) randomness and its NTT_q image
 //   K5 decrypt         Sec. 3.1 decryption, slot decode, channel-block fold
 #include <map>

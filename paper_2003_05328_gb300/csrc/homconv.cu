@@ -1,4 +1,4 @@
-// homconv.cu -- K4: HomConv fused with HomShare (Fig. 2 lines 3-4, Eq. 2).
+// homconv.cu -- K4: HomConv fused with HomShare (Fig. 2, Eq. 2).
 //
 // In the NTT_q domain the homomorphic Hadamard product of an input
 // ciphertext with a plaintext filter polynomial is a pointwise product, so

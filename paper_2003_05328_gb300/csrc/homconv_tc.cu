@@ -1,4 +1,4 @@
-// homconv_tc.cu -- HomConv + HomShare (Fig. 2 lines 3-4, Eq. 2) on the
+// homconv_tc.cu -- HomConv + HomShare (Fig. 2, Eq. 2) on the
 // tensor cores, exact.
 //
 // For every evaluation index J = (h, j) of the NTT_q domain the layer is a

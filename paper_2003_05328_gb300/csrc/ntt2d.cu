@@ -1,5 +1,5 @@
 // ntt2d.cu -- K1 / K2: batched cyclic NTT2D / INTT2D mod p over padded
-// H x W planes (Eq. 12 in two dimensions; Fig. 2 lines 1, 6, 9).
+// H x W planes (Eq. 12 in two dimensions; Fig. 2's forward and inverse transforms).
 //
 // One CTA transforms one plane at a time in shared memory: the plane is read
 // with coalesced loads and scattered into bit-reversed order, rows and then

@@ -211,7 +211,7 @@ def test_pool2x2_sum_pins():
 
 
 def test_two_layer_chain_with_pooling_reconstructs_the_network():
-    """A chain of FDSC layers (Fig. 2 lines 7-13, the activation protocol
+    """A chain of FDSC layers (Fig. 2's layer to layer steps, the activation protocol
     left out): layer 2 takes layer 1's output shares after sum pooling; the
     final shares add up to conv2(pool(conv1(x))) computed directly."""
     p, n = 65537, 1024
