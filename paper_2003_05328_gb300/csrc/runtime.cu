@@ -507,6 +507,11 @@ struct Req {
 struct Lane {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    // the batch's independent producers run beside the lane's stream: Bob's
+    // mask and output share, Alice's encryption constants, Bob's HomRec
+    // plaintext; events join them before HomConv and at the batch's end
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_seed = nullptr, ev_mask = nullptr, ev_yB = nullptr, ev_ct = nullptr, ev_R = nullptr;
     bool busy = false;
     std::vector<Req> batch;
     uint32_t type = 0;
@@ -574,17 +579,34 @@ int launch_batch(fdsc_server* S, Lane& ln) {
         ln.h_seeds[G + b] = r.mask_seed;
     }
     S->copies->run(jobs);
-    cudaStream_t s = ln.stream;
-    RT_TRY(cudaMemcpyAsync(ln.xA, ln.h_xA, G * in_img * 4, cudaMemcpyHostToDevice, s));
-    RT_TRY(cudaMemcpyAsync(ln.xB, ln.h_xB, G * in_img * 4, cudaMemcpyHostToDevice, s));
+    cudaStream_t s = ln.stream, s_mask = ln.side[0], s_ct = ln.side[1], s_rec = ln.side[2];
+    // seeds and keys first: the producers that need no share start on them
     RT_TRY(cudaMemcpyAsync(ln.seeds, ln.h_seeds, 2 * G * 8, cudaMemcpyHostToDevice, s));
     for (uint32_t b = 0; b < G; b++)
         RT_TRY(cudaMemcpyAsync(ln.keys + b * n, t.keys + (uint64_t)ln.batch[b].r.key * n, n * 8, cudaMemcpyDeviceToDevice,
                                s));
-    RT_TRY(launch_mask_prepare(P, D, 0, ln.seeds + G, 0, ln.M, ln.sB, s));
-    RT_TRY(launch_constants(P, D, ln.keys, n, 0, ln.seeds, ln.ct, s));
+    RT_TRY(cudaEventRecord(ln.ev_seed, s));
+    // Bob: HomShare mask, then his output share (INTT2D of s_B) and its copy out
+    RT_TRY(cudaStreamWaitEvent(s_mask, ln.ev_seed, 0));
+    RT_TRY(launch_mask_prepare(P, D, 0, ln.seeds + G, 0, ln.M, ln.sB, s_mask));
+    RT_TRY(cudaEventRecord(ln.ev_mask, s_mask));
+    RT_TRY(launch_ntt2d(P, D.H, D.W, ln.sB, ln.yB, (u64)G * D.Co, true, s_mask));
+    RT_TRY(cudaMemcpyAsync(ln.h_yB, ln.yB, G * out_img * 4, cudaMemcpyDeviceToHost, s_mask));
+    RT_TRY(cudaEventRecord(ln.ev_yB, s_mask));
+    // Alice: encryption constants (Enc(0) of every input ciphertext)
+    RT_TRY(cudaStreamWaitEvent(s_ct, ln.ev_seed, 0));
+    RT_TRY(launch_constants(P, D, ln.keys, n, 0, ln.seeds, ln.ct, s_ct));
+    RT_TRY(cudaEventRecord(ln.ev_ct, s_ct));
+    // Bob: HomRec plaintext from his share
+    RT_TRY(cudaMemcpyAsync(ln.xB, ln.h_xB, G * in_img * 4, cudaMemcpyHostToDevice, s_rec));
+    RT_TRY(launch_share(P, D, ln.xB, ln.R, false, s_rec));
+    RT_TRY(cudaEventRecord(ln.ev_R, s_rec));
+    // Alice's message on the lane's stream, then HomConv once all addends exist
+    RT_TRY(cudaMemcpyAsync(ln.xA, ln.h_xA, G * in_img * 4, cudaMemcpyHostToDevice, s));
     RT_TRY(launch_share(P, D, ln.xA, ln.A, false, s));
-    RT_TRY(launch_share(P, D, ln.xB, ln.R, false, s));
+    RT_TRY(cudaStreamWaitEvent(s, ln.ev_ct, 0));
+    RT_TRY(cudaStreamWaitEvent(s, ln.ev_R, 0));
+    RT_TRY(cudaStreamWaitEvent(s, ln.ev_mask, 0));
     if (t.Ptc && D.GB >= kServerTensorMinImages) {
         RT_TRY(launch_homconv_tc(P, D, ln.ct, ln.A, ln.R, t.Ptc, ln.M, ln.ct_out, s));
         S->tensor_batches++;
@@ -592,9 +614,9 @@ int launch_batch(fdsc_server* S, Lane& ln) {
         RT_TRY(launch_homconv_v(P, D, ln.ct, ln.A, ln.R, t.Phat, ln.M, ln.ct_out, t.variant, s));
     }
     RT_TRY(launch_decrypt_share(P, D, ln.keys, n, ln.ct_out, ln.yA, s));
-    RT_TRY(launch_ntt2d(P, D.H, D.W, ln.sB, ln.yB, (u64)G * D.Co, true, s));
     RT_TRY(cudaMemcpyAsync(ln.h_yA, ln.yA, G * out_img * 4, cudaMemcpyDeviceToHost, s));
-    RT_TRY(cudaMemcpyAsync(ln.h_yB, ln.yB, G * out_img * 4, cudaMemcpyDeviceToHost, s));
+    // the batch is done when both output shares are on the host
+    RT_TRY(cudaStreamWaitEvent(s, ln.ev_yB, 0));
     RT_TRY(cudaEventRecord(ln.done, s));
     (void)lay;
     return FDSC_OK;
@@ -687,6 +709,8 @@ void worker_loop(fdsc_server* S) {
             if (rc) {
                 S->error = rc;
                 lk.unlock();
+                for (cudaStream_t st : ln.side)
+                    if (st) cudaStreamSynchronize(st);
                 cudaStreamSynchronize(ln.stream);
                 finish_batch(S, ln, false);
                 lk.lock();
@@ -780,7 +804,15 @@ extern "C" int fdsc_server_start(fdsc_server* S) {
             (rc = S->arena.alloc((void**)&ln.seeds, 2 * B * 8)))
             return rc;
         if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&ln.side[0], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&ln.side[1], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&ln.side[2], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ln.ev_seed, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ln.ev_mask, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ln.ev_yB, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ln.ev_ct, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ln.ev_R, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost((void**)&ln.h_xA, B * S->max_in * 4) != cudaSuccess ||
             cudaMallocHost((void**)&ln.h_xB, B * S->max_in * 4) != cudaSuccess ||
             cudaMallocHost((void**)&ln.h_yA, B * S->max_out * 4) != cudaSuccess ||
@@ -866,11 +898,17 @@ extern "C" int fdsc_server_destroy(fdsc_server* S) {
     if (S->worker.joinable()) S->worker.join();
     S->copies.reset();
     for (auto& ln : S->lanes) {
+        for (cudaStream_t st : ln.side)
+            if (st) {
+                cudaStreamSynchronize(st);
+                cudaStreamDestroy(st);
+            }
         if (ln.stream) {
             cudaStreamSynchronize(ln.stream);
             cudaStreamDestroy(ln.stream);
         }
-        if (ln.done) cudaEventDestroy(ln.done);
+        for (cudaEvent_t ev : {ln.done, ln.ev_seed, ln.ev_mask, ln.ev_yB, ln.ev_ct, ln.ev_R})
+            if (ev) cudaEventDestroy(ev);
         cudaFreeHost(ln.h_xA);
         cudaFreeHost(ln.h_xB);
         cudaFreeHost(ln.h_yA);
