@@ -7,6 +7,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <map>
 #include <memory>
@@ -469,7 +470,7 @@ class CopyPool {
     }
 
   private:
-    static constexpr size_t kChunk = 256 << 10, kInline = 1 << 20;
+    static constexpr size_t kChunk = 64 << 10, kInline = 64 << 10;
     void work() {
         for (size_t i = next_.fetch_add(1); i < chunks_.size(); i = next_.fetch_add(1))
             memcpy(chunks_[i].dst, chunks_[i].src, chunks_[i].bytes);
@@ -512,6 +513,9 @@ struct Lane {
     // plaintext; events join them before HomConv and at the batch's end
     cudaStream_t side[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev_seed = nullptr, ev_mask = nullptr, ev_yB = nullptr, ev_ct = nullptr, ev_R = nullptr;
+    // the recorded batches: [type][G - 1], and which run HomConv on the tensor cores
+    std::vector<cudaGraphExec_t> graphs;
+    std::vector<char> graph_tensor;
     bool busy = false;
     std::vector<Req> batch;
     uint32_t type = 0;
@@ -557,34 +561,35 @@ uint64_t request_bytes(const ServerType& t) {
            4 * (2 * l.in_spectra_words + 3 * l.out_spectra_words);
 }
 
-// Launches one batch on a lane (worker thread, lock NOT held).
-int launch_batch(fdsc_server* S, Lane& ln) {
-    const ServerType& t = S->types[ln.type];
+// Each request's client key, gathered from its type's key pool:
+// keys[b][i] = pool[idx[b]][i] (idx[b] < pool size, checked at submission).
+__global__ void __launch_bounds__(256) gather_keys_kernel(const u64* __restrict__ pool, const u64* __restrict__ idx,
+                                                          u32 G, u32 n, u64* __restrict__ keys) {
+    const u64 total = (u64)G * n;
+    for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (u64)gridDim.x * blockDim.x)
+        keys[e] = pool[idx[e / n] * n + e % n];
+}
+
+// Enqueues the GPU work of a batch of G requests of type `type` on a lane,
+// reading the lane's pinned staging: h_seeds = [encryption seeds][mask
+// seeds][key indices] (G each), h_xA / h_xB the requests' shares; the
+// results land in h_yA / h_yB.  Recorded once per (type, G) into a graph.
+int record_batch(const fdsc_server* S, Lane& ln, uint32_t type, uint32_t G, bool* tensor) {
+    const ServerType& t = S->types[type];
     const DevParams& P = t.P->dev;
-    const uint32_t G = (uint32_t)ln.batch.size();
     fdsc_layer LG = t.L;
     LG.B = G;
     LG.g_b = 1;
     DevLayer D;
-    fdsc_layout lay;
-    int rc = fdsc_make_layer(t.P->info, &LG, &D, &lay);
+    int rc = fdsc_make_layer(t.P->info, &LG, &D, nullptr);
     if (rc) return rc;
     const uint64_t in_img = t.lay1.in_spectra_words, out_img = t.lay1.out_spectra_words, n = t.P->info.n;
-    std::vector<CopyPool::Job> jobs;
-    for (uint32_t b = 0; b < G; b++) {
-        const fdsc_request& r = ln.batch[b].r;
-        jobs.push_back({ln.h_xA + b * in_img, r.xA, in_img * 4});
-        jobs.push_back({ln.h_xB + b * in_img, r.xB, in_img * 4});
-        ln.h_seeds[b] = r.enc_seed;
-        ln.h_seeds[G + b] = r.mask_seed;
-    }
-    S->copies->run(jobs);
     cudaStream_t s = ln.stream, s_mask = ln.side[0], s_ct = ln.side[1], s_rec = ln.side[2];
     // seeds and keys first: the producers that need no share start on them
-    RT_TRY(cudaMemcpyAsync(ln.seeds, ln.h_seeds, 2 * G * 8, cudaMemcpyHostToDevice, s));
-    for (uint32_t b = 0; b < G; b++)
-        RT_TRY(cudaMemcpyAsync(ln.keys + b * n, t.keys + (uint64_t)ln.batch[b].r.key * n, n * 8, cudaMemcpyDeviceToDevice,
-                               s));
+    RT_TRY(cudaMemcpyAsync(ln.seeds, ln.h_seeds, 3 * G * 8, cudaMemcpyHostToDevice, s));
+    const u64 kb = ((u64)G * n + 255) / 256;
+    gather_keys_kernel<<<(u32)(kb < 608 ? kb : 608), 256, 0, s>>>(t.keys, ln.seeds + 2 * G, G, (u32)n, ln.keys);
+    RT_TRY(cudaGetLastError());
     RT_TRY(cudaEventRecord(ln.ev_seed, s));
     // Bob: HomShare mask, then his output share (INTT2D of s_B) and its copy out
     RT_TRY(cudaStreamWaitEvent(s_mask, ln.ev_seed, 0));
@@ -598,6 +603,7 @@ int launch_batch(fdsc_server* S, Lane& ln) {
     RT_TRY(launch_constants(P, D, ln.keys, n, 0, ln.seeds, ln.ct, s_ct));
     RT_TRY(cudaEventRecord(ln.ev_ct, s_ct));
     // Bob: HomRec plaintext from his share
+    RT_TRY(cudaStreamWaitEvent(s_rec, ln.ev_seed, 0));
     RT_TRY(cudaMemcpyAsync(ln.xB, ln.h_xB, G * in_img * 4, cudaMemcpyHostToDevice, s_rec));
     RT_TRY(launch_share(P, D, ln.xB, ln.R, false, s_rec));
     RT_TRY(cudaEventRecord(ln.ev_R, s_rec));
@@ -607,18 +613,75 @@ int launch_batch(fdsc_server* S, Lane& ln) {
     RT_TRY(cudaStreamWaitEvent(s, ln.ev_ct, 0));
     RT_TRY(cudaStreamWaitEvent(s, ln.ev_R, 0));
     RT_TRY(cudaStreamWaitEvent(s, ln.ev_mask, 0));
-    if (t.Ptc && D.GB >= kServerTensorMinImages) {
+    *tensor = t.Ptc && D.GB >= kServerTensorMinImages;
+    if (*tensor)
         RT_TRY(launch_homconv_tc(P, D, ln.ct, ln.A, ln.R, t.Ptc, ln.M, ln.ct_out, s));
-        S->tensor_batches++;
-    } else {
+    else
         RT_TRY(launch_homconv_v(P, D, ln.ct, ln.A, ln.R, t.Phat, ln.M, ln.ct_out, t.variant, s));
-    }
     RT_TRY(launch_decrypt_share(P, D, ln.keys, n, ln.ct_out, ln.yA, s));
     RT_TRY(cudaMemcpyAsync(ln.h_yA, ln.yA, G * out_img * 4, cudaMemcpyDeviceToHost, s));
     // the batch is done when both output shares are on the host
     RT_TRY(cudaStreamWaitEvent(s, ln.ev_yB, 0));
-    RT_TRY(cudaEventRecord(ln.done, s));
-    (void)lay;
+    return FDSC_OK;
+}
+
+// Records every (type, batch size) a lane can run into a graph, after one
+// direct run per type at the smallest and largest batch (zero inputs) so
+// that every kernel's attributes are set outside the capture.
+int record_lane_graphs(fdsc_server* S, Lane& ln) {
+    const uint32_t B = S->cfg.max_batch;
+    memset(ln.h_xA, 0, B * S->max_in * 4);
+    memset(ln.h_xB, 0, B * S->max_in * 4);
+    memset(ln.h_seeds, 0, 3 * (size_t)B * 8);
+    bool tensor = false;
+    for (uint32_t type = 0; type < S->types.size(); type++)
+        for (uint32_t G : {1u, B}) {
+            int rc = record_batch(S, ln, type, G, &tensor);
+            if (rc) return rc;
+        }
+    for (cudaStream_t st : ln.side) RT_TRY(cudaStreamSynchronize(st));
+    RT_TRY(cudaStreamSynchronize(ln.stream));
+    ln.graphs.assign(S->types.size() * (size_t)B, nullptr);
+    ln.graph_tensor.assign(ln.graphs.size(), 0);
+    for (uint32_t type = 0; type < S->types.size(); type++)
+        for (uint32_t G = 1; G <= B; G++) {
+            RT_TRY(cudaStreamBeginCapture(ln.stream, cudaStreamCaptureModeThreadLocal));
+            int rc = record_batch(S, ln, type, G, &tensor);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(ln.stream, &g);
+            if (rc || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return rc ? rc : fdsc_set_error(FDSC_ERR_CUDA, "server capture: %s", cudaGetErrorString(e));
+            }
+            const size_t k = (size_t)type * B + (G - 1);
+            e = cudaGraphInstantiate(&ln.graphs[k], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fdsc_set_error(FDSC_ERR_CUDA, "server instantiate: %s", cudaGetErrorString(e));
+            ln.graph_tensor[k] = tensor;
+        }
+    return FDSC_OK;
+}
+
+// Launches one batch on a lane (worker thread, lock NOT held): the requests'
+// shares into pinned staging, then the batch's graph.
+int launch_batch(fdsc_server* S, Lane& ln) {
+    const ServerType& t = S->types[ln.type];
+    const uint32_t G = (uint32_t)ln.batch.size();
+    const uint64_t in_img = t.lay1.in_spectra_words;
+    std::vector<CopyPool::Job> jobs;
+    for (uint32_t b = 0; b < G; b++) {
+        const fdsc_request& r = ln.batch[b].r;
+        jobs.push_back({ln.h_xA + b * in_img, r.xA, in_img * 4});
+        jobs.push_back({ln.h_xB + b * in_img, r.xB, in_img * 4});
+        ln.h_seeds[b] = r.enc_seed;
+        ln.h_seeds[G + b] = r.mask_seed;
+        ln.h_seeds[2 * G + b] = r.key;
+    }
+    S->copies->run(jobs);
+    const size_t k = (size_t)ln.type * S->cfg.max_batch + (G - 1);
+    RT_TRY(cudaGraphLaunch(ln.graphs[k], ln.stream));
+    RT_TRY(cudaEventRecord(ln.done, ln.stream));
+    if (ln.graph_tensor[k]) S->tensor_batches++;
     return FDSC_OK;
 }
 
@@ -648,8 +711,14 @@ void finish_batch(fdsc_server* S, Lane& ln, bool ok) {
     S->cv_done.notify_all();
 }
 
+// After its last batch retires the worker keeps polling for this long before it
+// blocks: a wake-up through the condition variable costs tens of microseconds,
+// more than a request's own work on the small layer types.
+constexpr auto kIdleSpin = std::chrono::microseconds(2000);
+
 void worker_loop(fdsc_server* S) {
     cudaSetDevice(S->device);
+    auto last_active = Clock::now();
     for (;;) {
         bool any_busy = false;
         // 1. retire finished batches
@@ -718,9 +787,15 @@ void worker_loop(fdsc_server* S) {
             any_busy = true;
         }
         if (!any_busy && S->pending.empty() && !S->stop) {
-            S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            if (Clock::now() - last_active < kIdleSpin) {
+                lk.unlock();
+                std::this_thread::yield();
+            } else {
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            }
             continue;
         }
+        last_active = Clock::now();
         lk.unlock();
         // batches in flight: poll again at once (a timed sleep would add tens of
         // microseconds to every request's latency); only yield the core
@@ -801,7 +876,7 @@ extern "C" int fdsc_server_start(fdsc_server* S) {
             (rc = S->arena.alloc((void**)&ln.A, B * S->max_add * 8)) || (rc = S->arena.alloc((void**)&ln.R, B * S->max_add * 8)) ||
             (rc = S->arena.alloc((void**)&ln.ct_out, B * S->max_ct_out * 8)) ||
             (rc = S->arena.alloc((void**)&ln.M, B * S->max_mask * 8)) || (rc = S->arena.alloc((void**)&ln.keys, B * S->max_n * 8)) ||
-            (rc = S->arena.alloc((void**)&ln.seeds, 2 * B * 8)))
+            (rc = S->arena.alloc((void**)&ln.seeds, 3 * B * 8)))
             return rc;
         if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&ln.side[0], cudaStreamNonBlocking) != cudaSuccess ||
@@ -817,8 +892,9 @@ extern "C" int fdsc_server_start(fdsc_server* S) {
             cudaMallocHost((void**)&ln.h_xB, B * S->max_in * 4) != cudaSuccess ||
             cudaMallocHost((void**)&ln.h_yA, B * S->max_out * 4) != cudaSuccess ||
             cudaMallocHost((void**)&ln.h_yB, B * S->max_out * 4) != cudaSuccess ||
-            cudaMallocHost((void**)&ln.h_seeds, 2 * B * 8) != cudaSuccess)
+            cudaMallocHost((void**)&ln.h_seeds, 3 * B * 8) != cudaSuccess)
             return fdsc_set_error(FDSC_ERR_CUDA, "lane setup failed");
+        if ((rc = record_lane_graphs(S, ln))) return rc;
     }
     // host copies: a quarter of the host's threads (2 to 8) besides the worker
     const unsigned hw = std::thread::hardware_concurrency();
@@ -909,6 +985,8 @@ extern "C" int fdsc_server_destroy(fdsc_server* S) {
         }
         for (cudaEvent_t ev : {ln.done, ln.ev_seed, ln.ev_mask, ln.ev_yB, ln.ev_ct, ln.ev_R})
             if (ev) cudaEventDestroy(ev);
+        for (cudaGraphExec_t g : ln.graphs)
+            if (g) cudaGraphExecDestroy(g);
         cudaFreeHost(ln.h_xA);
         cudaFreeHost(ln.h_xB);
         cudaFreeHost(ln.h_yA);
