@@ -671,7 +671,8 @@ def ntt2d_sweep(F, P, ls, back_to_back, args):
 def run_kernel_only(args):
     """A few launches of one part of the path, for profiler captures (no
     timing, no JSON line): `homconv` (HomConv + HomShare of the 32x32x64
-    layer on seeded random words), `homconv_tc` (the tensor-core HomConv of
+    layer on seeded random words), `homconv_b16` (the same layer at 16
+    images, the first layer of the 16-image stack), `homconv_tc` (the tensor-core HomConv of
     the 16x16x128->128 layer at 16 images), `ntt2d` (forward NTT2D of
     --planes 32x32 planes), `step` (the fused online step of that layer,
     eager) or `plan` (the 16-image stack as one autotuned plan; under a
@@ -739,7 +740,12 @@ def run_kernel_only(args):
             F.homconv_tc(P, L, ct, A1, A2, Ptc, Mh, out=out)
         torch.cuda.synchronize()
         assert F.homconv_tc_status() == 0
-    elif args.kernel_only == "homconv":
+    elif args.kernel_only in ("homconv", "homconv_b16"):
+        if args.kernel_only == "homconv_b16":
+            ls = FI.CONFIGS["cfg2"].layers[0]
+            g_c, g_b = FI.default_pack(ls, info.S)
+            L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
+            lay = F.layout(P, L)
         ct, Ph, Mh = rnd(info.q, lay.ct_in_words), rnd(info.q, lay.filter_words), rnd(info.q, lay.mask_words)
         A1, A2 = rnd(info.q, lay.n_in * ls.n), rnd(info.q, lay.n_in * ls.n)
         out = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
@@ -1067,7 +1073,7 @@ def main():
     ap.add_argument("--serve-keys", type=int, default=64)
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
-    ap.add_argument("--kernel-only", choices=["homconv", "homconv_tc", "ntt2d", "step", "plan"],
+    ap.add_argument("--kernel-only", choices=["homconv", "homconv_b16", "homconv_tc", "ntt2d", "step", "plan"],
                     help="only run --steps launches of one part of the path (for profiler captures)")
     ap.add_argument("--planes", type=int, default=65536, help="planes for --kernel-only ntt2d")
     args = ap.parse_args()
