@@ -414,7 +414,10 @@ int fdsc_server_create(const fdsc_server_config* cfg, fdsc_server** out);
  * a pointer to its key pool (device [nkeys][n]). */
 int fdsc_server_add_type(fdsc_server* s, const fdsc_params* P, const fdsc_layer* L, const int8_t* w, uint32_t fh,
                          uint32_t fw, const uint64_t* keys, uint32_t nkeys, uint32_t* type_id);
-/* Allocates the lanes' buffers and starts the scheduling thread. */
+/* Allocates the lanes' buffers, records every lane's batch of every type and
+ * size (1 .. max_batch) as a CUDA graph (after one run per type on zero
+ * inputs), and starts the scheduling thread.  Types must all be added
+ * before; FDSC_ERR_CUDA if a recording fails. */
 int fdsc_server_start(fdsc_server* s);
 /* Queues a request (thread-safe); FDSC_ERR_BUDGET if it can never fit. */
 int fdsc_server_submit(fdsc_server* s, const fdsc_request* r, uint64_t* ticket);
