@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -88,13 +89,13 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu, self.proc, self.path = gpu_index, None, None
+    def __init__(self, gpu_index: int, out_dir: str):
+        self.gpu, self.proc, self.path, self.out_dir = gpu_index, None, None, out_dir
 
     def start(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+            os.makedirs(self.out_dir, exist_ok=True)
+            self.path = os.path.join(self.out_dir, f"clocks_bench_{os.getpid()}.csv")
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
@@ -914,7 +915,7 @@ def run_gpu(args, rank, local_rank, world):
         ev[-1].record()
         return ev
 
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(local_rank, args.clocks_dir or tempfile.gettempdir())
     clocks.start()
     time.sleep(0.3)
     barrier()
@@ -1073,6 +1074,7 @@ def main():
     ap.add_argument("--serve-keys", type=int, default=64)
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--clocks-dir", default="", help="where the raw nvidia-smi clock samples go (default: a temp dir)")
     ap.add_argument("--kernel-only", choices=["homconv", "homconv_b16", "homconv_tc", "ntt2d", "step", "plan"],
                     help="only run --steps launches of one part of the path (for profiler captures)")
     ap.add_argument("--planes", type=int, default=65536, help="planes for --kernel-only ntt2d")
