@@ -35,7 +35,7 @@ def negacyclic_schoolbook(a, b, m):
     return [v % m for v in out]
 
 
-@pytest.mark.parametrize("p", [65537, 12289])
+@pytest.mark.parametrize("p", [65537, 12289, 147457, 786433])
 @pytest.mark.parametrize("H,W", [(4, 4), (8, 16), (16, 8), (2, 32)])
 def test_ntt2d_tier1_equals_definition(p, H, W):
     x = np.random.default_rng(H * W).integers(0, p, (3, H, W))
@@ -45,7 +45,7 @@ def test_ntt2d_tier1_equals_definition(p, H, W):
     assert np.array_equal(X0, X1)
 
 
-@pytest.mark.parametrize("p", [65537, 12289])
+@pytest.mark.parametrize("p", [65537, 12289, 147457, 786433])
 @pytest.mark.parametrize("H,W", [(8, 8), (16, 16), (32, 32), (4, 64)])
 def test_convolution_theorem(p, H, W):
     g = np.random.default_rng(3 + H)
@@ -58,7 +58,7 @@ def test_convolution_theorem(p, H, W):
     assert np.array_equal(y, cyclic_conv_bruteforce(x, w[:3, :3], p))
 
 
-@pytest.mark.parametrize("p", [65537, 12289])
+@pytest.mark.parametrize("p", [65537, 12289, 147457, 786433])
 def test_ntt2d_closed_forms_and_inverse(p):
     H, W = 16, 32
     delta = np.zeros((H, W), np.uint32)
@@ -82,7 +82,8 @@ def test_ntt2d_closed_forms_and_inverse(p):
     assert pow(r, H, p) == 1 and pow(r, H // 2, p) == p - 1
 
 
-@pytest.mark.parametrize("n,p", [(64, 65537), (256, 65537), (1024, 12289), (4096, 12289)])
+@pytest.mark.parametrize("n,p", [(64, 65537), (256, 65537), (1024, 12289), (4096, 12289), (128, 147457),
+                                 (2048, 147457), (256, 786433)])
 def test_slot_transform_is_ring_homomorphism(n, p):
     P = O.params(n, p)
     S = P.S
@@ -97,7 +98,7 @@ def test_slot_transform_is_ring_homomorphism(n, p):
     assert np.array_equal(O.slot_decode(P, O.slot_encode(P, s)), s)
 
 
-@pytest.mark.parametrize("n,p", [(64, 65537), (128, 12289)])
+@pytest.mark.parametrize("n,p", [(64, 65537), (128, 12289), (64, 147457), (128, 786433)])
 def test_slot_order_is_bit_reversed_roots(n, p):
     P = O.params(n, p)
     S = P.S
@@ -114,9 +115,9 @@ def test_slot_order_is_bit_reversed_roots(n, p):
         assert [int(v) for v in O.slot_decode(P, mono)] == roots
 
 
-@pytest.mark.parametrize("n", [16, 64, 256])
-def test_ntt_q_ring_product_and_tiers(n):
-    P = O.params(n, 65537)
+@pytest.mark.parametrize("n,p", [(16, 65537), (64, 65537), (256, 65537), (64, 12289), (64, 147457), (64, 786433)])
+def test_ntt_q_ring_product_and_tiers(n, p):
+    P = O.params(n, p)
     q = P.q
     g = np.random.default_rng(n)
     a = [int(v) for v in g.integers(0, 2**62, n, dtype=np.uint64) % np.uint64(q)]
