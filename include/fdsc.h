@@ -366,7 +366,12 @@ typedef struct fdsc_plan fdsc_plan;
 int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, uint32_t flags, void* stream, fdsc_plan** out);
 /* One launch of the recorded graph: every layer's online path. */
 int fdsc_plan_launch(fdsc_plan* plan, void* stream);
+/* Layer i's packing (g_c, g_b), HomConv variant (7: tensor cores), whether
+ * it runs the fused kernels, and the tuner's candidates and best time;
+ * FDSC_ERR_ARG if i >= count. */
 int fdsc_plan_layer_info_get(const fdsc_plan* plan, uint32_t i, fdsc_plan_layer_info* out);
+/* Frees the plan's buffers, streams, events and graph; its launches must have
+ * completed (synchronize their stream first). */
 int fdsc_plan_destroy(fdsc_plan* plan);
 
 /* ---------------------------------------------------------------------- */
@@ -408,6 +413,8 @@ typedef struct {
 
 typedef struct fdsc_server fdsc_server;
 
+/* A server for cfg on the current device (max_batch >= 1 and lanes >= 1,
+ * FDSC_ERR_ARG otherwise); device memory is taken at fdsc_server_start. */
 int fdsc_server_create(const fdsc_server_config* cfg, fdsc_server** out);
 /* Registers a layer type (B is ignored; fused shapes only: H W <= S,
  * 8 <= H, W): prepares its filter plaintexts from device weights w and keeps
@@ -423,6 +430,9 @@ int fdsc_server_start(fdsc_server* s);
 int fdsc_server_submit(fdsc_server* s, const fdsc_request* r, uint64_t* ticket);
 /* Waits at most timeout_ms for a ticket; FDSC_ERR_TIMEOUT if not done. */
 int fdsc_server_wait(fdsc_server* s, uint64_t ticket, uint32_t timeout_ms, double* latency_us);
+/* Counters, and latencies from submission until both output shares are in
+ * the caller's buffers, over the requests completed so far; returns the
+ * server's first failure, if any. */
 int fdsc_server_stats_get(fdsc_server* s, fdsc_server_stats* out);
 /* Stops the thread after the batches in flight finish and frees everything. */
 int fdsc_server_destroy(fdsc_server* s);
