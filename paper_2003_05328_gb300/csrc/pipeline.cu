@@ -9,7 +9,9 @@
 //                      NTT_q: the plaintext that encryption (Eq. 1) or
 //                      HomRec (Eq. 3) adds to c1;
 //   decrypt_share      decryption, slot decode, channel-block fold and
-//                      INTT2D in one pass: ct -> Alice's spatial share s_A.
+//                      INTT2D in one pass: ct -> Alice's spatial share s_A;
+//   decrypt_share_pair the same for a single image on a cluster of two CTAs
+//                      per ciphertext, one coefficient parity each.
 //
 // Because NTT_q is linear, Enc(m) = constants + (0, NTT_q(Delta m)) and
 // HomRec adds (0, NTT_q(Delta m_B)): the composed ciphertext is word for word
