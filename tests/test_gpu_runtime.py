@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+import fdsc_inputs as FI
 from fdsc_harness import dev, u32, u64
 from oracle import oracle as O
 
@@ -177,6 +178,52 @@ def test_server_large_batches_use_the_tensor_cores(F):
         ref = O.round_trip(OP, O.layer(OP, 1, Ci, Co, H, W), r["xA"][None], r["xB"][None], w,
                            key_seeds[r["key"]], r["es"], r["ss"])
         assert np.array_equal(r["yA"], ref["yA"][0]) and np.array_equal(r["yB"], ref["yB"][0])
+    P.close()
+
+
+def _served_mix_refs():
+    """The served mix's three layer types at full size, with the requests of
+    the full-size server test and the oracle's shares for each alone."""
+    c = FI.CONFIGS["cfg3"]
+    OP = O.params(2048, 65537)
+    key_seeds = [31, 32, 33]
+    types = []
+    for ti, ls in enumerate(c.layers):
+        xA, xB = FI.shares(ls, c.cid, ti)
+        types.append((ls, FI.weights(ls, c.cid, ti), np.ascontiguousarray(xA[0], dtype=np.uint32),
+                      np.ascontiguousarray(xB[0], dtype=np.uint32)))
+    reqs = []
+    for i, t in enumerate([1, 1, 1, 0, 2, 1, 2]):
+        ls, w, xA, xB = types[t]
+        ref = O.round_trip(OP, O.layer(OP, 1, ls.Ci, ls.Co, ls.H, ls.W), xA[None], xB[None], w, key_seeds[i % 3],
+                           100 + i, 200 + i)
+        reqs.append(dict(t=t, key=i % 3, es=100 + i, ss=200 + i, xA=xA, xB=xB, ref=ref,
+                         yA=np.zeros((ls.Co, ls.H, ls.W), np.uint32), yB=np.zeros((ls.Co, ls.H, ls.W), np.uint32)))
+    return c, key_seeds, types, reqs
+
+
+def test_server_served_mix_types_at_full_size(F):
+    """The served mix's layer types at their full sizes (28x28 padded to
+    32x32, 1 -> 16, 5x5; 32x32x64 -> 64, 3x3; 16x16x128 -> 128, 3x3) through
+    the server as the bench runs it (batches of up to 16 on 4 lanes, every
+    request its own key and seeds): each result is the oracle's pair of
+    shares for that request alone."""
+    c, key_seeds, types, reqs = _served_mix_refs()
+    P = F.Params(2048, 65537, max_T=64)
+    keys = torch.stack([F.keygen(P, k) for k in key_seeds]).reshape(-1)
+    S = F.Server(hbm_budget_bytes=c.extra["hbm_budget_bytes"], max_batch=16, lanes=4)
+    ids = []
+    for ls, w, _, _ in types:
+        g_c, _ = FI.default_pack(ls, P.info.S)
+        ids.append(S.add_type(P, F.LayerSpec(1, ls.Ci, ls.Co, ls.H, ls.W, g_c, 1), dev(w, np.int8), keys))
+    S.start()
+    tickets = [S.submit(ids[r["t"]], r["key"], r["es"], r["ss"], r["xA"], r["xB"], r["yA"], r["yB"]) for r in reqs]
+    for tk in tickets:
+        assert S.wait(tk) > 0
+    assert S.stats().completed == len(reqs)
+    S.close()
+    for r in reqs:
+        assert np.array_equal(r["yA"], r["ref"]["yA"][0]) and np.array_equal(r["yB"], r["ref"]["yB"][0]), r["t"]
     P.close()
 
 
