@@ -1,7 +1,9 @@
-"""The binding's ctypes structures have the C ABI's layout (CPU only): a
-small C program compiled against include/fdsc.h prints each structure's size
-and the offset of every field the binding declares, and they must equal
-what ctypes computes.  A field the header does not have fails to compile."""
+"""The binding agrees with the C ABI (CPU only).  Structures: a small C
+program compiled against include/fdsc.h prints each structure's size and the
+offset of every field the binding declares, and they must equal what ctypes
+computes (a field the header does not have fails to compile).  Functions:
+every prototype in the header has the binding's parameter count, and each
+parameter the same kind and width."""
 import ctypes as C
 import os
 import shutil
@@ -37,3 +39,46 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, ".")] == C.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def _prototypes():
+    """name -> (return type, [parameter declarations]) for every function the header declares."""
+    import re
+
+    with open(os.path.join(ROOT, "include", "fdsc.h")) as f:
+        text = re.sub(r"/\*.*?\*/", " ", f.read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(int|const\s+char\s*\*)\s*(fdsc_\w+)\s*\(([^)]*)\)\s*;", text):
+        ret, name, params = m.groups()
+        ps = [] if params.strip() in ("", "void") else [" ".join(p.split()) for p in params.split(",")]
+        out[name] = (ret, ps)
+    return out
+
+
+def _c_kind(decl: str) -> str:
+    if "*" in decl:
+        return "ptr"
+    ty = decl.replace("const ", "").split()[0]
+    return {"uint32_t": "u32", "uint64_t": "u64", "size_t": "u64", "int": "i32", "double": "f64"}[ty]
+
+
+def _py_kind(t) -> str:
+    if t is C.c_void_p or t is C.c_char_p or (isinstance(t, type) and issubclass(t, C._Pointer)):
+        return "ptr"
+    return {C.sizeof(C.c_uint32): "u32", C.sizeof(C.c_uint64): "u64"}[C.sizeof(t)] if t in (
+        C.c_uint32, C.c_uint64) else {C.c_int: "i32", C.c_double: "f64"}[t]
+
+
+def test_binding_signatures_match_the_header():
+    """Every function the binding declares exists in fdsc.h with the same
+    number of parameters, and each parameter has the same width and kind
+    (pointer, 32- or 64-bit unsigned, int, double)."""
+    protos = _prototypes()
+    assert set(protos) == set(F._SIGS)
+    for name, (res, args) in F._SIGS.items():
+        assert name in protos, name
+        ret, params = protos[name]
+        assert (ret == "int") == (res is C.c_int), name
+        assert len(params) == len(args), (name, params, args)
+        for i, (decl, t) in enumerate(zip(params, args)):
+            assert _c_kind(decl) == _py_kind(t), (name, i, decl, t)
