@@ -3,7 +3,8 @@ program compiled against include/fdsc.h prints each structure's size and the
 offset of every field the binding declares, and they must equal what ctypes
 computes (a field the header does not have fails to compile).  Functions:
 every prototype in the header has the binding's parameter count, and each
-parameter the same kind and width."""
+parameter the same kind and width; NULL handles are refused before any
+device work."""
 import ctypes as C
 import os
 import shutil
@@ -82,3 +83,24 @@ def test_binding_signatures_match_the_header():
         assert len(params) == len(args), (name, params, args)
         for i, (decl, t) in enumerate(zip(params, args)):
             assert _c_kind(decl) == _py_kind(t), (name, i, decl, t)
+
+
+def test_null_handles_are_refused_before_any_device_work():
+    """Every call whose first parameter is a params, plan or server handle (or
+    the plan's layer list, or the server's config) refuses NULL and zero
+    arguments with FDSC_ERR_ARG and a message, touching no device (this test
+    runs where there is none); the destroy calls accept NULL, as free() does."""
+    lib = F.lib()
+    handles = ("fdsc_params", "fdsc_plan", "fdsc_server")
+    seen = 0
+    for name, (ret, params) in sorted(_prototypes().items()):
+        if not params or not any(h in params[0] for h in handles):
+            continue
+        seen += 1
+        _, args = F._SIGS[name]
+        rc = getattr(lib, name)(*[None if _py_kind(t) == "ptr" else 0 for t in args])
+        if name.endswith("_destroy"):
+            assert rc == F.FDSC_OK, name
+        else:
+            assert rc == -1 and lib.fdsc_last_error(), name
+    assert seen >= 35
