@@ -139,6 +139,38 @@ def test_layer_variants_bit_exact(F, args):
     _check_layer(F, **args)
 
 
+def _sweep_cases():
+    """A seeded sweep of small layers over the property ranges: n in {64,
+    128, 256}, H, W in {4, 8, 16} with H W <= S (S = n for these n and both
+    primes), Ci, Co in {1, 2, 3, 5}, 1 to 3 images, and random packings of
+    channel and image blocks."""
+    g = np.random.default_rng(2024)
+    cases = []
+    while len(cases) < 12:
+        n, p = int(g.choice([64, 128, 256])), int(g.choice([65537, 12289]))
+        H, W = int(g.choice([4, 8, 16])), int(g.choice([4, 8, 16]))
+        if H * W > n:
+            continue
+        Ci, Co, B = int(g.choice([1, 2, 3, 5])), int(g.choice([1, 2, 3, 5])), int(g.integers(1, 4))
+        blocks = n // (H * W)
+        g_c = int(g.integers(1, min(blocks, Ci) + 1))
+        g_b = int(g.integers(1, blocks // g_c + 1))
+        cases.append(dict(n=n, p=p, B=B, Ci=Ci, Co=Co, H=H, W=W, g_c=g_c, g_b=g_b))
+    return cases
+
+
+@pytest.mark.parametrize("i,case", list(enumerate(_sweep_cases())))
+def test_small_layer_sweep_with_edge_values(F, i, case):
+    """Every stage word-exact on the sweep, with shares drawn from the edge
+    values {0, 1, p - 1} and 3x3 weights from {-8, -1, 0, 7}."""
+    g = np.random.default_rng(100 + i)
+    n, p, B, Ci, Co, H, W = (case[k] for k in ("n", "p", "B", "Ci", "Co", "H", "W"))
+    xA = g.choice(np.array([0, 1, p - 1], np.uint32), (B, Ci, H, W))
+    xB = g.choice(np.array([0, 1, p - 1], np.uint32), (B, Ci, H, W))
+    w = g.choice(np.array([-8, -1, 0, 7], np.int8), (Co, Ci, 3, 3))
+    _check_layer(F, n, p, B, Ci, Co, H, W, 3, g_c=case["g_c"], g_b=case["g_b"], seed=200 + i, xA=xA, xB=xB, w=w)
+
+
 @pytest.mark.parametrize("layer", [0, 1, 2])
 def test_batched_stack_layers_reduced_batch_bit_exact(F, layer):
     ls = FI.CONFIGS["cfg2"].layers[layer]
