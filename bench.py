@@ -1005,7 +1005,7 @@ def run_gpu(args, rank, local_rank, world):
                 "hbm": hbm_side, "alu": alu_side}
     useful_macs = 2 * ls.Co * ls.Ci * ls.H * ls.W * ls.B
     cpu = cpu_all = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # the oracle baseline: rank 0 of a single-GPU run
         per_layer, sample = oracle_online_sample(args.cpu_seconds)
         st = oracle_online_sample.stages_ms
         cpu = {"value": 1.0 / per_layer, "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": sample,
