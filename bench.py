@@ -39,6 +39,8 @@ sys.path.insert(0, ROOT)
 import fdsc_inputs as FI  # noqa: E402
 
 METRIC = "HomConv layers/s & mod-q MAC/s at 32×32×64; p50/p99 served latency"
+PIPE_DEPTH = 2      # steps in flight in the pipelined schedule
+GRAPH_STEPS = 220   # steps recorded in one graph of the timed loop (20 rotations of the instances)
 WORKLOAD = "cfg1"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "homconv_traffic.json")
@@ -81,6 +83,26 @@ def layer_counts(ls, T, beta, GB, n, addends=2):
     per_group = 8 * ((2 + addends) * T * beta * n + 2 * ls.Co * beta * n + ls.Co * beta * n)
     macs = 2 * ls.Co * T * beta * n * GB
     return filt + GB * per_group, macs
+
+
+# the HomConv kernel behind each variant number (fdsc_set_homconv_variant)
+HOMCONV_KERNELS = {3: "homconv_kernel<1,false,2>", 4: "homconv3_kernel<0>", 10: "homconv5_kernel<8>",
+                   11: "homconv6_kernel<16>", 12: "homconv6_kernel<8>"}
+
+
+def variant_used(T, requested):
+    """The variant the library runs for T input ciphertexts (0 = its default)."""
+    if requested in (11, 12) and T <= 64:
+        return requested
+    if requested == 10 and T <= 128 and T % 4 == 0:
+        return 10
+    if requested in (3, 4):
+        return requested if T <= 256 or requested == 3 else 3
+    return 12 if T <= 64 else (4 if T <= 256 else 3)
+
+
+def homconv_kernel_name(T, requested):
+    return HOMCONV_KERNELS.get(variant_used(T, requested), "homconv variant %d" % variant_used(T, requested))
 
 
 # ------------------------------------------------------------------ clocks
@@ -239,21 +261,21 @@ def oracle_all_cores_sample(t_in_s: float, reps: int = 2):
 
 def oracle_slice_step():
     """One reference step: the oracle on a proportional slice of the bench
-    layer, scaled to the whole layer.  The input side (NTT2D, encryption,
-    HomRec) is linear in the input channels and the output side (HomConv +
-    HomShare, decryption, INTT2D x2) in the output channels, so the step times
-    Ci/8 input channels and Co/8 output channels and scales each part (about
-    40 ms of CPU work per step)."""
+    layer -- the input side (NTT2D, encryption, HomRec) for Ci/8 input
+    channels and the output side (HomConv + HomShare, decryption, INTT2D x2)
+    for Co/8 output channels.  Both sides are linear in those counts, so the
+    step is 1/8 of a layer's work.  Returns (measured wall seconds, the
+    fraction of a layer processed)."""
     from oracle import oracle as O
 
     c = FI.CONFIGS[WORKLOAD]
     ls = c.layers[0]
     P = O.params(ls.n, ls.p)
     g_c, g_b = FI.default_pack(ls, P.S)
-    ci = max(g_c, ls.Ci // 8)
+    ci, co = ls.Ci // 8, ls.Co // 8
+    assert ci % g_c == 0 and ci * ls.Co == co * ls.Ci  # the same fraction of both sides
     Lin = O.layer(P, ls.B, ci, ls.Co, ls.H, ls.W, g_c, g_b)
     Lfull = O.layer(P, ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
-    co = max(1, ls.Co // 8)
     Lout = O.layer(P, ls.B, ls.Ci, co, ls.H, ls.W, g_c, g_b)
     key = (ls.n, ls.p, ci, co)
     cache = oracle_slice_step.__dict__.setdefault("cache", {})
@@ -271,13 +293,11 @@ def oracle_slice_step():
     XA = O.ntt2d(xA, ls.p).reshape(ls.B, ci, -1)
     ct = O.encrypt(P, Lin, t_hat, XA, es)
     O.homrec(P, Lin, ct, O.ntt2d(xB, ls.p).reshape(ls.B, ci, -1))
-    b = time.perf_counter()
     out = O.homconv(P, Lout, ct_full, Phat, Mhat)
     SA, _ = O.decrypt(P, Lout, t_hat, out)
     O.ntt2d(SA.reshape(ls.B, co, ls.H, ls.W), ls.p, inverse=True)
     O.ntt2d(sB.reshape(ls.B, co, ls.H, ls.W), ls.p, inverse=True)
-    e = time.perf_counter()
-    return (b - a) * ls.Ci / ci + (e - b) * ls.Co / co
+    return time.perf_counter() - a, ci / ls.Ci
 
 
 def run_reference(args, rank, world):
@@ -286,21 +306,23 @@ def run_reference(args, rank, world):
     for _ in range(args.warmup):
         oracle_slice_step()
     t0 = time.perf_counter()
-    per = [oracle_slice_step() for _ in range(args.steps)]
-    wall = (time.perf_counter() - t0) / max(1, args.steps)
-    sec = float(np.mean(per))
+    fracs = [oracle_slice_step()[1] for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    sec = wall / max(1, args.steps)  # measured wall time of one step (a 1/8 slice of the layer)
+    frac = fracs[0]
     ls = FI.CONFIGS[WORKLOAD].layers[0]
-    value = 1.0 / sec
+    value = frac / sec  # layers of work processed per second
     sample = ("each of the %d steps: the oracle on %d of %d input channels and %d of %d output channels of the %s "
-              "layer, each side scaled to the full layer; single thread" % (args.steps, max(1, ls.Ci // 8), ls.Ci,
-                                                                           max(1, ls.Co // 8), ls.Co, WORKLOAD))
+              "layer (%.3f of a layer's work, both sides being linear in those counts); single thread; "
+              "ms_per_step is the measured wall time of one such step" %
+              (args.steps, ls.Ci // 8, ls.Ci, ls.Co // 8, ls.Co, WORKLOAD, frac))
     line = {"metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "layer": "32x32x64->64 3x3", "batch": ls.B, "n": ls.n, "p": ls.p,
                        "q_bits": 60, "l2": "cpu"},
+            "layer_fraction_per_step": frac,
             "mac_per_s": value * 2 * ls.Co * ls.Ci * ls.H * ls.W,
-            "sample_wall_ms_per_step": wall * 1e3,
             "cpu_baseline": {"value": value, "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -819,15 +841,60 @@ def run_gpu(args, rank, local_rank, world):
         d["A_rec"] = torch.empty_like(d["A_msg"])
         d["c1"] = F.encrypt_constants_seeded(P, L, d["t_hat"], es)  # the seeded form: c1 alone
         insts.append(d)
-    LAUNCHES_PER_STEP = 6
+    LAUNCHES_PER_STEP = 4  # producers, HomConv, decryption, Bob's INTT2D
     side = [torch.cuda.Stream() for _ in range(3)]
+    lanes = [torch.cuda.Stream() for _ in range(PIPE_DEPTH)]
+    lane_side = [torch.cuda.Stream() for _ in range(PIPE_DEPTH)]
 
     def step(d):
-        """One online layer.  Four independent producers run concurrently:
-        Alice's encryption constants (Enc(0)), Alice's share encoding, Bob's
-        HomRec plaintext from his share, and Bob's INTT2D of his mask share;
-        then HomConv (+ HomRec addends + HomShare) and Alice's fused
-        decryption + INTT2D."""
+        """One online layer on the current stream: Alice's encryption
+        constants and both parties' share encodings in one launch
+        (fdsc_online_produce), then HomConv (+ HomRec addends + HomShare) and
+        Alice's fused decryption + INTT2D; Bob's INTT2D of his mask share runs
+        on a side stream.  Returns an event recorded after the producers."""
+        main = torch.cuda.current_stream()
+        side[2].wait_stream(main)
+        with torch.cuda.stream(side[2]):
+            F.intt2d(P, d["sB4"], out=d["yB"])
+        F.online_produce(P, L, d["t_hat"], d["es"], d["xA"], d["xB"], d["ct"], d["A_msg"], d["A_rec"])
+        produced = torch.cuda.Event()
+        produced.record(main)
+        F.homconv_sum(P, L, d["ct"], d["A_msg"], d["A_rec"], d["Phat"], d["Mhat"], out=d["ct_out"])
+        F.decrypt_share(P, L, d["t_hat"], d["ct_out"], out=d["yA"])
+        main.wait_stream(side[2])
+        return produced
+
+    def steps_pipelined(seq):
+        """Consecutive steps (independent layers) software-pipelined over
+        PIPE_DEPTH streams: step i runs on lane i mod PIPE_DEPTH, and its
+        producers start once step i-1's producers are done, so they overlap
+        step i-1's HomConv and decryption; a lane's next step waits for its
+        previous one (at most PIPE_DEPTH steps in flight).  Every step is the
+        whole layer, in the paper's order."""
+        main = torch.cuda.current_stream()
+        for st in lanes + lane_side:
+            st.wait_stream(main)
+        prev = None
+        for i, d in enumerate(seq):
+            st, sd = lanes[i % PIPE_DEPTH], lane_side[i % PIPE_DEPTH]
+            with torch.cuda.stream(st):
+                if prev is not None:
+                    st.wait_event(prev)
+                sd.wait_stream(st)
+                with torch.cuda.stream(sd):
+                    F.intt2d(P, d["sB4"], out=d["yB"])
+                F.online_produce(P, L, d["t_hat"], d["es"], d["xA"], d["xB"], d["ct"], d["A_msg"], d["A_rec"])
+                prev = torch.cuda.Event()
+                prev.record(st)
+                F.homconv_sum(P, L, d["ct"], d["A_msg"], d["A_rec"], d["Phat"], d["Mhat"], out=d["ct_out"])
+                F.decrypt_share(P, L, d["t_hat"], d["ct_out"], out=d["yA"])
+                st.wait_stream(sd)
+        for st in lanes:
+            main.wait_stream(st)
+
+    def step_4streams(d):
+        """The previous form of the step: the four producers as separate
+        launches on four streams, each step after the one before."""
         main = torch.cuda.current_stream()
         for st in side:
             st.wait_stream(main)
@@ -860,11 +927,24 @@ def run_gpu(args, rank, local_rank, world):
     def homconv_seeded_only(d):
         F.homconv_seeded(P, L, d["es"], d["c1"], d["A_msg"], d["A_rec"], d["Phat"], d["Mhat"], out=d["ct_out"])
 
+    # programmatic dependent launch for the online kernels recorded below:
+    # each may start while its predecessor in the stream drains
+    F.set_launch_overlap(True)
     for _ in range(max(1, args.warmup)):
         for d in insts:
             step(d)
             step_unfused(d)
     torch.cuda.synchronize()
+    # the pipelined schedule gives every step's words exactly (checked on two instances)
+    ref = [(d["yA"].clone(), d["yB"].clone()) for d in insts[:2]]
+    for d in insts[:2]:
+        d["yA"].zero_()
+        d["yB"].zero_()
+    steps_pipelined(insts)
+    torch.cuda.synchronize()
+    pipelined_ok = all(torch.equal(d["yA"], a) and torch.equal(d["yB"], b) for d, (a, b) in zip(insts, ref))
+    if not pipelined_ok:
+        raise RuntimeError("pipelined steps differ from single steps")
     s = torch.cuda.Stream()
 
     def capture(fn):
@@ -878,17 +958,31 @@ def run_gpu(args, rank, local_rank, world):
         torch.cuda.current_stream().wait_stream(s)
         return gr
 
+    # exactly K steps: G = min(K, GRAPH_STEPS) consecutive steps (cycling over the
+    # R instances) recorded in one pipelined graph, replayed K // G times, then a
+    # graph of the remaining K mod G steps
+    G = max(1, min(args.steps, GRAPH_STEPS))
+    g_main = capture(lambda: steps_pipelined([insts[i % R] for i in range(G)]))
+    rem = args.steps % G
+    g_rem = capture(lambda: steps_pipelined([insts[i % R] for i in range(rem)])) if rem else None
     g_step = [capture(lambda d=d: step(d)) for d in insts]
-    # the same steps, R of them (one per instance, in order) recorded in one graph
-    g_step_r = capture(lambda: [step(d) for d in insts])
+    # each instance's producers alone, and followed by its HomConv (one graph
+    # each): the difference is the time HomConv adds after the producers' join
+    g_prod = [capture(lambda d=d: F.online_produce(P, L, d["t_hat"], d["es"], d["xA"], d["xB"], d["ct"], d["A_msg"],
+                                                   d["A_rec"])) for d in insts]
+    g_prod_hc = [capture(lambda d=d: (F.online_produce(P, L, d["t_hat"], d["es"], d["xA"], d["xB"], d["ct"],
+                                                       d["A_msg"], d["A_rec"]), homconv_only(d))) for d in insts]
+    # the rest is recorded without the early launch: kernels measured alone
+    F.set_launch_overlap(False)
+    # the four-stream step of the unpipelined form, R steps per graph, each after the one before
+    g_4s = capture(lambda: [step_4streams(d) for d in insts])
     g_unfused = [capture(lambda d=d: step_unfused(d)) for d in insts]
     # HomConv alone: one graph of R launches, one per instance, back to back
     g_hc = capture(lambda: [homconv_only(d) for d in insts])
     g_hc_warm = capture(lambda: [homconv_only(insts[0]) for _ in insts])
     g_hc_seeded = capture(lambda: [homconv_seeded_only(d) for d in insts])
     for _ in range(args.warmup):
-        for gr in g_step:
-            gr.replay()
+        g_main.replay()
         g_hc.replay()
     torch.cuda.synchronize()
     sleep_cycles = int(60e6)  # about 30 ms at 2 GHz
@@ -919,22 +1013,31 @@ def run_gpu(args, rank, local_rank, world):
     clocks.start()
     time.sleep(0.3)
     barrier()
-    # exactly K steps: K // R replays of the graph of R steps (one per instance, in
-    # order), then K mod R single-step graphs
-    seq = [g_step_r] * (args.steps // R) + g_step[:args.steps % R]
+    seq = [g_main] * (args.steps // G) + ([g_rem] if g_rem is not None else [])
     ev = back_to_back(seq, len(seq))
     barrier()
     total_ms = ev[0].elapsed_time(ev[-1])
-    # per-step distribution: a shorter pass with an event at every boundary
+    # per-step latency: one step alone per graph, an event at every boundary
     # (the events themselves add a few microseconds per step)
     ev_d = back_to_back(g_step, min(args.steps, 1000), every=1)
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev_d[:-2], ev_d[1:-1])]
-    # the same steps with one graph launch per step, for comparison
-    n_one = min(args.steps, 1000)
-    ev_1 = back_to_back(g_step, n_one)
+    # the unpipelined four-stream step, R steps per graph launch
+    n_4s = max(1, min(args.steps, 2200) // R)
+    ev_4 = back_to_back([g_4s], n_4s)
     torch.cuda.synchronize()
-    one_graph_ms = ev_1[0].elapsed_time(ev_1[-1]) / n_one
+    four_stream_ms = ev_4[0].elapsed_time(ev_4[-1]) / (n_4s * R)
+    # producers alone vs producers followed by HomConv, one instance per graph
+    # launch (rotated: cold filters), an event at every boundary; the median
+    # difference is the time HomConv adds after the producers' join
+    n_pj = max(2 * R, min(args.steps, 1100))
+    ev_p = back_to_back(g_prod, n_pj, every=1)
+    ev_ph = back_to_back(g_prod_hc, n_pj, every=1)
+    torch.cuda.synchronize()
+    t_p = [a.elapsed_time(b) for a, b in zip(ev_p[:-2], ev_p[1:-1])]
+    t_ph = [a.elapsed_time(b) for a, b in zip(ev_ph[:-2], ev_ph[1:-1])]
+    prod_ms = float(np.median(t_p))
+    post_join_ms = float(np.median(t_ph)) - prod_ms
 
     # the step-by-step path, for comparison
     n_unfused = min(args.steps, 600)
@@ -997,12 +1100,22 @@ def run_gpu(args, rank, local_rank, world):
                 "peak_source": "measured here (fdsc_calibrate: register-resident loop-carried chains of HomConv's "
                                "exact 60x60->128-bit multiply-accumulate on every SM)"}
     main = hbm_side if bound == "hbm" else alu_side
-    roofline = {"kernel": "homconv_kernel (homconv_sum: HomRec addends + HomConv + HomShare)", "bound": bound,
+    pj_us = post_join_ms * 1e3
+    roofline = {"kernel": "%s (homconv_sum, variant %d: HomRec addends + HomConv + HomShare)"
+                          % (homconv_kernel_name(lay.T, args.homconv_variant), variant_used(lay.T, args.homconv_variant)),
+                "bound": bound,
                 "achieved": main["achieved"], "peak": main["peak"], "peak_source": main["peak_source"],
                 "unit": main["unit"], "frac": main["frac"], "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
                 "macs_per_launch": macs, "launch_us": hc_avg * 1e3,
                 "timing": "%d launches back to back over the %d instances (cold), CUDA events" % (hc_reps * R, R),
-                "hbm": hbm_side, "alu": alu_side}
+                "hbm": hbm_side, "alu": alu_side,
+                "after_producers": {
+                    "us": pj_us, "achieved_GB_per_s": alg_bytes / (pj_us * 1e-6) / 1e9,
+                    "frac_of_hbm": alg_bytes / (pj_us * 1e-6) / 1e9 / peak,
+                    "producers_us": prod_ms * 1e3,
+                    "definition": "time HomConv adds after the producers' join: median time of a one-instance "
+                                  "[online_produce -> homconv_sum] graph minus that of an [online_produce] graph "
+                                  "(programmatic dependent launch on, instances rotated: cold filters)"}}
     useful_macs = 2 * ls.Co * ls.Ci * ls.H * ls.W * ls.B
     cpu = cpu_all = None
     if not args.no_cpu_baseline and world == 1:  # the oracle baseline: rank 0 of a single-GPU run
@@ -1021,11 +1134,14 @@ def run_gpu(args, rank, local_rank, world):
                    "l2": "inputs larger than L2: %d independent instances of the layer (%d MiB; L2 %d MiB) "
                          "rotated step by step, each step's inputs last read %d steps earlier"
                          % (R, R * inst_bytes >> 20, l2 >> 20, R - 1),
-                   "step": "[encrypt_constants | encode_share(x_A) | encode_share(x_B) | intt2d(s_B)] -> "
-                           "homconv_sum (HomRec + HomConv + HomShare) -> decrypt_share (4 streams); the R "
-                           "instances' steps recorded in order in one CUDA graph (each step waits for the one "
-                           "before), K steps timed back to back (K // R such graphs, then K mod R one-step graphs); "
-                           "per-step p50/p99 from one-step graphs with an event at every boundary"},
+                   "step": "online_produce (encryption constants | encode_share(x_A) | encode_share(x_B), one "
+                           "launch) -> homconv_sum (HomRec + HomConv + HomShare) -> decrypt_share, intt2d(s_B) on a "
+                           "side stream, programmatic dependent launch; consecutive steps (independent layers) "
+                           "pipelined over %d streams (step i's producers after step i-1's, overlapping its HomConv "
+                           "and decryption); K steps timed back to back as %d-step graphs (K // %d of them, then one "
+                           "of K mod %d); per-step p50/p99 from one step alone per graph with an event at every "
+                           "boundary" % (PIPE_DEPTH, G, G, G),
+                   "homconv_variant": variant_used(lay.T, args.homconv_variant)},
         "mac_per_s": value * 2 * ls.Co * ls.Ci * ls.H * ls.W,
         "homconv_layers_per_s": ls.B / (hc_avg * 1e-3),
         "homconv_mac_per_s": macs / (hc_avg * 1e-3),
@@ -1034,9 +1150,10 @@ def run_gpu(args, rank, local_rank, world):
                            "note": "seeded input ciphertexts: c1 read, c0 drawn again from the encryption seed"},
         "useful_macs_per_layer": useful_macs // ls.B,
         "step_ms_p50": float(np.percentile(step_ms, 50)), "step_ms_p99": float(np.percentile(step_ms, 99)),
-        "step_ms_distribution": "%d steps with an event at every boundary" % len(step_ms),
+        "step_ms_distribution": "%d single steps (not pipelined) with an event at every boundary" % len(step_ms),
+        "pipelined_words_checked": pipelined_ok,
         "step_by_step_ms": unfused_ms,
-        "step_ms_one_graph_per_step": one_graph_ms,
+        "step_ms_unpipelined_four_streams": four_stream_ms,
         "roofline": roofline,
         "e2e": {"value": e2e_units / e2e_sec, "unit": "layers/s", "h2d_bytes_per_step": e2e["h2d"],
                 "d2h_bytes_per_step": e2e["d2h"], "requests": e2e["requests"], "p50_us": e2e["p50_us"],
@@ -1049,7 +1166,8 @@ def run_gpu(args, rank, local_rank, world):
         "serving": serving,
         "ntt2d_sweep": sweep,
         "primitive_rates": {k: {"ops_per_s": v[0], "ops_per_clk_per_sm": v[1]} for k, v in calib.items()},
-        "gpu_launches": LAUNCHES_PER_STEP * (args.steps + len(step_ms) + n_one) + 8 * n_unfused + 3 * hc_reps * R
+        "gpu_launches": LAUNCHES_PER_STEP * (args.steps + len(step_ms)) + 6 * n_4s * R + 8 * n_unfused
+                        + 3 * hc_reps * R + 3 * n_pj
                         + sum(pt["launches"] for pt in sweep["points"]),
         "homconv_variant": args.homconv_variant,
         "clocks": clk,

@@ -224,6 +224,21 @@ int fdsc_encrypt_constants(const fdsc_params* P, const fdsc_layer* L, const uint
  * H, W >= 8 (FDSC_ERR_UNSUPPORTED otherwise; use fdsc_ntt2d + fdsc_encrypt). */
 int fdsc_encode_share(const fdsc_params* P, const fdsc_layer* L, const uint32_t* x, uint64_t* A, void* stream);
 
+/* The three input-side producers of one online layer in ONE launch, with the
+ * words of the separate calls: ct <- fdsc_encrypt_constants(t_hat, seed)
+ * (Alice's RLWE constants of Eq. 1, Sec. 5.1), A <- fdsc_encode_share(xA)
+ * (her message plaintext) and R <- fdsc_encode_share(xB) (Bob's HomRec
+ * plaintext of Eq. 3); one CTA per (producer, input ciphertext).  ct:
+ * [n_in][2][n], A, R: [n_in][n], none overlapping.  P_hat and M_hat (either
+ * may be NULL) are the filter plaintexts [Co][T][beta][n] and HomShare masks
+ * [GB][Co][beta][n] of the HomConv that follows: the launch asks the L2
+ * cache to fetch them while its transforms run, so that the HomConv finds
+ * them on chip.  The kernel lets the next kernel in the stream start early
+ * (programmatic dependent launch).  Same restrictions as fdsc_encode_share. */
+int fdsc_online_produce(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, uint64_t seed,
+                        const uint32_t* xA, const uint32_t* xB, uint64_t* ct, uint64_t* A, uint64_t* R,
+                        const uint64_t* P_hat, const uint64_t* M_hat, void* stream);
+
 /* Eq. 3 (HomRec) from Bob's SPATIAL share: ct.c1 += fdsc_encode_share(xB).
  * Same restrictions as fdsc_encode_share. */
 int fdsc_homrec_share(const fdsc_params* P, const fdsc_layer* L, const uint32_t* xB, uint64_t* ct, void* stream);

@@ -215,6 +215,27 @@ extern "C" int fdsc_encode_share(const fdsc_params* P, const fdsc_layer* L, cons
     return launched(launch_share(P->dev, D, x, A, false, (cudaStream_t)stream), "encode_share");
 }
 
+extern "C" int fdsc_online_produce(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, uint64_t seed,
+                                   const uint32_t* xA, const uint32_t* xB, uint64_t* ct, uint64_t* A, uint64_t* R,
+                                   const uint64_t* P_hat, const uint64_t* M_hat, void* stream) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    DevLayer D;
+    fdsc_layout lay;
+    if ((rc = fdsc_make_layer(P->info, L, &D, &lay))) return rc;
+    if ((rc = check_fused(P, D, produce_smem_bytes(P->dev, D), "online_produce"))) return rc;
+    if ((rc = check_ptr(t_hat, "t_hat")) || (rc = check_ptr(xA, "xA")) || (rc = check_ptr(xB, "xB")) ||
+        (rc = check_ptr(ct, "ct")) || (rc = check_ptr(A, "A")) || (rc = check_ptr(R, "R")))
+        return rc;
+    if ((P_hat && (rc = check_ptr(P_hat, "P_hat"))) || (M_hat && (rc = check_ptr(M_hat, "M_hat")))) return rc;
+    const u64 cb = lay.ct_in_words * 8, ab = (u64)D.n_in * P->info.n * 8;
+    if (overlap(ct, cb, A, ab) || overlap(ct, cb, R, ab) || overlap(A, ab, R, ab))
+        return fdsc_set_error(FDSC_ERR_ARG, "ct, A and R must not overlap");
+    return launched(launch_produce(P->dev, D, t_hat, seed, xA, xB, ct, A, R, P_hat, P_hat ? lay.filter_words * 8 : 0,
+                                   M_hat, M_hat ? lay.mask_words * 8 : 0, (cudaStream_t)stream),
+                    "online_produce");
+}
+
 extern "C" int fdsc_homrec_share(const fdsc_params* P, const fdsc_layer* L, const uint32_t* xB, uint64_t* ct,
                                  void* stream) {
     int rc = check_params(P);

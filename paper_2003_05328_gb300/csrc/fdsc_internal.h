@@ -114,6 +114,7 @@ cudaError_t launch_homconv(const DevParams& P, const DevLayer& L, const u64* ct_
 cudaError_t launch_homconv_v(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
                              const u64* Phat, const u64* Mhat, u64* ct_out, int variant, cudaStream_t s);
 int homconv_default_variant(const DevLayer& L);
+int homconv_effective_variant(const DevLayer& L, int variant);
 // tensor-core HomConv (homconv_tc.cu)
 bool homconv_tc_supported(u32 n, const DevLayer& L);
 u64 filter_tc_words(u32 n, const DevLayer& L);
@@ -128,6 +129,10 @@ cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u6
                          cudaStream_t s);
 cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, const u64* ct,
                                  u32* y, cudaStream_t s);
+cudaError_t launch_produce(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 seed, const u32* xA,
+                           const u32* xB, u64* ct, u64* A, u64* R, const void* pf0, u64 pf0_bytes, const void* pf1,
+                           u64 pf1_bytes, cudaStream_t s);
+size_t produce_smem_bytes(const DevParams& P, const DevLayer& L);
 size_t share_smem_bytes(const DevParams& P, const DevLayer& L);
 size_t decrypt_share_smem_bytes(const DevParams& P, const DevLayer& L);
 cudaError_t launch_decrypt(const DevParams& P, const DevLayer& L, const u64* t_hat, const u64* ct, u32* SA,

@@ -421,15 +421,443 @@ cudaError_t launch_v3(const DevParams& P, const DevLayer& L, const u64* ct_in, c
                          jtiles, ctiles, seed, seeded);
 }
 
+// ---------------------------------------------------------------- v4: Karatsuba limb columns
+// Words below q < 2^60 split into 30-bit limbs, x = x1 2^30 + x0 and
+// w = w1 2^30 + w0, and Karatsuba's identity
+//   x w = x0 w0 + ((x0 + x1)(w0 + w1) - x0 w0 - x1 w1) 2^30 + x1 w1 2^60
+// needs three 32 x 32 -> 64-bit multiply-adds per product (the carry chain
+// needs ten 32-bit multiply steps, the plain limb columns four wide ones).
+// Over k the three column sums lo = sum x0 w0, hi = sum x1 w1 (terms below
+// 2^60) and mid = sum (x0 + x1)(w0 + w1) (terms below 2^62) live in 64-bit
+// registers whose high words move into 64-bit carry registers every 4 terms
+// (mid) or 8 terms (lo, hi), so no column overflows.  The 128-bit sum
+// lo + (mid - lo - hi) 2^30 + hi 2^60 is assembled once per output word in
+// wrapping 128-bit arithmetic -- exact, because the true sum (at most 256
+// products of words below q, plus a residue) is below 2^128 -- and reduced
+// mod q; longer sums are folded every 256 terms.
+//
+// Tiling as v3 (32 evaluation indices x 8 output channels per CTA, the input
+// tile staged in shared memory as limb pairs), with NB image groups per CTA:
+// each filter word, split once, serves the NB groups from registers.
+constexpr u32 kJ4 = 32, kW4 = 8, kThreads4 = 32 * kW4, kPF4 = 8;
+constexpr u32 kMaxStage4 = 160 * 1024;  // shared-memory cap of the staged tiles
+
+struct AccK {
+    u64 lo, lo_c, mid, mid_c, hi, hi_c;
+};
+__device__ __forceinline__ void acck_zero(AccK& a) { a.lo = a.lo_c = a.mid = a.mid_c = a.hi = a.hi_c = 0; }
+// x: limb pair (x0 | x1 << 32); w0, w1 the filter word's limbs, ws = w0 + w1
+__device__ __forceinline__ void acck_mac(AccK& a, u64 x, u32 w0, u32 w1, u32 ws) {
+    const u32 x0 = (u32)x, x1 = (u32)(x >> 32);
+    a.lo += (u64)x0 * w0;
+    a.hi += (u64)x1 * w1;
+    a.mid += (u64)(x0 + x1) * ws;
+}
+// mid < 2^32 afterwards; 4 more terms keep it below 2^32 + 4 (2^31 - 2)^2 < 2^64
+__device__ __forceinline__ void acck_norm_mid(AccK& a) {
+    a.mid_c += a.mid >> 32;
+    a.mid &= 0xFFFFFFFFull;
+}
+// lo, hi < 2^32 afterwards; 8 more terms keep them below 2^32 + 8 2^60 < 2^64
+__device__ __forceinline__ void acck_norm_lh(AccK& a) {
+    a.lo_c += a.lo >> 32;
+    a.lo &= 0xFFFFFFFFull;
+    a.hi_c += a.hi >> 32;
+    a.hi &= 0xFFFFFFFFull;
+}
+// (sum of the window's products + base) mod q
+__device__ __forceinline__ u64 acck_reduce(const AccK& a, u64 base, const DevParams& P) {
+    typedef unsigned __int128 u128;
+    const u128 lo = ((u128)a.lo_c << 32) + a.lo, hi = ((u128)a.hi_c << 32) + a.hi;
+    const u128 mid = ((u128)a.mid_c << 32) + a.mid;
+    const u128 t = lo + ((mid - lo - hi) << 30) + (hi << 60) + base;
+    return reduce128((u64)(t >> 64), (u64)t, P);
+}
+__device__ __forceinline__ u64 split30(u64 x) { return (x & kM30) | ((x >> 30) << 32); }
+
+template <int NB, bool kFold>
+__global__ void __launch_bounds__(kThreads4, NB == 1 ? 4 : 2)
+    homconv4_kernel(DevParams P, DevLayer L, const u64* __restrict__ ct_in, const u64* __restrict__ A1,
+                    const u64* __restrict__ A2, const u64* __restrict__ Phat, const u64* __restrict__ Mhat,
+                    u64* __restrict__ ct_out, u32 jtiles, u32 ctiles) {
+    extern __shared__ __align__(16) u64 xs4[];  // [NB][T][2][kJ4] limb pairs
+    u32 blk = blockIdx.x;
+    const u32 jt = blk % jtiles;
+    blk /= jtiles;
+    const u32 ct = blk % ctiles, bb0 = (blk / ctiles) * NB;
+    const u32 nJ = L.beta * P.n, T = L.T;
+    const u64 n = P.n, beta = L.beta;
+    griddep_release();
+    griddep_wait();
+    const u32 per_g = T * kJ4;
+    for (u32 e = threadIdx.x; e < NB * per_g; e += kThreads4) {
+        const u32 g = e / per_g, r = e - g * per_g, k = r / kJ4, jj = r % kJ4, J = jt * kJ4 + jj;
+        u64 x0 = 0, x1 = 0;
+        if (J < nJ && bb0 + g < L.GB) {
+            const u32 h = J >> P.logn, j = J & (P.n - 1);
+            const u64 u = ((u64)(bb0 + g) * T + k) * beta + h;
+            x0 = __ldg(ct_in + u * 2 * n + j);
+            x1 = __ldg(ct_in + u * 2 * n + n + j);
+            if (A1) x1 = addmod_q(x1, __ldg(A1 + u * n + j), P.q);
+            if (A2) x1 = addmod_q(x1, __ldg(A2 + u * n + j), P.q);
+        }
+        xs4[((g * T + k) * 2 + 0) * kJ4 + jj] = split30(x0);
+        xs4[((g * T + k) * 2 + 1) * kJ4 + jj] = split30(x1);
+    }
+    __syncthreads();
+    const u32 lane = threadIdx.x & 31, co = ct * kW4 + (threadIdx.x >> 5), J = jt * kJ4 + lane;
+    if (co >= L.Co || J >= nJ) return;
+    const u32 h = J >> P.logn, j = J & (P.n - 1);
+    const u64* wp = Phat + ((u64)co * T * beta + h) * n + j;
+    const u64 w_step = beta * n;
+
+    AccK acc[NB][2];
+    u64 base[kFold ? NB : 1][2];  // residues of the folded 256-term windows (kFold only)
+#pragma unroll
+    for (int g = 0; g < NB; g++) {
+        acck_zero(acc[g][0]);
+        acck_zero(acc[g][1]);
+    }
+#pragma unroll
+    for (int g = 0; g < (kFold ? NB : 1); g++) base[g][0] = base[g][1] = 0;
+    // a ring of kPF4 filter words in flight: the word for term k is replaced
+    // by the one for term k + kPF4 as soon as it is used
+    u64 wbuf[kPF4];
+#pragma unroll
+    for (u32 u = 0; u < kPF4; u++) wbuf[u] = u < T ? __ldg(wp + u * w_step) : 0;
+    for (u32 k0 = 0; k0 < T; k0 += kPF4) {
+#pragma unroll
+        for (u32 u = 0; u < kPF4; u++) {
+            const u32 k = k0 + u;
+            if (k < T) {
+                const u64 w = wbuf[u];
+                if (k + kPF4 < T) wbuf[u] = __ldg(wp + (k + kPF4) * w_step);
+                const u32 w0 = (u32)w & (u32)kM30, w1 = (u32)(w >> 30), ws = w0 + w1;
+#pragma unroll
+                for (int g = 0; g < NB; g++) {
+                    const u64* xg = xs4 + (((u32)g * T + k) * 2) * kJ4 + lane;
+                    acck_mac(acc[g][0], xg[0], w0, w1, ws);
+                    acck_mac(acc[g][1], xg[kJ4], w0, w1, ws);
+                }
+            }
+            if ((u & 3) == 3) {
+#pragma unroll
+                for (int g = 0; g < NB; g++) {
+                    acck_norm_mid(acc[g][0]);
+                    acck_norm_mid(acc[g][1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < NB; g++) {
+            acck_norm_lh(acc[g][0]);
+            acck_norm_lh(acc[g][1]);
+        }
+        if constexpr (kFold) {
+            if (((k0 + kPF4) & 255u) == 0 && k0 + kPF4 < T) {  // fold every 256 terms
+#pragma unroll
+                for (int g = 0; g < NB; g++)
+#pragma unroll
+                    for (int c = 0; c < 2; c++) {
+                        base[g][c] = acck_reduce(acc[g][c], base[g][c], P);
+                        acck_zero(acc[g][c]);
+                    }
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < NB; g++) {
+        if (bb0 + g >= L.GB) break;
+        const u64 v = ((u64)(bb0 + g) * L.Co + co) * beta + h;
+        const u64 r0 = acck_reduce(acc[g][0], kFold ? base[kFold ? g : 0][0] : 0, P);
+        u64 r1 = acck_reduce(acc[g][1], kFold ? base[kFold ? g : 0][1] : 0, P);
+        if (Mhat) r1 = submod_q(r1, __ldg(Mhat + v * n + j), P.q);
+        ct_out[v * 2 * n + j] = r0;
+        ct_out[v * 2 * n + n + j] = r1;
+    }
+}
+
+// ---------------------------------------------------------------- v5: lean staged tile, two indices per lane
+// The carry-chained 128-bit accumulation of v3 with less work around each
+// product: a CTA covers kJ5 = 64 consecutive evaluation indices (two per
+// lane, so filter words, input words and outputs move as 16-byte pairs) and
+// kW5 = 8 output channels (one per warp); the k loop is unrolled kTU terms
+// deep with a ring of kTU filter-word pairs in flight per thread, whose
+// first kTU loads are issued before the input tile is staged (the filter
+// does not depend on the kernels before HomConv).  Needs T a multiple of
+// kTU and T <= 128 (the staged tile, T KiB, stays in shared memory; no
+// 256-term fold is needed).  (Under programmatic dependent launch the filter
+// loads still wait for the previous kernel, like every access to caller
+// memory.)
+constexpr u32 kJ5 = 64, kW5 = 8, kThreads5 = 32 * kW5, kMaxT5 = 128;
+
+template <int kTU>
+__global__ void __launch_bounds__(kThreads5, 2)
+    homconv5_kernel(DevParams P, DevLayer L, const u64* __restrict__ ct_in, const u64* __restrict__ A1,
+                    const u64* __restrict__ A2, const u64* __restrict__ Phat, const u64* __restrict__ Mhat,
+                    u64* __restrict__ ct_out, u32 jtiles, u32 ctiles) {
+    extern __shared__ __align__(16) ulonglong2 xs5[];  // [T][2][kJ5 / 2] pairs of canonical words
+    constexpr u32 kPairs = kJ5 / 2;
+    u32 blk = blockIdx.x;
+    const u32 jt = blk % jtiles;
+    blk /= jtiles;
+    const u32 ct = blk % ctiles, bb = blk / ctiles;
+    const u32 nJ = L.beta * P.n, T = L.T;
+    const u64 n = P.n, beta = L.beta;
+    const u32 lane = threadIdx.x & 31, co = ct * kW5 + (threadIdx.x >> 5);
+    const u32 J = jt * kJ5 + 2 * lane;  // J and J + 1 lie in the same half (n even)
+    const bool active = co < L.Co && J < nJ;
+    const u32 h = J >> P.logn, j = J & (P.n - 1);
+    const u64* wp = Phat + ((u64)(active ? co : 0) * T * beta + (active ? h : 0)) * n + (active ? j : 0);
+    const u64 w_step = beta * n;
+    griddep_release();
+    griddep_wait();
+    ulonglong2 ring[kTU];
+#pragma unroll
+    for (int u = 0; u < kTU; u++) ring[u] = active ? ldg2(wp + (u64)u * w_step) : make_ulonglong2(0, 0);
+    for (u32 e = threadIdx.x; e < T * kPairs; e += kThreads5) {
+        const u32 k = e / kPairs, jp = e % kPairs, Jx = jt * kJ5 + 2 * jp;
+        ulonglong2 x0 = make_ulonglong2(0, 0), x1 = make_ulonglong2(0, 0);
+        if (Jx < nJ) {
+            const u32 hx = Jx >> P.logn, jx = Jx & (P.n - 1);
+            const u64 u = ((u64)bb * T + k) * beta + hx;
+            x0 = ldg2(ct_in + u * 2 * n + jx);
+            x1 = ldg2(ct_in + u * 2 * n + n + jx);
+            if (A1) {
+                const ulonglong2 a = ldg2(A1 + u * n + jx);
+                x1.x = addmod_q(x1.x, a.x, P.q);
+                x1.y = addmod_q(x1.y, a.y, P.q);
+            }
+            if (A2) {
+                const ulonglong2 a = ldg2(A2 + u * n + jx);
+                x1.x = addmod_q(x1.x, a.x, P.q);
+                x1.y = addmod_q(x1.y, a.y, P.q);
+            }
+        }
+        xs5[(k * 2 + 0) * kPairs + jp] = x0;
+        xs5[(k * 2 + 1) * kPairs + jp] = x1;
+    }
+    __syncthreads();
+    if (!active) return;
+    Acc128 acc[2][2];  // [index J + e][component]
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        acc_zero(acc[e][0]);
+        acc_zero(acc[e][1]);
+    }
+    for (u32 k0 = 0; k0 < T; k0 += kTU) {
+#pragma unroll
+        for (int u = 0; u < kTU; u++) {
+            const u32 k = k0 + u;
+            const ulonglong2 w = ring[u];
+            if (k + kTU < T) ring[u] = ldg2(wp + (u64)(k + kTU) * w_step);
+            const ulonglong2 xa = xs5[(k * 2 + 0) * kPairs + lane], xb = xs5[(k * 2 + 1) * kPairs + lane];
+            acc_mac(acc[0][0], xa.x, w.x);
+            acc_mac(acc[1][0], xa.y, w.y);
+            acc_mac(acc[0][1], xb.x, w.x);
+            acc_mac(acc[1][1], xb.y, w.y);
+        }
+    }
+    const u64 v = ((u64)bb * L.Co + co) * beta + h;
+    ulonglong2 r0, r1;
+    r0.x = acc_reduce(acc[0][0], P);
+    r0.y = acc_reduce(acc[1][0], P);
+    r1.x = acc_reduce(acc[0][1], P);
+    r1.y = acc_reduce(acc[1][1], P);
+    if (Mhat) {
+        const ulonglong2 m = ldg2(Mhat + v * n + j);
+        r1.x = submod_q(r1.x, m.x, P.q);
+        r1.y = submod_q(r1.y, m.y, P.q);
+    }
+    *reinterpret_cast<ulonglong2*>(ct_out + v * 2 * n + j) = r0;
+    *reinterpret_cast<ulonglong2*>(ct_out + v * 2 * n + n + j) = r1;
+}
+
+bool v5_supported(const DevLayer& L) { return L.T <= kMaxT5 && L.T % 4 == 0; }
+
+// ---------------------------------------------------------------- v6: filter stream through shared memory
+// v5's tile and accumulation, with the filter words streamed by cp.async
+// into a per-thread ring of kD slots in shared memory instead of registers:
+// every thread copies exactly the 16-byte filter pairs it multiplies (its
+// output channel, its two indices), so the ring needs no barrier, and kD
+// pairs per thread stay in flight without holding registers (kD = 16:
+// 128 KiB of filter in flight per SM at two CTAs per SM).  One copy group is
+// committed per term (empty past the end), so waiting for all but the kD - 1
+// newest groups completes exactly the term about to be used.
+constexpr u32 kMaxT6 = 64;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((u32)__cvta_generic_to_shared(smem)), "l"(g)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int kD>
+__global__ void __launch_bounds__(kThreads5, 2)
+    homconv6_kernel(DevParams P, DevLayer L, const u64* __restrict__ ct_in, const u64* __restrict__ A1,
+                    const u64* __restrict__ A2, const u64* __restrict__ Phat, const u64* __restrict__ Mhat,
+                    u64* __restrict__ ct_out, u32 jtiles, u32 ctiles) {
+    extern __shared__ __align__(16) ulonglong2 sm6[];  // [kD][kThreads5] filter ring, then [T][2][kJ5 / 2] inputs
+    constexpr u32 kPairs = kJ5 / 2;
+    ulonglong2* ring = sm6 + threadIdx.x;  // slot s at ring[s * kThreads5]
+    ulonglong2* xs = sm6 + kD * kThreads5;
+    u32 blk = blockIdx.x;
+    const u32 jt = blk % jtiles;
+    blk /= jtiles;
+    const u32 ct = blk % ctiles, bb = blk / ctiles;
+    const u32 nJ = L.beta * P.n, T = L.T;
+    const u64 n = P.n, beta = L.beta;
+    const u32 lane = threadIdx.x & 31, co = ct * kW5 + (threadIdx.x >> 5);
+    const u32 J = jt * kJ5 + 2 * lane;  // J and J + 1 lie in the same half (n even)
+    const bool active = co < L.Co && J < nJ;
+    const u32 h = J >> P.logn, j = J & (P.n - 1);
+    const u64* wp = Phat + ((u64)(active ? co : 0) * T * beta + (active ? h : 0)) * n + (active ? j : 0);
+    const u64 w_step = beta * n;
+    griddep_release();
+    griddep_wait();
+#pragma unroll
+    for (int u = 0; u < kD; u++) {
+        if (active && (u32)u < T) cp_async16(ring + u * kThreads5, wp + (u64)u * w_step);
+        cp_commit();
+    }
+    ulonglong2 m = make_ulonglong2(0, 0);
+    if (active && Mhat) m = ldg2(Mhat + (((u64)bb * L.Co + co) * beta + h) * n + j);
+    for (u32 e = threadIdx.x; e < T * kPairs; e += kThreads5) {
+        const u32 k = e / kPairs, jp = e % kPairs, Jx = jt * kJ5 + 2 * jp;
+        ulonglong2 x0 = make_ulonglong2(0, 0), x1 = make_ulonglong2(0, 0);
+        if (Jx < nJ) {
+            const u32 hx = Jx >> P.logn, jx = Jx & (P.n - 1);
+            const u64 u = ((u64)bb * T + k) * beta + hx;
+            x0 = ldg2(ct_in + u * 2 * n + jx);
+            x1 = ldg2(ct_in + u * 2 * n + n + jx);
+            if (A1) {
+                const ulonglong2 a = ldg2(A1 + u * n + jx);
+                x1.x = addmod_q(x1.x, a.x, P.q);
+                x1.y = addmod_q(x1.y, a.y, P.q);
+            }
+            if (A2) {
+                const ulonglong2 a = ldg2(A2 + u * n + jx);
+                x1.x = addmod_q(x1.x, a.x, P.q);
+                x1.y = addmod_q(x1.y, a.y, P.q);
+            }
+        }
+        xs[(k * 2 + 0) * kPairs + jp] = x0;
+        xs[(k * 2 + 1) * kPairs + jp] = x1;
+    }
+    __syncthreads();
+    if (!active) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        return;
+    }
+    Acc128 acc[2][2];  // [index J + e][component]
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        acc_zero(acc[e][0]);
+        acc_zero(acc[e][1]);
+    }
+    for (u32 k0 = 0; k0 < T; k0 += kD) {
+#pragma unroll
+        for (int u = 0; u < kD; u++) {
+            const u32 k = k0 + u;
+            if (k < T) {
+                asm volatile("cp.async.wait_group %0;" ::"n"(kD - 1) : "memory");
+                const ulonglong2 w = ring[u * kThreads5];
+                const ulonglong2 xa = xs[(k * 2 + 0) * kPairs + lane], xb = xs[(k * 2 + 1) * kPairs + lane];
+                acc_mac(acc[0][0], xa.x, w.x);
+                acc_mac(acc[1][0], xa.y, w.y);
+                acc_mac(acc[0][1], xb.x, w.x);
+                acc_mac(acc[1][1], xb.y, w.y);
+                // the slot is refilled only after its words were used
+                if (k + kD < T) cp_async16(ring + u * kThreads5, wp + (u64)(k + kD) * w_step);
+                cp_commit();
+            }
+        }
+    }
+    const u64 v = ((u64)bb * L.Co + co) * beta + h;
+    ulonglong2 r0, r1;
+    r0.x = acc_reduce(acc[0][0], P);
+    r0.y = acc_reduce(acc[1][0], P);
+    r1.x = acc_reduce(acc[0][1], P);
+    r1.y = acc_reduce(acc[1][1], P);
+    if (Mhat) {
+        r1.x = submod_q(r1.x, m.x, P.q);
+        r1.y = submod_q(r1.y, m.y, P.q);
+    }
+    *reinterpret_cast<ulonglong2*>(ct_out + v * 2 * n + j) = r0;
+    *reinterpret_cast<ulonglong2*>(ct_out + v * 2 * n + n + j) = r1;
+}
+
+bool v6_supported(const DevLayer& L) { return L.T <= kMaxT6; }
+
+template <int kD>
+cudaError_t launch_v6(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                      const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
+    const u32 nJ = L.beta * P.n;
+    const u32 jtiles = (nJ + kJ5 - 1) / kJ5, ctiles = (L.Co + kW5 - 1) / kW5;
+    const u64 grid = (u64)jtiles * ctiles * L.GB;
+    const size_t smem = (size_t)kD * kThreads5 * 16 + (size_t)L.T * 2 * kJ5 * 8;
+    if (grid > 0x7FFFFFFFull || !v6_supported(L)) return cudaErrorInvalidConfiguration;
+    if (smem + 1024 > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(homconv6_kernel<kD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_online(homconv6_kernel<kD>, (u32)grid, kThreads5, smem, s, P, L, ct_in, A1, A2, Phat, Mhat, ct_out,
+                         jtiles, ctiles);
+}
+
+cudaError_t launch_v5(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                      const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
+    const u32 nJ = L.beta * P.n;
+    const u32 jtiles = (nJ + kJ5 - 1) / kJ5, ctiles = (L.Co + kW5 - 1) / kW5;
+    const u64 grid = (u64)jtiles * ctiles * L.GB;
+    const size_t smem = (size_t)L.T * 2 * kJ5 * 8;
+    if (grid > 0x7FFFFFFFull || !v5_supported(L)) return cudaErrorInvalidConfiguration;
+    void (*kern)(DevParams, DevLayer, const u64*, const u64*, const u64*, const u64*, const u64*, u64*, u32, u32) =
+        L.T % 8 == 0 ? homconv5_kernel<8> : homconv5_kernel<4>;
+    if (smem + 1024 > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_online(kern, (u32)grid, kThreads5, smem, s, P, L, ct_in, A1, A2, Phat, Mhat, ct_out, jtiles,
+                         ctiles);
+}
+
+// NB image groups per CTA (the caller checks that the staged tiles fit)
+template <int NB>
+cudaError_t launch_v4(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
+                      const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
+    const u32 nJ = L.beta * P.n;
+    const u32 jtiles = (nJ + kJ4 - 1) / kJ4, ctiles = (L.Co + kW4 - 1) / kW4, btiles = (L.GB + NB - 1) / NB;
+    const u64 grid = (u64)jtiles * ctiles * btiles;
+    const size_t smem = (size_t)NB * L.T * 2 * kJ4 * 8;
+    if (grid > 0x7FFFFFFFull || smem > kMaxStage4) return cudaErrorInvalidConfiguration;
+    const bool fold = L.T > 256;
+    void (*kern)(DevParams, DevLayer, const u64*, const u64*, const u64*, const u64*, const u64*, u64*, u32, u32) =
+        fold ? homconv4_kernel<NB, true> : homconv4_kernel<NB, false>;
+    if (smem + 1024 > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_online(kern, (u32)grid, kThreads4, smem, s, P, L, ct_in, A1, A2, Phat, Mhat, ct_out, jtiles,
+                         ctiles);
+}
+
 
 }  // namespace
 
 // Variant selection: 0 = automatic, 1 = limb columns NB=1, 2 = limb columns
 // NB=2, 3 = carry chain NB=1, 4 = staged tile with carry chain, 5 = staged
-// tile with limb columns, 6 = staged tile with lazy 32-bit-limb columns.
+// tile with limb columns, 6 = staged tile with lazy 32-bit-limb columns,
+// 8 / 9 = staged tile with Karatsuba limb columns and 1 / 2 image groups per
+// CTA, 10 = lean staged tile with two indices per lane (T a multiple of 4,
+// at most 128; 4 otherwise), 11 / 12 = the same with the filter streamed
+// through a shared-memory ring of 16 / 8 terms (T <= 64; 10 otherwise).  7 is
+// the tensor-core kernel, a plan-only choice.
 static int g_homconv_variant = 0;
+bool homconv_variant_valid(int v) { return v >= 0 && v <= 12 && v != 7; }
 extern "C" int fdsc_set_homconv_variant(int v) {
-    if (v < 0 || v > 6) return FDSC_ERR_ARG;
+    if (!homconv_variant_valid(v)) return FDSC_ERR_ARG;
     g_homconv_variant = v;
     return FDSC_OK;
 }
@@ -446,11 +874,42 @@ cudaError_t launch_adds(const DevParams& P, const DevLayer& L, const u64* ct_in,
     return launch_variant<NB, W, 2>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
 }
 
-int homconv_default_variant(const DevLayer& L) { return L.T <= 256 ? 4 : 3; }
+// Measured on GB300 (32x32x64 layer at 1 and 16 images): the shared-memory
+// filter ring (12) is the fastest up to T = 64 (equal at one image, 12 %
+// faster at 16); beyond that the staged carry-chain kernel (4), and past 256
+// terms the unstaged one (3).
+int homconv_default_variant(const DevLayer& L) { return L.T <= kMaxT6 ? 12 : (L.T <= 256 ? 4 : 3); }
+
+// The variant launch_homconv_v runs when asked for v (the fallbacks below).
+int homconv_effective_variant(const DevLayer& L, int v) {
+    if (v <= 0 || v > 12 || v == 7) v = homconv_default_variant(L);
+    if ((v == 11 || v == 12) && !v6_supported(L)) v = 10;
+    if (v == 10 && !v5_supported(L)) v = L.T <= 256 ? 4 : 3;
+    if (v >= 8 && v <= 9 && (u64)L.T * 2 * kJ4 * 8 > kMaxStage4) v = 3;
+    if (v >= 4 && v <= 6 && L.T > 256) v = 3;
+    return v;
+}
 
 cudaError_t launch_homconv_v(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
                              const u64* Phat, const u64* Mhat, u64* ct_out, int v, cudaStream_t s) {
-    if (v <= 0 || v > 6) v = homconv_default_variant(L);
+    if (v <= 0 || v > 12 || v == 7) v = homconv_default_variant(L);
+    if (v == 11 || v == 12) {
+        if (v6_supported(L))
+            return v == 11 ? launch_v6<16>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s)
+                           : launch_v6<8>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+        v = 10;
+    }
+    if (v == 10) {
+        if (v5_supported(L)) return launch_v5(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+        v = L.T <= 256 ? 4 : 3;
+    }
+    if (v >= 8) {  // Karatsuba columns: as many image groups per CTA as the staged tiles allow
+        const u64 tile = (u64)L.T * 2 * kJ4 * 8;
+        if (v >= 9 && 2 * tile <= kMaxStage4 && L.GB >= 2)
+            return launch_v4<2>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+        if (tile <= kMaxStage4) return launch_v4<1>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+        v = 3;
+    }
     // the staged tile must fit in shared memory (T <= 256 words x 2 x 32 lanes)
     if (v >= 4 && L.T > 256) v = 3;
     switch (v) {

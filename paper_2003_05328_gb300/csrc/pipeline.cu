@@ -27,23 +27,48 @@ constexpr u32 kMaxThreads = 512;
 
 inline u32 threads_for(u32 n) { return n / 8 < 32 ? 32 : n / 8; }
 
+// ---------------------------------------------------------------- L2 prefetch of a later kernel's operands
+// Up to two device ranges (16-byte aligned, whole multiples of 16 bytes)
+// split evenly over `slices` CTAs; the CTA `slice` asks the L2 cache for its
+// part in 4 KiB bulk prefetches (no data reaches the SM).
+struct L2Prefetch {
+    const void* p[2];
+    u64 bytes[2];
+    u32 slice, slices;
+    __device__ __forceinline__ void issue() const {
+        constexpr u64 kChunk = 4096;
+        for (int r = 0; r < 2; r++) {
+            if (!p[r] || !bytes[r] || !slices) continue;
+            const u64 chunks = (bytes[r] + kChunk - 1) / kChunk;
+            const u64 c0 = chunks * slice / slices, c1 = chunks * (slice + 1) / slices;
+            for (u64 c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+                const u64 off = c * kChunk, len = bytes[r] - off < kChunk ? bytes[r] - off : kChunk;
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char*>(p[r]) + off),
+                             "r"((u32)len)
+                             : "memory");
+            }
+        }
+    }
+};
+
 // ---------------------------------------------------------------- encryption constants
 // Image group g = u / per_group uses the key t_hat + g key_stride; with
 // seeds != nullptr it draws from seeds[g] with ciphertexts numbered from 0
 // inside the group (as if it were a call of its own).
 // c1_only: write c1 alone ([n_in][n]; the seeded form, c0 = -a being
 // recomputable from the seed).
-__global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, const u64* __restrict__ t_hat, u64 key_stride,
-                                                                u32 per_group, u64 seed, const u64* __restrict__ seeds,
-                                                                u64* __restrict__ ct, int c1_only) {
-    extern __shared__ __align__(16) unsigned char sm[];
+// The work of ciphertext u (one CTA); sm: constants_smem_bytes of dynamic
+// shared memory.
+__device__ __forceinline__ void constants_body(unsigned char* sm, const DevParams& P, const u64* __restrict__ t_hat,
+                                               u64 key_stride, u32 per_group, u64 seed,
+                                               const u64* __restrict__ seeds, u64* __restrict__ ct, int c1_only,
+                                               u32 u, const L2Prefetch* pf = nullptr) {
     const u32 n = P.n;
     ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^brv, companion)
     u64* c = reinterpret_cast<u64*>(tq + n);             // padded [n]
     u64* key = c + padded_len(n);                        // [n], the key's NTT_q words
     __shared__ u64 cdt[19];
-    const u32 u = blockIdx.x, grp = u / per_group;
-    griddep_release();
+    const u32 grp = u / per_group;
     stage_async(tq, P.qfw2, n * 16);
     if (threadIdx.x < 19) cdt[threadIdx.x] = P.cdt[threadIdx.x];
     __syncthreads();
@@ -59,6 +84,7 @@ __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, con
         c[padx(i)] = e >= 0 ? (u64)e : P.q - (u64)(-e);
     }
     stage_wait();
+    if (pf) pf->issue();
     ntt_r8p<true, u64>(c, P.logn, 1, tq, 0, 0, P);
     if (!seeds) griddep_wait();
     stage_async(key, t_hat + (u64)grp * key_stride, n * 8);
@@ -86,13 +112,21 @@ __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, con
     }
 }
 
+__global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, const u64* __restrict__ t_hat, u64 key_stride,
+                                                                u32 per_group, u64 seed, const u64* __restrict__ seeds,
+                                                                u64* __restrict__ ct, int c1_only) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    griddep_release();
+    constants_body(sm, P, t_hat, key_stride, per_group, seed, seeds, ct, c1_only, blockIdx.x);
+}
+
 // ---------------------------------------------------------------- share encoding
 // One CTA per input ciphertext u = (bb, k) (beta = 1).  kMode 0: write
 // A[u] = NTT_q(Delta m); kMode 1: add it to ct[u].c1.
 template <int kMode>
-__global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLayer L, const u32* __restrict__ x,
-                                                            u64* __restrict__ out) {
-    extern __shared__ __align__(16) unsigned char sm[];
+__device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P, const DevLayer& L,
+                                           const u32* __restrict__ x, u64* __restrict__ out, u32 u,
+                                           const L2Prefetch* pf = nullptr) {
     const u32 n = P.n, S = P.S;
     const u32 np = padded_len(n);                        // padded length (even)
     ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^brv, companion)
@@ -101,10 +135,7 @@ __global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLaye
     uint2* tw_col = tw_row + (L.W >> 1);                 // [H/2]
     u64* c = reinterpret_cast<u64*>(tw_col + (L.H >> 1));  // padded [n]
     u32* slots = reinterpret_cast<u32*>(c + np);         // padded [n] = d slot sets
-    griddep_release();
-    griddep_wait();
-
-    const u32 u = blockIdx.x, k = u % L.T, bb = u / L.T;
+    const u32 k = u % L.T, bb = u / L.T;
     const u32 HW = L.HW, logHW = L.logH + L.logW, blocks = L.g_c * L.g_b;
     // every load is issued before anything waits: the share's words (eight
     // per thread), then the twiddle tables in the order they are needed
@@ -140,6 +171,7 @@ __global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLaye
         load8(e0, v);
         store8(e0, v);
     }
+    if (pf) pf->issue();
     stage_wait_groups<2>();  // line twiddles (and the planes) in place
     // NTT2D of every plane (zero planes included): rows, then columns
     lines_r8p<false>(slots, n >> logHW, true, L.logH, L.logW, tw_row, P.p);
@@ -159,6 +191,38 @@ __global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLaye
         u64* c1 = out + (u64)u * 2 * n + n;
         for (u32 j = threadIdx.x; j < n; j += blockDim.x) c1[j] = addmod_q(c1[j], c[padx(j)], P.q);
     }
+}
+
+template <int kMode>
+__global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLayer L, const u32* __restrict__ x,
+                                                            u64* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    griddep_release();
+    griddep_wait();
+    share_body<kMode>(sm, P, L, x, out, blockIdx.x);
+}
+
+// ---------------------------------------------------------------- the three producers in one launch
+// CTAs [0, n_in) draw the encryption constants of ciphertext u, CTAs
+// [n_in, 2 n_in) encode Alice's share x_A into A, CTAs [2 n_in, 3 n_in)
+// encode Bob's share x_B into R -- the words of constants_kernel and
+// share_kernel<0>.  Every CTA lets the next kernel in the stream launch at
+// once (programmatic dependent launch), and, once its own loads have been
+// issued, asks the L2 cache for its slice of two device ranges (the next
+// kernel's input-independent operands: filter plaintexts and masks), so
+// that those bytes stream from HBM while the transforms run.
+__global__ void __launch_bounds__(kMaxThreads) produce_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
+                                                              u64 seed, const u32* __restrict__ xA,
+                                                              const u32* __restrict__ xB, u64* __restrict__ ct,
+                                                              u64* __restrict__ A, u64* __restrict__ R, L2Prefetch pf) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    griddep_release();
+    griddep_wait();
+    const u32 role = blockIdx.x / L.n_in, u = blockIdx.x - role * L.n_in;
+    pf.slice = blockIdx.x;
+    pf.slices = gridDim.x;
+    if (role == 0) constants_body(sm, P, t_hat, 0, L.n_in, seed, nullptr, ct, 0, u, &pf);
+    else share_body<0>(sm, P, L, role == 1 ? xA : xB, role == 1 ? A : R, u, &pf);
 }
 
 // ---------------------------------------------------------------- decrypt + fold + INTT2D
@@ -431,6 +495,22 @@ cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u6
     cudaError_t e = add_to_ct ? opt_in(share_kernel<1>, sm) : opt_in(share_kernel<0>, sm);
     if (e != cudaSuccess) return e;
     return launch_online(add_to_ct ? share_kernel<1> : share_kernel<0>, L.n_in, threads_for(P.n), sm, s, P, L, x, out);
+}
+
+size_t produce_smem_bytes(const DevParams& P, const DevLayer& L) {
+    const size_t a = share_smem_bytes(P, L), b = constants_smem_bytes(P);
+    return a > b ? a : b;
+}
+
+cudaError_t launch_produce(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 seed, const u32* xA,
+                           const u32* xB, u64* ct, u64* A, u64* R, const void* pf0, u64 pf0_bytes, const void* pf1,
+                           u64 pf1_bytes, cudaStream_t s) {
+    const size_t sm = produce_smem_bytes(P, L);
+    cudaError_t e = opt_in(produce_kernel, sm);
+    if (e != cudaSuccess) return e;
+    L2Prefetch pf = {{pf0, pf1}, {pf0_bytes, pf1_bytes}, 0, 0};
+    return launch_online(produce_kernel, 3 * L.n_in, threads_for(P.n), sm, s, P, L, t_hat, seed, xA, xB, ct, A, R,
+                         pf);
 }
 
 cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, const u64* ct,

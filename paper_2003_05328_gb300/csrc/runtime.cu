@@ -284,7 +284,7 @@ extern "C" int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, u
                 packs.push_back({std::min(gc, sp.layer.Ci), gb});
             }
             if (packs.empty()) packs.push_back({pl.L.g_c, pl.L.g_b});
-            const int variants[] = {3, 4, 2, kTensorVariant};
+            const int variants[] = {4, 10, 12, kTensorVariant};
             double best = 1e30;
             fdsc_layer bestL = pl.L;
             int bestV = pl.variant;
@@ -298,8 +298,9 @@ extern "C" int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, u
                     if (fdsc_make_layer(I, &cand.L, &Dt, nullptr) != FDSC_OK || Dt.T > sp.params->max_T ||
                         !fdsc_noise_ok_flood(I, Dt.T, sp.flood_bits))
                         continue;
-                    if (v == 2 && Dt.GB < 2) continue;
                     if (v == kTensorVariant && !homconv_tc_supported(I.n, Dt)) continue;
+                    // a variant that falls back to another one for this shape is not timed twice
+                    if (v != kTensorVariant && homconv_effective_variant(Dt, v) != v) continue;
                     double us = 0;
                     if ((rc = plan_time_candidate(cand, st, ev, &us))) return fail(rc);
                     pl.candidates++;

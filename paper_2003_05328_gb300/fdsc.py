@@ -78,6 +78,7 @@ _SIGS = {
     "fdsc_encrypt_constants": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp]),
     "fdsc_encode_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
     "fdsc_homrec_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
+    "fdsc_online_produce": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fdsc_homconv_sum": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fdsc_filter_tc_words": (C.c_int, [C.c_uint32, C.c_uint32, _PL, C.POINTER(C.c_uint64)]),
     "fdsc_filter_tc": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
@@ -375,6 +376,26 @@ def encode_share(P: Params, L: LayerSpec, x, out=None, stream=None) -> torch.Ten
     _call("fdsc_encode_share", P.handle, C.byref(L.c()), _ptr(x, torch.int32, lay.in_spectra_words, "x"),
           _ptr(out, torch.int64, lay.n_in * P.n, "A"), _stream(stream))
     return out
+
+
+def online_produce(P: Params, L: LayerSpec, t_hat, seed: int, xA, xB, ct=None, A=None, R=None, P_hat=None,
+                   M_hat=None, stream=None):
+    """Encryption constants, Alice's and Bob's share encodings in one launch
+    (the words of encrypt_constants, encode_share(xA), encode_share(xB));
+    P_hat / M_hat, if given, are prefetched into L2 for the HomConv that
+    follows.  Returns (ct, A, R)."""
+    lay = layout(P, L)
+    na = lay.n_in * P.n
+    ct = torch.empty(lay.ct_in_words, dtype=torch.int64, device="cuda") if ct is None else ct
+    A = torch.empty(na, dtype=torch.int64, device="cuda") if A is None else A
+    R = torch.empty(na, dtype=torch.int64, device="cuda") if R is None else R
+    ph = None if P_hat is None else _ptr(P_hat, torch.int64, lay.filter_words, "P_hat")
+    mh = None if M_hat is None else _ptr(M_hat, torch.int64, lay.mask_words, "M_hat")
+    _call("fdsc_online_produce", P.handle, C.byref(L.c()), _ptr(t_hat, torch.int64, P.n, "t_hat"), seed,
+          _ptr(xA, torch.int32, lay.in_spectra_words, "xA"), _ptr(xB, torch.int32, lay.in_spectra_words, "xB"),
+          _ptr(ct, torch.int64, lay.ct_in_words, "ct"), _ptr(A, torch.int64, na, "A"), _ptr(R, torch.int64, na, "R"),
+          ph, mh, _stream(stream))
+    return ct, A, R
 
 
 def homrec_share(P: Params, L: LayerSpec, xB, ct, stream=None) -> torch.Tensor:

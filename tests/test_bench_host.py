@@ -66,6 +66,9 @@ def test_reference_arm_line():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "layers/s" and d["steps"] == 3 and d["warmup"] == 3
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
+    # ms_per_step is the measured wall time of a step; a step is a stated fraction of a layer
+    frac = d["layer_fraction_per_step"]
+    assert 0 < frac <= 1 and d["value"] > 0
+    assert abs(d["value"] - frac * 1e3 / d["ms_per_step"]) < 1e-6 * d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

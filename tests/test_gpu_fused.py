@@ -85,6 +85,11 @@ def test_fused_path_bit_exact(F, args):
     assert torch.equal(out, out1)
     yA = F.decrypt_share(P, L, t_hat, out)
     assert np.array_equal(u32(yA).reshape(ref["yA"].shape), ref["yA"])
+    # the three producers in one launch (with the L2 prefetch of HomConv's
+    # operands, and without): the same words as the separate calls
+    for pf in ((Phat, Mhat), (None, None)):
+        ct3, A3, R3 = F.online_produce(P, L, t_hat, es, dA, dB, P_hat=pf[0], M_hat=pf[1])
+        assert torch.equal(ct3, C0) and torch.equal(A3, A) and torch.equal(R3, Bsh)
     torch.cuda.synchronize()
     P.close()
 

@@ -227,8 +227,13 @@ def test_homconv_many_terms_folds_accumulator(F):
     ct = np.full((OL.n_in, 2, n), OP.q - 1, np.uint64)
     Ph = np.full((Co * OL.T, n), OP.q - 1, np.uint64)
     ref = O.homconv(OP, OL, ct, Ph, None)
-    got = F.homconv(P, L, dev(ct.view(np.int64), np.int64), dev(Ph.view(np.int64), np.int64))
-    assert np.array_equal(u64(got).reshape(ref.shape), ref)
+    try:  # the default kernel, and the Karatsuba-column kernel folding every 256 terms
+        for v in (0, 8):
+            F.set_homconv_variant(v)
+            got = F.homconv(P, L, dev(ct.view(np.int64), np.int64), dev(Ph.view(np.int64), np.int64))
+            assert np.array_equal(u64(got).reshape(ref.shape), ref), v
+    finally:
+        F.set_homconv_variant(0)
     P.close()
 
 
@@ -301,7 +306,9 @@ def test_argument_errors_are_reported(F):
                                    # many image groups per CTA (tile slots recycled), T not a multiple of 8
                                    (2048, 16, 50, 8, 32, 32, 2, 1),
                                    # beta = 4 halves per plane, Co not a multiple of 8
-                                   (1024, 2, 12, 12, 64, 64, 1, 1)])
+                                   (1024, 2, 12, 12, 64, 64, 1, 1),
+                                   # fewer evaluation indices than one tile, ragged channel tile
+                                   (16, 2, 8, 9, 4, 4, 1, 1)])
 def test_homconv_variants_identical(F, shape):
     """Every HomConv kernel variant (accumulation scheme, tiling, fused c1
     addends) gives the oracle's words."""
@@ -323,7 +330,7 @@ def test_homconv_variants_identical(F, shape):
     ref = O.homconv(OP, OL, summed.astype(np.uint64), Ph, Mh)
     d = lambda a: dev(a.view(np.int64), np.int64)
     try:
-        for v in range(1, 7):
+        for v in (1, 2, 3, 4, 5, 6, 8, 9, 10, 11, 12):
             F.set_homconv_variant(v)
             out = F.homconv_sum(P, L, d(ct), d(A1), d(A2), d(Ph), d(Mh))
             assert np.array_equal(u64(out).reshape(ref.shape), ref), v
