@@ -472,8 +472,9 @@ int fdsc_server_destroy(fdsc_server* s);
  * with the shapes of those calls (t_hat [n], P_hat [Co][T][n], M_hat
  * [GB][Co][n], sB_hat, yA, yB [B][Co][H][W], xA, xB [B][Ci][H][W]).
  *
- *  - The first call on a device looks up the array's device address (once per
- *    device); make that first call before any stream capture.
+ *  - The first call in a CUDA context (per device, and again after a device
+ *    reset) looks up the array's device address; make that first call before
+ *    any stream capture.
  *  - Layers whose intermediate ciphertexts need more than the array
  *    (8 (2 n_in + 2 n_in + 2 n_out) n bytes, each part rounded up to 256)
  *    are rejected with FDSC_ERR_UNSUPPORTED; so are shapes the fused kernels do

@@ -2,9 +2,7 @@
 // then one kernel launch each on the caller's stream.
 #include "fdsc_internal.h"
 
-namespace {
-
-int check_params(const fdsc_params* P) {
+int fdsc_check_params(const fdsc_params* P) {
     if (!P) return fdsc_set_error(FDSC_ERR_ARG, "params is NULL");
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -14,6 +12,10 @@ int check_params(const fdsc_params* P) {
                               dev);
     return FDSC_OK;
 }
+
+namespace {
+
+int check_params(const fdsc_params* P) { return fdsc_check_params(P); }
 
 int check_ptr(const void* p, const char* name, bool align16 = true) {
     if (!p) return fdsc_set_error(FDSC_ERR_ARG, "%s is NULL", name);
@@ -174,24 +176,25 @@ extern "C" int fdsc_decrypt(const fdsc_params* P, const fdsc_layer* L, const uin
 }
 
 // ---------------------------------------------------------------- fused online path
-namespace {
-
 // The fused spatial-domain kernels need whole spectra inside one ciphertext
 // (H W <= S), radix-8 lines (H, W >= 8) and their shared memory to fit.
-int check_fused(const fdsc_params* P, const DevLayer& D, size_t smem, const char* what) {
+int fdsc_check_fused(const fdsc_params* P, const DevLayer& D, size_t smem, const char* what) {
     if (D.beta != 1 || D.logH < 3 || D.logW < 3 || D.logH > 9 || D.logW > 9)
         return fdsc_set_error(FDSC_ERR_UNSUPPORTED,
                               "%s needs 8 <= H, W <= 512 and H W <= S; use fdsc_ntt2d/fdsc_encrypt/fdsc_decrypt",
                               what);
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+    if (e != cudaSuccess) return fdsc_set_error(FDSC_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
     if (smem + 1024 > (size_t)optin)
         return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "%s needs %zu bytes of shared memory", what, smem);
-    (void)P;
     return FDSC_OK;
 }
 
+namespace {
+int check_fused(const fdsc_params* P, const DevLayer& D, size_t smem, const char* what) {
+    return fdsc_check_fused(P, D, smem, what);
+}
 }  // namespace
 
 extern "C" int fdsc_encrypt_constants(const fdsc_params* P, const fdsc_layer* L, const uint64_t* t_hat, uint64_t seed,

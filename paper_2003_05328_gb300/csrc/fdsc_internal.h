@@ -62,6 +62,11 @@ struct fdsc_params {
 
 // ---- host helpers (params.cu) ----
 int fdsc_set_error(int code, const char* fmt, ...);
+// Argument checks shared by the entry points (api.cu): the params object
+// belongs to the current device; a layer fits the fused online kernels
+// (H W <= S, 8 <= H, W <= 512, `smem` bytes of shared memory per CTA).
+int fdsc_check_params(const fdsc_params* P);
+int fdsc_check_fused(const fdsc_params* P, const DevLayer& D, size_t smem, const char* what);
 
 // Whether online kernels are launched with programmatic stream serialisation
 // (fdsc_set_launch_overlap; off by default).

@@ -22,26 +22,47 @@ namespace {
 // comes from cudaGetSymbolAddress, per device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FDSC_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
+// The array's device address, looked up once per CUDA context with that
+// context current and remembered under the context's handle, so that a
+// context created after a device reset (cudaDeviceReset) gets its own
+// lookup instead of an address that belonged to the old one.
+constexpr int kMaxContexts = 64;
 std::mutex g_scratch_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchEntry {
+    void* ctx;
+    void* addr;
+};
+ScratchEntry g_scratch[kMaxContexts] = {};
+int g_scratch_used = 0;
 
-// The array's device address on the current device, looked up once per
-// device (the first call on a device does the lookup).
+typedef int (*CtxGetCurrentFn)(void**);  // the driver's cuCtxGetCurrent
+
 int scratch_on_current_device(void** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fdsc_set_error(FDSC_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "device %d out of range", dev);
+    static CtxGetCurrentFn ctx_get_current = nullptr;
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fdsc_set_error(FDSC_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
+    if (!ctx_get_current) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult st;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &st);
+        if (e != cudaSuccess || st != cudaDriverEntryPointSuccess || !fn)
+            return fdsc_set_error(FDSC_ERR_CUDA, "cuCtxGetCurrent not available: %s", cudaGetErrorString(e));
+        ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
     }
-    *out = g_scratch_ptr[dev];
+    void* ctx = nullptr;
+    if (ctx_get_current(&ctx) != 0 || !ctx) return fdsc_set_error(FDSC_ERR_CUDA, "no current CUDA context");
+    for (int i = 0; i < g_scratch_used; i++)
+        if (g_scratch[i].ctx == ctx) {
+            *out = g_scratch[i].addr;
+            return FDSC_OK;
+        }
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fdsc_set_error(FDSC_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    // a full table forgets its oldest context
+    const int slot = g_scratch_used < kMaxContexts ? g_scratch_used++ : 0;
+    g_scratch[slot] = {ctx, p};
+    *out = p;
     return FDSC_OK;
 }
 
@@ -53,16 +74,15 @@ extern "C" int fdsc_layer_online_noalloc(const fdsc_params* P, const fdsc_layer*
                                          uint64_t enc_seed, const uint64_t* P_hat, const uint64_t* M_hat,
                                          const uint32_t* sB_hat, const uint32_t* xA, const uint32_t* xB, uint32_t* yA,
                                          uint32_t* yB, void* stream) {
-    if (!P) return fdsc_set_error(FDSC_ERR_ARG, "params is NULL");
-    int dev = -1;
-    cudaGetDevice(&dev);
-    if (dev != P->device) return fdsc_set_error(FDSC_ERR_ARG, "params belong to device %d, %d is current", P->device, dev);
+    int rc = fdsc_check_params(P);
+    if (rc) return rc;
     DevLayer D;
     fdsc_layout lay;
-    int rc = fdsc_make_layer(P->info, L, &D, &lay);
-    if (rc) return rc;
-    if (D.beta != 1 || D.logH < 3 || D.logW < 3 || D.logH > 9 || D.logW > 9)
-        return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "layer_online_noalloc needs 8 <= H, W <= 512 and H W <= S");
+    if ((rc = fdsc_make_layer(P->info, L, &D, &lay))) return rc;
+    // exactly what the fused calls it runs accept
+    if ((rc = fdsc_check_fused(P, D, share_smem_bytes(P->dev, D), "layer_online_noalloc")) ||
+        (rc = fdsc_check_fused(P, D, decrypt_share_smem_bytes(P->dev, D), "layer_online_noalloc")))
+        return rc;
     if (D.T > P->max_T)
         return fdsc_set_error(FDSC_ERR_NOISE, "T = %u exceeds the params' max_T = %u", D.T, P->max_T);
     const void* ptrs[] = {t_hat, P_hat, M_hat, sB_hat, xA, xB, yA, yB};

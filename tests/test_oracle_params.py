@@ -52,6 +52,47 @@ def test_decoupled_moduli_do_not_reconstruct_mod_pN():
     assert P.S == 2048 and O.noise_ok(P, 32)
 
 
+def test_no_share_conversion_exists_at_table2_decoupled_moduli():
+    """Why Table 2's Binary and High rows are not built (Sec. 5.2, Sec. 6.4).
+
+    1. Information is lost, so no rule -- interactive or not -- can work on
+       HomConv's output: a slot of the decrypted, masked result is a
+       function of Y mod p_E, Y the integer Hadamard sum; two spectrum pairs
+       with the same product mod p_E but different products mod p_N give
+       the same output distribution and different wanted results.
+    2. A correct variant keeps the integer Y below p_E and masks it with
+       r < 2^kappa Y_max (statistical hiding), so Alice lifts Y - r exactly
+       and both parties reduce mod p_N: it needs p_E > (2^kappa + 1) Y_max
+       with Y_max = Ci (2 p_N - 2)(p_N - 1) (HomRec adds Bob's spectrum
+       without a reduction mod p_N), and a ciphertext modulus q whose
+       worst-case noise bound (fresh error times filter, T n 20 p_E / 2, at
+       p_E's scale Delta = q / p_E) holds.  Even with kappa = 0 and a single
+       input channel, q needs more than 60 bits at n = 2048.
+    3. p_N - 1 has a single factor 2 for both rows, so no power-of-two
+       plane transform exists mod p_N (only mixed-radix lengths)."""
+    rows = {r[0]: (int(r[1]), int(r[3]), int(r[5])) for r in _rows("table2_moduli.txt")}
+    n = 2048
+    for name in ("Binary", "High"):
+        pN, pE, lg_q = rows[name]
+        # 1: a collision of products mod p_E that differs mod p_N
+        x = pE + 1  # = 1 * (pE + 1) as a product of two spectrum values below p_N
+        a = next(d for d in range(2, pN) if x % d == 0 and x // d < pN)
+        u1, w1, u2, w2 = 1, 1, a, x // a
+        assert max(u1, w1, u2, w2) < pN
+        assert (u1 * w1) % pE == (u2 * w2) % pE and (u1 * w1) % pN != (u2 * w2) % pN, name
+        # 2: the smallest plaintext modulus that keeps Y exact at Ci = 1, kappa = 0, and the q it needs
+        y_max = 1 * (2 * pN - 2) * (pN - 1)
+        pE_min = sympy.nextprime(y_max)
+        while (pE_min - 1) % (2 * n):
+            pE_min = sympy.nextprime(pE_min)
+        T = 1
+        eta = T * n * 20 * (pE_min // 2)  # fresh error and HomRec carry (r_q = 1 at best), times the filter
+        q_min = 2 * (pE_min * eta + (pE_min - 1))  # p_E |eta| + r_q (p_E - 1) < q / 2, with r_q = 1
+        assert pE_min > pE and math.log2(q_min) > 60 and int(lg_q) <= 60, name
+        # 3: no power-of-two transform lengths beyond 2
+        assert (pN - 1) % 2 == 0 and (pN - 1) % 4 != 0, name
+
+
 def test_smallest_prime_splitting_x2048_plus_1_is_12289():
     # Sec. 5.2: "for n = 2048, p_E >= 12289" -- x^n + 1 splits completely mod
     # a prime iff 2n | p - 1.

@@ -28,10 +28,15 @@ def _dev(a, dt):
     return torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
 
 
-def test_noalloc_layer_matches_existing_entry_points_twice(F):
-    n, p, B, Ci, Co, H, W = 2048, 65537, 1, 64, 64, 32, 32
+@pytest.mark.parametrize("n,p,B,Ci,Co,H,W,g_c,g_b", [
+    (2048, 65537, 1, 64, 64, 32, 32, 2, 1),   # the 32x32x64 layer
+    (1024, 65537, 1, 4, 4, 16, 16, 4, 1),     # the 16x16 4 -> 4 layer
+    (2048, 65537, 3, 16, 24, 16, 16, 4, 2),   # Ci != Co, several images per slot set, a ragged last group
+    (4096, 12289, 4, 3, 5, 16, 16, 2, 2),     # two slot sets per ciphertext
+])
+def test_noalloc_layer_matches_existing_entry_points_twice(F, n, p, B, Ci, Co, H, W, g_c, g_b):
     P = F.Params(n, p, max_T=64)
-    L = F.LayerSpec(B, Ci, Co, H, W, 2, 1)
+    L = F.LayerSpec(B, Ci, Co, H, W, g_c, g_b)
     g = np.random.default_rng(2024)
     w = _dev(g.integers(-8, 8, (Co, Ci, 3, 3)), np.int8)
     t_hat = F.keygen(P, 31)
