@@ -508,6 +508,144 @@ def run_tensor_homconv(F, flush, args):
             "l2": "flushed before every timed replay", "shapes": out}
 
 
+def plain_conv_plane(p, x, w):
+    """One output plane of the cyclic convolution mod p, computed directly
+    with numpy (a property check of the GPU shares; the filter taps sit at
+    the top-left of the padded plane): y[i][j] = sum_ci sum_{a,c}
+    w[ci][a][c] x[ci][(i-a) mod H][(j-c) mod W]."""
+    Ci, fh, fw = w.shape
+    y = np.zeros(x.shape[1:], np.int64)
+    for ci in range(Ci):
+        for a in range(fh):
+            for c in range(fw):
+                y += int(w[ci, a, c]) * np.roll(np.roll(x[ci].astype(np.int64), a, axis=0), c, axis=1)
+    return y % p
+
+
+def run_binarized(F, sleep_cycles, args):
+    """The binarized 64x64x128 -> 128 layer at batch 8 (n = 4096, p = 12289,
+    two slot sets per ciphertext and each spectrum over two ciphertexts,
+    weights in {-1, +1}) through the fused online path: producers in one
+    launch, HomConv on the tensor cores, fused decryption, Bob's INTT2D on a
+    side stream.  One instance holds about 2 GB, far above L2, so every step
+    reads its operands from HBM.  Shares are checked against the plain
+    convolution on sampled planes."""
+    import torch
+
+    c = FI.CONFIGS["cfg4"]
+    ls = c.layers[0]
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    P = F.Params(ls.n, ls.p, max_T=ls.Ci)
+    L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, 1, 1)
+    lay = F.layout(P, L)
+    dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
+    xA_h, xB_h = FI.shares(ls, c.cid)
+    w_h = FI.weights(ls, c.cid)
+    ks, es, ss = FI.seeds(c.cid)
+    t_hat = F.keygen(P, ks)
+    Phat = F.filter_prepare(P, L, dev(w_h, np.int8))
+    Ptc = F.filter_tc(P, L, Phat)
+    Mhat, sB = F.mask_prepare(P, L, ss)
+    xA, xB = dev(xA_h, np.int32), dev(xB_h, np.int32)
+    ct = torch.empty(lay.ct_in_words, dtype=torch.int64, device="cuda")
+    A = torch.empty(lay.n_in * ls.n, dtype=torch.int64, device="cuda")
+    R = torch.empty_like(A)
+    out = torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda")
+    yA = torch.empty((ls.B, ls.Co, ls.H, ls.W), dtype=torch.int32, device="cuda")
+    yB = torch.empty_like(yA)
+    side = torch.cuda.Stream()
+
+    def step(tensor=True):
+        main = torch.cuda.current_stream()
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            F.intt2d(P, sB.view(ls.B, ls.Co, ls.H, ls.W), out=yB)
+        F.online_produce(P, L, t_hat, es, xA, xB, ct, A, R)
+        if tensor:
+            F.homconv_tc(P, L, ct, A, R, Ptc, Mhat, out=out)
+        else:
+            F.homconv_sum(P, L, ct, A, R, Phat, Mhat, out=out)
+        F.decrypt_share(P, L, t_hat, out, out=yA)
+        main.wait_stream(side)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        s0 = torch.cuda.Stream()
+        s0.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s0):
+            with torch.cuda.graph(gr, stream=s0):
+                fn()
+        torch.cuda.current_stream().wait_stream(s0)
+        for _ in range(2):
+            gr.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda._sleep(sleep_cycles)
+        a.record()
+        for _ in range(reps):
+            gr.replay()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e3 / reps
+
+    F.set_launch_overlap(True)
+    reps = max(5, min(args.steps // 20, 40))
+    step_us = timed(step, reps)
+    F.set_launch_overlap(False)
+    hc_tc_us = timed(lambda: F.homconv_tc(P, L, ct, A, R, Ptc, Mhat, out=out), reps)
+    hc_cc_us = timed(lambda: F.homconv_sum(P, L, ct, A, R, Phat, Mhat, out=out), max(3, reps // 4))
+    prod_us = timed(lambda: F.online_produce(P, L, t_hat, es, xA, xB, ct, A, R), reps)
+    dec_us = timed(lambda: F.decrypt_share(P, L, t_hat, out, out=yA), reps)
+    assert F.homconv_tc_status() == 0
+    # property check of the shares on sampled planes
+    step()
+    torch.cuda.synchronize()
+    yA_n = yA.cpu().numpy().view(np.uint32).astype(np.int64)
+    yB_n = yB.cpu().numpy().view(np.uint32).astype(np.int64)
+    x = (xA_h.astype(np.int64) + xB_h) % ls.p
+    rng = np.random.default_rng(c.cid)
+    checked = 0
+    for _ in range(4):
+        b, co = int(rng.integers(ls.B)), int(rng.integers(ls.Co))
+        if not np.array_equal((yA_n[b, co] + yB_n[b, co]) % ls.p, plain_conv_plane(ls.p, x[b], w_h[co])):
+            raise RuntimeError("binarized layer: shares do not reconstruct the convolution")
+        checked += 1
+    # algorithmic bytes of one HomConv launch (the method's 8-byte words, the
+    # filter once per group of d indices) and the bytes the tensor-core kernel moves
+    d = P.info.d
+    filt = 8 * ls.Co * lay.T * lay.beta * ls.n // d
+    per_groups = 8 * lay.GB * (4 * lay.T * lay.beta * ls.n + 3 * ls.Co * lay.beta * ls.n)
+    alg = filt + per_groups
+    moved = 8 * Ptc.numel() + per_groups
+    macs = 2 * ls.Co * lay.T * lay.beta * ls.n * lay.GB
+    res = {"workload": "cfg4", "layer": "64x64x128->128 3x3, binarized weights, batch 8", "n": ls.n, "p": ls.p,
+           "d": d, "beta": lay.beta, "T": lay.T, "image_groups": lay.GB,
+           "step_us": step_us, "layers_per_s": ls.B / (step_us * 1e-6),
+           "stage_us": {"online_produce": prod_us, "homconv_tc": hc_tc_us, "homconv_cuda_cores": hc_cc_us,
+                        "decrypt_share": dec_us},
+           "roofline": {"kernel": "homconv_tc_kernel (fdsc_homconv_tc)", "bound": "hbm",
+                        "alg_bytes_per_launch": alg, "achieved": alg / (hc_tc_us * 1e-6) / 1e9, "peak": hbm,
+                        "unit": "GB/s", "frac": alg / (hc_tc_us * 1e-6) / 1e9 / hbm,
+                        "bytes_moved_per_launch": moved,
+                        "frac_of_moved": moved / (hc_tc_us * 1e-6) / 1e9 / hbm,
+                        "note": "alg: 8-byte filter words once per group of d = 2 evaluation indices, input, "
+                                "addend, output and mask words; moved: the fp16 digit-plane filter (16 bytes a "
+                                "distinct word) plus the same per-group words"},
+           "mod_q_macs_per_s": macs / (hc_tc_us * 1e-6),
+           "shares_checked_planes": checked,
+           "launches": 4 * (reps + 4) + 3 * (reps + 3) + (max(3, reps // 4) + 3),
+           "timing": "one CUDA graph per measurement, %d replays back to back, CUDA events; the step with "
+                     "programmatic dependent launch" % reps}
+    for t in (Phat, Ptc, Mhat, sB, xA, xB, ct, A, R, out, yA, yB):
+        del t
+    torch.cuda.empty_cache()
+    P.close()
+    return res
+
+
 # the appendix network (MiniONN's CIFAR-10 network, Fig. 13 there): its six
 # convolution layers, (Ci, Co, H, filter, 2x2 pooling after); the
 # fully-connected layer and the activations are not part of the path
@@ -1070,6 +1208,7 @@ def run_gpu(args, rank, local_rank, world):
     batched = None if args.skip_batched else run_batched(F, flush, sleep_cycles, args)
     tensor = None if args.skip_batched else run_tensor_homconv(F, flush, args)
     chain = None if args.skip_batched else run_chain(F, flush, sleep_cycles, args)
+    binarized = None if args.skip_batched else run_binarized(F, sleep_cycles, args)
     serving = None if args.skip_serving else run_serving(F, args)
 
     local_sec = total_ms / 1e3
@@ -1163,11 +1302,12 @@ def run_gpu(args, rank, local_rank, world):
         "batched": batched,
         "homconv_tensor": tensor,
         "chain": chain,
+        "binarized": binarized,
         "serving": serving,
         "ntt2d_sweep": sweep,
         "primitive_rates": {k: {"ops_per_s": v[0], "ops_per_clk_per_sm": v[1]} for k, v in calib.items()},
         "gpu_launches": LAUNCHES_PER_STEP * (args.steps + len(step_ms)) + 6 * n_4s * R + 8 * n_unfused
-                        + 3 * hc_reps * R + 3 * n_pj
+                        + 3 * hc_reps * R + 3 * n_pj + (binarized["launches"] if binarized else 0)
                         + sum(pt["launches"] for pt in sweep["points"]),
         "homconv_variant": args.homconv_variant,
         "clocks": clk,

@@ -109,7 +109,7 @@ typedef struct {
     uint32_t n_in, n_out;       /* input ciphertexts GB T beta; outputs GB Co beta */
     uint64_t ct_in_words;       /* n_in  * 2 * n   (uint64)                       */
     uint64_t ct_out_words;      /* n_out * 2 * n                                  */
-    uint64_t filter_words;      /* Co * T * beta * n                              */
+    uint64_t filter_words;      /* Co * T * beta * n / d (one word per group of d) */
     uint64_t mask_words;        /* n_out * n                                      */
     uint64_t in_spectra_words;  /* B * Ci * H W    (uint32)                       */
     uint64_t out_spectra_words; /* B * Co * H W                                   */
@@ -148,8 +148,12 @@ int fdsc_keygen(const fdsc_params* P, uint64_t seed, uint64_t* t_hat, void* stre
 /* Fig. 2, Bob's filter transform: w_hat = flatten(NTT2D(W)) packed into plaintext
  * polynomials and lifted to NTT_q.  w: int8 [Co][Ci][fh][fw] (taps at the
  * top-left of the padded plane, fh <= H, fw <= W); P_hat: uint64
- * [Co][T][beta][n] -- plaintext (co, k, h) holds the spectra of channels
- * k g_c .. k g_c + g_c - 1 in its blocks, centred-lifted, at x^(d i). */
+ * [Co][T][beta][n / d] -- plaintext (co, k, h) holds the spectra of channels
+ * k g_c .. k g_c + g_c - 1 in its blocks, centred-lifted, at x^(d i), so it
+ * is a polynomial w_0(x^d) and takes one value on each group of d
+ * consecutive NTT_q indices (the points x times the d-th roots of unity):
+ * word i is the value of indices i d .. i d + d - 1 (with d = 1, one word per
+ * index). */
 int fdsc_filter_prepare(const fdsc_params* P, const fdsc_layer* L, const int8_t* w, uint32_t fh,
                         uint32_t fw, uint64_t* P_hat, void* stream);
 
@@ -192,7 +196,7 @@ int fdsc_homrec(const fdsc_params* P, const fdsc_layer* L, const uint32_t* XB, u
                 void* stream);
 
 /* Fig. 2, Bob's HomConv and HomShare (Eq. 2): ct_out[bb][co][h][c][j] = sum_k ct_in[bb][k][h][c][j]
- * P_hat[co][k][h][j] mod q, then c1 -= M_hat[bb][co][h] (HomShare; skipped
+ * P_hat[co][k][h][j / d] mod q, then c1 -= M_hat[bb][co][h] (HomShare; skipped
  * when M_hat is NULL).  ct_out: uint64 [GB][Co][beta][2][n]; must not alias
  * ct_in.  Exact: the sum is formed in 128 bits and reduced once per 256
  * terms. */
@@ -220,8 +224,11 @@ int fdsc_encrypt_constants(const fdsc_params* P, const fdsc_layer* L, const uint
 /* The message part of Alice's encryption in Fig. 2 (and of Bob's HomRec
  * plaintext) from a SPATIAL share
  * x: uint32 [B][Ci][H][W] -> NTT2D -> flatten and pack -> slot encode ->
- * times Delta -> NTT_q, written to A: uint64 [n_in][n].  Needs H W <= S and
- * H, W >= 8 (FDSC_ERR_UNSUPPORTED otherwise; use fdsc_ntt2d + fdsc_encrypt). */
+ * times Delta -> NTT_q, written to A: uint64 [n_in][n].  Needs
+ * 8 <= H, W <= 512 (FDSC_ERR_UNSUPPORTED otherwise; use fdsc_ntt2d +
+ * fdsc_encrypt).  When H W > S the spectrum of a channel spans beta
+ * ciphertexts: the kernel of ciphertext (bb, k, h) transforms the d image
+ * planes of its slot sets and keeps half h. */
 int fdsc_encode_share(const fdsc_params* P, const fdsc_layer* L, const uint32_t* x, uint64_t* A, void* stream);
 
 /* The three input-side producers of one online layer in ONE launch, with the
@@ -259,8 +266,8 @@ int fdsc_homconv_sum(const fdsc_params* P, const fdsc_layer* L, const uint64_t* 
  * into the 128-bit sum and reduced mod q once.
  * fdsc_filter_tc_words: the size in uint64 words of the digit-plane filter
  * for layer L at (n, p) (host only); FDSC_ERR_UNSUPPORTED if T > 128.
- * fdsc_filter_tc: P_hat uint64 [Co][T][beta][n] (fdsc_filter_prepare) ->
- * P_tc: per evaluation index J < beta n, block of 16 input ciphertexts and
+ * fdsc_filter_tc: P_hat uint64 [Co][T][beta][n / d] (fdsc_filter_prepare) ->
+ * P_tc: per group of d evaluation indices (beta n / d), block of 16 input ciphertexts and
  * tile of up to 128 output channels (rows rounded up to a multiple of 8),
  * the eight fp16 digit planes of the filter words in the canonical layout of
  * a tcgen05 A operand (256 bytes per row); twice the bytes of P_hat.  Setup,
@@ -376,7 +383,7 @@ typedef struct fdsc_plan fdsc_plan;
  * filters and masks, runs every layer once and records the graph; with
  * FDSC_PLAN_TUNE it first times every candidate packing x HomConv variant.
  * All of this runs on the plan's own streams and has finished on return
- * (`stream` is reserved).  Layers with H W > S or H, W outside [8, 512] use
+ * (`stream` is reserved).  Layers with H or W outside [8, 512] use
  * the step-by-step kernels. */
 int fdsc_plan_create(const fdsc_plan_layer* layers, uint32_t count, uint32_t flags, void* stream, fdsc_plan** out);
 /* One launch of the recorded graph: every layer's online path. */
@@ -431,8 +438,9 @@ typedef struct fdsc_server fdsc_server;
 /* A server for cfg on the current device (max_batch >= 1 and lanes >= 1,
  * FDSC_ERR_ARG otherwise); device memory is taken at fdsc_server_start. */
 int fdsc_server_create(const fdsc_server_config* cfg, fdsc_server** out);
-/* Registers a layer type (B is ignored; fused shapes only: H W <= S,
- * 8 <= H, W): prepares its filter plaintexts from device weights w and keeps
+/* Registers a layer type (B is ignored; fused shapes with H W <= S and one
+ * slot set per ciphertext, d = 1, since a batch packs one client per image
+ * group): prepares its filter plaintexts from device weights w and keeps
  * a pointer to its key pool (device [nkeys][n]). */
 int fdsc_server_add_type(fdsc_server* s, const fdsc_params* P, const fdsc_layer* L, const int8_t* w, uint32_t fh,
                          uint32_t fw, const uint64_t* keys, uint32_t nkeys, uint32_t* type_id);
@@ -469,7 +477,7 @@ int fdsc_server_destroy(fdsc_server* s);
  * fixed device array of FDSC_NOALLOC_SCRATCH_BYTES compiled into the library
  * (every device that loads the library holds it until the process exits).  It
  * calls no allocator.  Inputs and outputs are the caller's device buffers,
- * with the shapes of those calls (t_hat [n], P_hat [Co][T][n], M_hat
+ * with the shapes of those calls (t_hat [n], P_hat [Co][T][n / d], M_hat
  * [GB][Co][n], sB_hat, yA, yB [B][Co][H][W], xA, xB [B][Ci][H][W]).
  *
  *  - The first call in a CUDA context (per device, and again after a device

@@ -176,13 +176,13 @@ extern "C" int fdsc_decrypt(const fdsc_params* P, const fdsc_layer* L, const uin
 }
 
 // ---------------------------------------------------------------- fused online path
-// The fused spatial-domain kernels need whole spectra inside one ciphertext
-// (H W <= S), radix-8 lines (H, W >= 8) and their shared memory to fit.
+// The fused spatial-domain kernels need radix-8 lines (8 <= H, W <= 512)
+// and their shared memory to fit (a spectrum spanning several ciphertexts,
+// H W > S, keeps the d whole planes of its images on chip).
 int fdsc_check_fused(const fdsc_params* P, const DevLayer& D, size_t smem, const char* what) {
-    if (D.beta != 1 || D.logH < 3 || D.logW < 3 || D.logH > 9 || D.logW > 9)
+    if (D.logH < 3 || D.logW < 3 || D.logH > 9 || D.logW > 9)
         return fdsc_set_error(FDSC_ERR_UNSUPPORTED,
-                              "%s needs 8 <= H, W <= 512 and H W <= S; use fdsc_ntt2d/fdsc_encrypt/fdsc_decrypt",
-                              what);
+                              "%s needs 8 <= H, W <= 512; use fdsc_ntt2d/fdsc_encrypt/fdsc_decrypt", what);
     int optin = 0;
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
     if (e != cudaSuccess) return fdsc_set_error(FDSC_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
@@ -284,7 +284,7 @@ extern "C" int fdsc_filter_tc_words(uint32_t n, uint32_t p, const fdsc_layer* L,
     if ((rc = fdsc_make_layer(I, L, &D, nullptr))) return rc;
     if (!homconv_tc_supported(n, D))
         return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "the tensor-core HomConv needs T <= 128 (T = %u)", D.T);
-    *words = filter_tc_words(n, D);
+    *words = filter_tc_words(n, I.d, D);
     return FDSC_OK;
 }
 
@@ -298,7 +298,7 @@ extern "C" int fdsc_filter_tc(const fdsc_params* P, const fdsc_layer* L, const u
     if (!homconv_tc_supported(P->info.n, D))
         return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "the tensor-core HomConv needs T <= 128 (T = %u)", D.T);
     if ((rc = check_ptr(P_hat, "P_hat")) || (rc = check_ptr(P_tc, "P_tc"))) return rc;
-    if (overlap(P_hat, lay.filter_words * 8, P_tc, filter_tc_words(P->info.n, D) * 8))
+    if (overlap(P_hat, lay.filter_words * 8, P_tc, filter_tc_words(P->info.n, P->info.d, D) * 8))
         return fdsc_set_error(FDSC_ERR_ARG, "P_tc overlaps P_hat");
     return launched(launch_filter_tc(P->dev, D, P_hat, P_tc, (cudaStream_t)stream), "filter_tc");
 }
@@ -323,7 +323,7 @@ extern "C" int fdsc_homconv_tc(const fdsc_params* P, const fdsc_layer* L, const 
         return rc;
     const u64 ob = lay.ct_out_words * 8, ab = (u64)D.n_in * P->info.n * 8;
     if (overlap(ct_in, lay.ct_in_words * 8, ct_out, ob) || (A1 && overlap(A1, ab, ct_out, ob)) ||
-        (A2 && overlap(A2, ab, ct_out, ob)) || overlap(P_tc, filter_tc_words(P->info.n, D) * 8, ct_out, ob))
+        (A2 && overlap(A2, ab, ct_out, ob)) || overlap(P_tc, filter_tc_words(P->info.n, P->info.d, D) * 8, ct_out, ob))
         return fdsc_set_error(FDSC_ERR_ARG, "ct_out overlaps an input");
     return launched(launch_homconv_tc(P->dev, D, ct_in, A1, A2, P_tc, M_hat, ct_out, (cudaStream_t)stream),
                     "homconv_tc");

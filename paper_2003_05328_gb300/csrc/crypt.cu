@@ -162,8 +162,11 @@ __global__ void __launch_bounds__(kMaxThreads) filter_kernel(DevParams P, DevLay
     }
     __syncthreads();
     ntt_q_fwd8(c, P);
-    u64* out = Phat + (u64)v * P.n;
-    for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) out[j] = c[j];
+    // w(x) = w_0(x^d): the d consecutive evaluation indices of one group
+    // (the points x times the d-th roots of unity) share one value, stored once
+    const u32 nd = P.n / P.d;
+    u64* out = Phat + (u64)v * nd;
+    for (u32 i = threadIdx.x; i < nd; i += blockDim.x) out[i] = c[(u64)i * P.d];
 }
 
 // ---------------------------------------------------------------- mask prepare

@@ -122,7 +122,7 @@ int homconv_default_variant(const DevLayer& L);
 int homconv_effective_variant(const DevLayer& L, int variant);
 // tensor-core HomConv (homconv_tc.cu)
 bool homconv_tc_supported(u32 n, const DevLayer& L);
-u64 filter_tc_words(u32 n, const DevLayer& L);
+u64 filter_tc_words(u32 n, u32 d, const DevLayer& L);
 cudaError_t launch_filter_tc(const DevParams& P, const DevLayer& L, const u64* Phat, u64* Ptc, cudaStream_t s);
 cudaError_t launch_homconv_tc(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
                               const u64* Ptc, const u64* Mhat, u64* ct_out, cudaStream_t s);

@@ -142,6 +142,14 @@ __device__ __forceinline__ void acc_set(AccLazy& a, u64 r) {
 }
 
 __device__ __forceinline__ ulonglong2 ldg2(const u64* p) { return __ldg(reinterpret_cast<const ulonglong2*>(p)); }
+// The filter words of two consecutive evaluation indices (the first even):
+// a pair when every index has its own word (d = 1), else the one word the
+// group of d shares (filter plaintexts are w_0(x^d)).
+__device__ __forceinline__ ulonglong2 ldgw2(const u64* p, u32 d) {
+    if (d == 1) return ldg2(p);
+    const u64 w = __ldg(p);
+    return make_ulonglong2(w, w);
+}
 
 // kAdd extra c1 addends A1, A2 ([n_in][n] words) are added to every input
 // ciphertext's c1 as it is loaded (HomRec of Bob's encoded share, and the
@@ -177,8 +185,8 @@ __global__ void __launch_bounds__(kThreads) homconv_kernel(DevParams P, DevLayer
             acc_zero(acc[b][e][1]);
         }
 
-    const u64 w_step = beta * n, x_step = beta * 2 * n;
-    const u64* wp = Phat + ((u64)co * T * beta + h) * n + j;
+    const u64 nd = n / P.d, w_step = beta * nd, x_step = beta * 2 * n;
+    const u64* wp = Phat + ((u64)co * T * beta + h) * nd + j / P.d;
     const u64* xp[NB];
     u64 ap[NB];
 #pragma unroll
@@ -193,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) homconv_kernel(DevParams P, DevLayer
 #pragma unroll
         for (int u = 0; u < (int)kUnroll; u++) {
             if (k0 + u < L.T) {
-                wv[u] = ldg2(wp + (k0 + u) * w_step);
+                wv[u] = ldgw2(wp + (k0 + u) * w_step, P.d);
 #pragma unroll
                 for (int b = 0; b < NB; b++) {
                     xv[b][u][0] = ldg2(xp[b] + (k0 + u) * x_step);
@@ -351,8 +359,9 @@ __global__ void __launch_bounds__(kThreads3) homconv3_kernel(DevParams P, DevLay
     const u32 lane = threadIdx.x & 31, co = ct * kW3 + (threadIdx.x >> 5), J = jt * kJ3 + lane;
     if (co >= L.Co || J >= nJ) return;
     const u32 h = J >> P.logn, j = J & (P.n - 1);
-    const u64* wp = Phat + ((u64)co * T * beta + h) * n + j;
-    const u64 w_step = beta * n;
+    const u64 nd = n / P.d;
+    const u64* wp = Phat + ((u64)co * T * beta + h) * nd + j / P.d;
+    const u64 w_step = beta * nd;
 
     Acc acc0, acc1;
     acc_zero(acc0);
@@ -508,8 +517,9 @@ __global__ void __launch_bounds__(kThreads4, NB == 1 ? 4 : 2)
     const u32 lane = threadIdx.x & 31, co = ct * kW4 + (threadIdx.x >> 5), J = jt * kJ4 + lane;
     if (co >= L.Co || J >= nJ) return;
     const u32 h = J >> P.logn, j = J & (P.n - 1);
-    const u64* wp = Phat + ((u64)co * T * beta + h) * n + j;
-    const u64 w_step = beta * n;
+    const u64 nd = n / P.d;
+    const u64* wp = Phat + ((u64)co * T * beta + h) * nd + j / P.d;
+    const u64 w_step = beta * nd;
 
     AccK acc[NB][2];
     u64 base[kFold ? NB : 1][2];  // residues of the folded 256-term windows (kFold only)
@@ -608,13 +618,14 @@ __global__ void __launch_bounds__(kThreads5, 2)
     const u32 J = jt * kJ5 + 2 * lane;  // J and J + 1 lie in the same half (n even)
     const bool active = co < L.Co && J < nJ;
     const u32 h = J >> P.logn, j = J & (P.n - 1);
-    const u64* wp = Phat + ((u64)(active ? co : 0) * T * beta + (active ? h : 0)) * n + (active ? j : 0);
-    const u64 w_step = beta * n;
+    const u64 nd = n / P.d;
+    const u64* wp = Phat + ((u64)(active ? co : 0) * T * beta + (active ? h : 0)) * nd + (active ? j / P.d : 0);
+    const u64 w_step = beta * nd;
     griddep_release();
     griddep_wait();
     ulonglong2 ring[kTU];
 #pragma unroll
-    for (int u = 0; u < kTU; u++) ring[u] = active ? ldg2(wp + (u64)u * w_step) : make_ulonglong2(0, 0);
+    for (int u = 0; u < kTU; u++) ring[u] = active ? ldgw2(wp + (u64)u * w_step, P.d) : make_ulonglong2(0, 0);
     for (u32 e = threadIdx.x; e < T * kPairs; e += kThreads5) {
         const u32 k = e / kPairs, jp = e % kPairs, Jx = jt * kJ5 + 2 * jp;
         ulonglong2 x0 = make_ulonglong2(0, 0), x1 = make_ulonglong2(0, 0);
@@ -650,7 +661,7 @@ __global__ void __launch_bounds__(kThreads5, 2)
         for (int u = 0; u < kTU; u++) {
             const u32 k = k0 + u;
             const ulonglong2 w = ring[u];
-            if (k + kTU < T) ring[u] = ldg2(wp + (u64)(k + kTU) * w_step);
+            if (k + kTU < T) ring[u] = ldgw2(wp + (u64)(k + kTU) * w_step, P.d);
             const ulonglong2 xa = xs5[(k * 2 + 0) * kPairs + lane], xb = xs5[(k * 2 + 1) * kPairs + lane];
             acc_mac(acc[0][0], xa.x, w.x);
             acc_mac(acc[1][0], xa.y, w.y);
@@ -691,6 +702,14 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* g) {
                  : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// A thread's filter pair: 16 bytes, or the 8 bytes both indices share
+__device__ __forceinline__ void cp_async_w(void* smem, const void* g, bool shared_w) {
+    if (shared_w)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((u32)__cvta_generic_to_shared(smem)), "l"(g)
+                     : "memory");
+    else
+        cp_async16(smem, g);
+}
 
 template <int kD>
 __global__ void __launch_bounds__(kThreads5, 2)
@@ -711,13 +730,15 @@ __global__ void __launch_bounds__(kThreads5, 2)
     const u32 J = jt * kJ5 + 2 * lane;  // J and J + 1 lie in the same half (n even)
     const bool active = co < L.Co && J < nJ;
     const u32 h = J >> P.logn, j = J & (P.n - 1);
-    const u64* wp = Phat + ((u64)(active ? co : 0) * T * beta + (active ? h : 0)) * n + (active ? j : 0);
-    const u64 w_step = beta * n;
+    const u64 nd = n / P.d;
+    const u64* wp = Phat + ((u64)(active ? co : 0) * T * beta + (active ? h : 0)) * nd + (active ? j / P.d : 0);
+    const u64 w_step = beta * nd;
+    const bool shared_w = P.d > 1;  // both indices use one filter word (copied as 8 bytes)
     griddep_release();
     griddep_wait();
 #pragma unroll
     for (int u = 0; u < kD; u++) {
-        if (active && (u32)u < T) cp_async16(ring + u * kThreads5, wp + (u64)u * w_step);
+        if (active && (u32)u < T) cp_async_w(ring + u * kThreads5, wp + (u64)u * w_step, shared_w);
         cp_commit();
     }
     ulonglong2 m = make_ulonglong2(0, 0);
@@ -761,14 +782,15 @@ __global__ void __launch_bounds__(kThreads5, 2)
             const u32 k = k0 + u;
             if (k < T) {
                 asm volatile("cp.async.wait_group %0;" ::"n"(kD - 1) : "memory");
-                const ulonglong2 w = ring[u * kThreads5];
+                ulonglong2 w = ring[u * kThreads5];
+                if (shared_w) w.y = w.x;
                 const ulonglong2 xa = xs[(k * 2 + 0) * kPairs + lane], xb = xs[(k * 2 + 1) * kPairs + lane];
                 acc_mac(acc[0][0], xa.x, w.x);
                 acc_mac(acc[1][0], xa.y, w.y);
                 acc_mac(acc[0][1], xb.x, w.x);
                 acc_mac(acc[1][1], xb.y, w.y);
                 // the slot is refilled only after its words were used
-                if (k + kD < T) cp_async16(ring + u * kThreads5, wp + (u64)(k + kD) * w_step);
+                if (k + kD < T) cp_async_w(ring + u * kThreads5, wp + (u64)(k + kD) * w_step, shared_w);
                 cp_commit();
             }
         }

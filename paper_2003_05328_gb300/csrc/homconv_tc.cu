@@ -297,8 +297,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 if (!mbar_wait(b_sempty + 8 * s, ((u / G.NC) & 1) ^ 1, abort)) break;
                 const u32 rp = tile_rows8(L.Co, it.ct), bytes = 256 * rp;
                 mbar_expect_tx(bar, bytes);
+                // indices J of one group of d share their filter unit (w_0(x^d) plaintexts)
                 bulk_g2s(smem_u32(sm + G.off_slot + s * G.ssz),
-                         Ptc + ((u64)(it.J * G.KB + it.kb) * G.co_pad + it.ct * 128) * 256, bytes, bar);
+                         Ptc + ((u64)((it.J / P.d) * G.KB + it.kb) * G.co_pad + it.ct * 128) * 256, bytes, bar);
             }
             if (u < total_units) {
                 *abort = 1;
@@ -526,8 +527,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
 }
 
-// Phat [Co][T][beta][n] -> Ptc: per (J, 16-ciphertext block kb, 128-channel
-// tile of R rows, R rounded up to rp, a multiple of 8) one contiguous unit of
+// Phat [Co][T][beta][n/d] -> Ptc: per (group of d evaluation indices J' = J / d,
+// 16-ciphertext block kb, 128-channel tile of R rows, R rounded up to rp, a
+// multiple of 8) one contiguous unit of
 // 256 rp bytes holding the eight fp16 digit planes of the filter words in the
 // canonical no-swizzle K-major layout of a tcgen05 A operand: plane a at
 // 32 rp a bytes, row r / k in the plane at (r / 8) 256 + (k / 8) 128 +
@@ -535,7 +537,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 __global__ void filter_tc_kernel(const DevParams P, const DevLayer L, u32 KB, u32 co_pad,
                                  const u64* __restrict__ Phat, unsigned char* __restrict__ Ptc) {
     __shared__ u64 tile[16][65];
-    const u32 nJ = L.beta * P.n;
+    const u32 nJ = L.beta * P.n / P.d;  // distinct filter words per (co, k)
     const u32 J0 = blockIdx.x * 64, kb = blockIdx.y, co = blockIdx.z;
     const u32 ct = co / 128, rl = co % 128, rp = tile_rows8(L.Co, ct);
     for (u32 e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
@@ -598,16 +600,17 @@ bool homconv_tc_supported(u32 n, const DevLayer& L) {
 }
 
 // Words (u64) of the tensor-core filter layout: 256 bytes per row per
-// (J, ciphertext block), rows padded per tile to a multiple of 8.
-u64 filter_tc_words(u32 n, const DevLayer& L) {
+// (group of d evaluation indices, ciphertext block), rows padded per tile to
+// a multiple of 8.
+u64 filter_tc_words(u32 n, u32 d, const DevLayer& L) {
     const u32 n_ct = (L.Co + 127) / 128, co_pad = 128 * (n_ct - 1) + tile_rows8(L.Co, n_ct - 1);
-    return (u64)L.beta * n * ((L.T + 15) / 16) * co_pad * 32;
+    return (u64)L.beta * (n / d) * ((L.T + 15) / 16) * co_pad * 32;
 }
 
 cudaError_t launch_filter_tc(const DevParams& P, const DevLayer& L, const u64* Phat, u64* Ptc, cudaStream_t s) {
-    const u32 nJ = L.beta * P.n, KB = (L.T + 15) / 16;
+    const u32 nJ = L.beta * P.n / P.d, KB = (L.T + 15) / 16;
     const u32 n_ct = (L.Co + 127) / 128, co_pad = 128 * (n_ct - 1) + tile_rows8(L.Co, n_ct - 1);
-    cudaError_t e = cudaMemsetAsync(Ptc, 0, filter_tc_words(P.n, L) * 8, s);  // padding rows stay zero
+    cudaError_t e = cudaMemsetAsync(Ptc, 0, filter_tc_words(P.n, P.d, L) * 8, s);  // padding rows stay zero
     if (e != cudaSuccess) return e;
     dim3 grid((nJ + 63) / 64, KB, L.Co);
     filter_tc_kernel<<<grid, 128, 0, s>>>(P, L, KB, co_pad, Phat, reinterpret_cast<unsigned char*>(Ptc));

@@ -194,7 +194,7 @@ int fdsc_make_layer(const fdsc_params_info& I, const fdsc_layer* L, DevLayer* D,
         lay->n_in = d.n_in; lay->n_out = d.n_out;
         lay->ct_in_words = n_in * 2 * I.n;
         lay->ct_out_words = n_out * 2 * I.n;
-        lay->filter_words = (u64)d.Co * d.T * d.beta * I.n;
+        lay->filter_words = (u64)d.Co * d.T * d.beta * (I.n / I.d);
         lay->mask_words = n_out * I.n;
         lay->in_spectra_words = (u64)d.B * d.Ci * d.HW;
         lay->out_spectra_words = (u64)d.B * d.Co * d.HW;

@@ -135,8 +135,34 @@ __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P
     uint2* tw_col = tw_row + (L.W >> 1);                 // [H/2]
     u64* c = reinterpret_cast<u64*>(tw_col + (L.H >> 1));  // padded [n]
     u32* slots = reinterpret_cast<u32*>(c + np);         // padded [n] = d slot sets
-    const u32 k = u % L.T, bb = u / L.T;
+    u32* planes = slots + np;                            // beta > 1: padded [d][HW], the d images' planes
+    const u32 h = u % L.beta, k = (u / L.beta) % L.T, bb = u / (L.beta * L.T);
     const u32 HW = L.HW, logHW = L.logH + L.logW, blocks = L.g_c * L.g_b;
+    if (L.beta > 1) {
+        // a spectrum spans beta ciphertexts (H W > S, g_c = g_b = 1): slot set r
+        // of this ciphertext holds half h of the spectrum of channel k of image
+        // bb d + r, so the CTA transforms the d whole planes and keeps half h
+        for (u32 e = threadIdx.x; e < P.d * HW; e += blockDim.x) {
+            const u32 r = e >> logHW, f = e & (HW - 1), b = bb * P.d + r;
+            const u32 pos = (r << logHW) + (brv_bits(f >> L.logW, L.logH) << L.logW) + brv_bits(f & (L.W - 1), L.logW);
+            planes[padx(pos)] = b < L.B ? __ldg(x + ((u64)b * L.Ci + k) * HW + f) : 0u;
+        }
+        stage_pairs_for_length(tw_row, L.logW, false, P);  // group 3
+        stage_pairs_for_length(tw_col, L.logH, false, P);  // group 2
+        stage_async(tp, P.pinv2, S * 8);                    // group 1
+        stage_async(tq, P.qfw2, n * 16);                    // group 0
+        if (pf) pf->issue();
+        stage_wait_groups<2>();
+        for (u32 r = 0; r < P.d; r++) {  // one plane per pass: H W / 8 <= blockDim threads
+            lines_r8p<false>(planes + padx(r * HW), 1, true, L.logH, L.logW, tw_row, P.p);
+            lines_r8p<false>(planes + padx(r * HW), 1, false, L.logH, L.logW, tw_col, P.p);
+        }
+        for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
+            const u32 r = e >> P.logS, s = e & (S - 1);
+            slots[padx(e)] = planes[padx((r << logHW) + h * S + s)];
+        }
+        __syncthreads();
+    } else {
     // every load is issued before anything waits: the share's words (eight
     // per thread), then the twiddle tables in the order they are needed
     auto load8 = [&](u32 e0, u32 (&v)[8]) {
@@ -176,6 +202,7 @@ __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P
     // NTT2D of every plane (zero planes included): rows, then columns
     lines_r8p<false>(slots, n >> logHW, true, L.logH, L.logW, tw_row, P.p);
     lines_r8p<false>(slots, n >> logHW, false, L.logH, L.logW, tw_col, P.p);
+    }
     stage_wait_groups<1>();
     ntt_r8p<false, u32>(slots, P.logS, P.d, tp, P.Sinv, P.Sinv_s, P);  // slot encode
     for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
@@ -236,6 +263,8 @@ __device__ __forceinline__ u32 round_pq2(u64 v, const DevParams& P) {
     return (u32)(z >= P.p ? z - P.p : z);
 }
 
+// kMulti: a spectrum spans L.beta > 1 ciphertexts (H W > S); otherwise one.
+template <bool kMulti>
 __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
                                                                     u64 key_stride, const u64* __restrict__ ct,
                                                                     u32* __restrict__ y, u32 scale, u32 scale_s) {
@@ -254,51 +283,76 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
     griddep_release();
     griddep_wait();
 
-    const u32 v = blockIdx.x, co = v % L.Co, bb = v / L.Co;
+    // one CTA per (image group, output channel): with H W > S its spectrum
+    // spans beta ciphertexts (g_b = 1), decrypted one after the other into
+    // the halves of the d planes
+    const u32 vv = blockIdx.x, co = vv % L.Co, bb = vv / L.Co;
+    const u32 beta = kMulti ? L.beta : 1u;
     t_hat += (u64)bb * key_stride;
-    const u64* c0 = ct + (u64)v * 2 * n;
-    const u64* c1 = c0 + n;
-    // v = c0 t + c1: all of a thread's words (n / blockDim <= 8 of each) are
-    // requested at once, before the twiddle tables, which are copied in the
-    // order they are needed
-    u64 a[8], t[8], b[8];
+#pragma unroll 1
+    for (u32 h = 0; h < beta; h++) {
+        const u64* c0 = ct + ((u64)vv * beta + h) * 2 * n;
+        const u64* c1 = c0 + n;
+        // v = c0 t + c1: all of a thread's words (n / blockDim <= 8 of each) are
+        // requested at once, before the twiddle tables, which are copied in the
+        // order they are needed
+        u64 a[8], t[8], b[8];
 #pragma unroll
-    for (int r = 0; r < 8; r++) {
-        const u32 j = threadIdx.x + (u32)r * blockDim.x;
-        if (j < n) {
-            a[r] = __ldg(c0 + j);
-            t[r] = __ldg(t_hat + j);
-            b[r] = __ldg(c1 + j);
+        for (int r = 0; r < 8; r++) {
+            const u32 j = threadIdx.x + (u32)r * blockDim.x;
+            if (j < n) {
+                a[r] = __ldg(c0 + j);
+                t[r] = __ldg(t_hat + j);
+                b[r] = __ldg(c1 + j);
+            }
         }
-    }
-    stage_async(tq, P.qinv2, n * 16);                  // group 3
-    stage_async(tp, P.pfw2, S * 8);                    // group 2
-    stage_pairs_for_length(tw_row, L.logW, true, P);  // group 1
-    stage_pairs_for_length(tw_col, L.logH, true, P);  // group 0
+        if (h == 0) {
+            stage_async(tq, P.qinv2, n * 16);                  // group 3
+            stage_async(tp, P.pfw2, S * 8);                    // group 2
+            stage_pairs_for_length(tw_row, L.logW, true, P);  // group 1
+            stage_pairs_for_length(tw_col, L.logH, true, P);  // group 0
+        }
 #pragma unroll
-    for (int r = 0; r < 8; r++) {
-        const u32 j = threadIdx.x + (u32)r * blockDim.x;
-        if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
-    }
-    stage_wait_groups<3>();
-    ntt_r8p<false, u64>(c, P.logn, 1, tq, P.ninv, P.ninv_s, P);
-    for (u32 coef = threadIdx.x; coef < n; coef += blockDim.x) {
-        const u32 r = coef & (P.d - 1), i = coef / P.d;
-        slots[padx(r * S + i)] = round_pq2(c[padx(coef)], P);
-    }
-    stage_wait_groups<2>();
-    ntt_r8p<true, u32>(slots, P.logS, P.d, tp, 0, 0, P);  // slot decode
-    // fold the g_c channel blocks of every image block: plane (r, ib)
-    for (u32 e = threadIdx.x; e < nplanes * HW; e += blockDim.x) {
-        const u32 pl = e >> logHW, f = e & (HW - 1), r = pl / L.g_b, ib = pl % L.g_b;
-        const u32 src = r * S + ib * L.g_c * HW + f;
-        u32 acc = 0;
-        for (u32 ic = 0; ic < L.g_c; ic++) acc = addmod_p(acc, slots[padx(src + ic * HW)], P.p);
-        planes[padx(e)] = acc;
+        for (int r = 0; r < 8; r++) {
+            const u32 j = threadIdx.x + (u32)r * blockDim.x;
+            if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
+        }
+        stage_wait_groups<3>();
+        ntt_r8p<false, u64>(c, P.logn, 1, tq, P.ninv, P.ninv_s, P);
+        for (u32 coef = threadIdx.x; coef < n; coef += blockDim.x) {
+            const u32 r = coef & (P.d - 1), i = coef / P.d;
+            slots[padx(r * S + i)] = round_pq2(c[padx(coef)], P);
+        }
+        stage_wait_groups<2>();
+        ntt_r8p<true, u32>(slots, P.logS, P.d, tp, 0, 0, P);  // slot decode
+        if (!kMulti) {
+            // fold the g_c channel blocks of every image block: plane (r, ib)
+            for (u32 e = threadIdx.x; e < nplanes * HW; e += blockDim.x) {
+                const u32 pl = e >> logHW, f = e & (HW - 1), r = pl / L.g_b, ib = pl % L.g_b;
+                const u32 src = r * S + ib * L.g_c * HW + f;
+                u32 acc = 0;
+                for (u32 ic = 0; ic < L.g_c; ic++) acc = addmod_p(acc, slots[padx(src + ic * HW)], P.p);
+                planes[padx(e)] = acc;
+            }
+        } else {
+            // slot set r holds half h of image bb d + r's spectrum
+            for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
+                const u32 r = e >> P.logS, s = e & (S - 1);
+                planes[padx((r << logHW) + h * S + s)] = slots[padx(e)];
+            }
+        }
+        __syncthreads();
     }
     stage_wait_groups<0>();
-    lines_r8p<true>(planes, nplanes, true, L.logH, L.logW, tw_row, P.p);
-    lines_r8p<true>(planes, nplanes, false, L.logH, L.logW, tw_col, P.p);
+    if (!kMulti) {
+        lines_r8p<true>(planes, nplanes, true, L.logH, L.logW, tw_row, P.p);
+        lines_r8p<true>(planes, nplanes, false, L.logH, L.logW, tw_col, P.p);
+    } else {
+        for (u32 r = 0; r < nplanes; r++) {  // one plane per pass: H W / 8 <= blockDim threads
+            lines_r8p<true>(planes + padx(r * HW), 1, true, L.logH, L.logW, tw_row, P.p);
+            lines_r8p<true>(planes + padx(r * HW), 1, false, L.logH, L.logW, tw_col, P.p);
+        }
+    }
     for (u32 e = threadIdx.x; e < nplanes * HW; e += blockDim.x) {
         const u32 pl = e >> logHW, f = e & (HW - 1), r = pl / L.g_b, ib = pl % L.g_b;
         const u32 b = (bb * P.d + r) * L.g_b + ib;
@@ -471,12 +525,19 @@ cudaError_t opt_in(K kernel, size_t bytes) {
 }  // namespace
 
 size_t share_smem_bytes(const DevParams& P, const DevLayer& L) {
-    const size_t np = padded_len(P.n);
-    return (size_t)P.n * 16 + np * 8 + (size_t)P.S * 8 + np * 4 + (size_t)4 * (L.W + L.H);
+    const size_t np = padded_len(P.n), npl = L.beta > 1 ? padded_len(P.d * L.HW) : 0;
+    return (size_t)P.n * 16 + np * 8 + (size_t)P.S * 8 + np * 4 + npl * 4 + (size_t)4 * (L.W + L.H);
 }
 size_t decrypt_share_smem_bytes(const DevParams& P, const DevLayer& L) {
     const size_t np = padded_len(P.n), npl = padded_len(P.d * L.g_b * L.HW);
     return (size_t)P.n * 16 + np * 8 + (size_t)P.S * 8 + np * 4 + npl * 4 + (size_t)4 * (L.W + L.H);
+}
+// Threads of the fused kernels: n / 8 for the length-n passes, and at least
+// H W / 8 for the line passes of one plane (more than n / 8 only when a
+// spectrum spans several ciphertexts).
+u32 fused_threads(const DevParams& P, const DevLayer& L) {
+    const u32 t = threads_for(P.n), tl = L.HW / 8;
+    return t > tl ? t : tl;
 }
 size_t constants_smem_bytes(const DevParams& P) { return (size_t)P.n * 24 + (size_t)padded_len(P.n) * 8; }
 
@@ -494,7 +555,8 @@ cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u6
     const size_t sm = share_smem_bytes(P, L);
     cudaError_t e = add_to_ct ? opt_in(share_kernel<1>, sm) : opt_in(share_kernel<0>, sm);
     if (e != cudaSuccess) return e;
-    return launch_online(add_to_ct ? share_kernel<1> : share_kernel<0>, L.n_in, threads_for(P.n), sm, s, P, L, x, out);
+    return launch_online(add_to_ct ? share_kernel<1> : share_kernel<0>, L.n_in, fused_threads(P, L), sm, s, P, L, x,
+                         out);
 }
 
 size_t produce_smem_bytes(const DevParams& P, const DevLayer& L) {
@@ -509,8 +571,8 @@ cudaError_t launch_produce(const DevParams& P, const DevLayer& L, const u64* t_h
     cudaError_t e = opt_in(produce_kernel, sm);
     if (e != cudaSuccess) return e;
     L2Prefetch pf = {{pf0, pf1}, {pf0_bytes, pf1_bytes}, 0, 0};
-    return launch_online(produce_kernel, 3 * L.n_in, threads_for(P.n), sm, s, P, L, t_hat, seed, xA, xB, ct, A, R,
-                         pf);
+    return launch_online(produce_kernel, 3 * L.n_in, fused_threads(P, L), sm, s, P, L, t_hat, seed, xA, xB, ct, A,
+                         R, pf);
 }
 
 cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, const u64* ct,
@@ -523,7 +585,7 @@ cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u6
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    if (P.d == 1 && P.n >= 32 && 2ull * L.n_out <= (u64)sms) {
+    if (P.d == 1 && L.beta == 1 && P.n >= 32 && 2ull * L.n_out <= (u64)sms) {
         // one slot set and fewer output ciphertexts than half the SMs (a single
         // image): the two CTAs of a cluster take one parity of the coefficients
         // each, on SMs that would otherwise idle; batched work keeps one CTA per
@@ -533,8 +595,9 @@ cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u6
         return launch_online(decrypt_share_pair_kernel, 2 * L.n_out, threads_for(P.n), sm, s, P, L, t_hat, key_stride,
                              ct, y, scale, fdsc_shoup32(scale, P.p));
     }
-    cudaError_t e = opt_in(decrypt_share_kernel, sm);
+    auto kern = L.beta > 1 ? decrypt_share_kernel<true> : decrypt_share_kernel<false>;
+    cudaError_t e = opt_in(kern, sm);
     if (e != cudaSuccess) return e;
-    return launch_online(decrypt_share_kernel, L.n_out, threads_for(P.n), sm, s, P, L, t_hat, key_stride, ct, y, scale,
+    return launch_online(kern, L.n_out / L.beta, fused_threads(P, L), sm, s, P, L, t_hat, key_stride, ct, y, scale,
                          fdsc_shoup32(scale, P.p));
 }

@@ -63,7 +63,9 @@ void default_pack(const fdsc_params_info& I, const fdsc_layer& L, uint32_t* g_c,
     *g_c = std::max(1u, std::min(L.Ci, g));
 }
 
-bool fused_ok(const DevLayer& D) { return D.beta == 1 && D.logH >= 3 && D.logW >= 3 && D.logH <= 9 && D.logW <= 9; }
+// The fused online kernels take radix-8 plane lines (8 <= H, W <= 512);
+// spectra spanning several ciphertexts (H W > S) included.
+bool fused_ok(const DevLayer& D) { return D.logH >= 3 && D.logW >= 3 && D.logH <= 9 && D.logW <= 9; }
 
 }  // namespace
 
@@ -111,7 +113,7 @@ cudaError_t plan_homconv(const DevParams& P, const PlanLayer& pl, const u64* A1,
 int plan_alloc_layer(PlanLayer& pl, Arena& ar, fdsc_layout& lay) {
     const fdsc_params_info& I = pl.spec.params->info;
     int rc;
-    if (pl.variant == kTensorVariant && (rc = ar.alloc((void**)&pl.Ptc, filter_tc_words(I.n, pl.D) * 8))) return rc;
+    if (pl.variant == kTensorVariant && (rc = ar.alloc((void**)&pl.Ptc, filter_tc_words(I.n, I.d, pl.D) * 8))) return rc;
     if ((rc = ar.alloc((void**)&pl.Phat, lay.filter_words * 8)) || (rc = ar.alloc((void**)&pl.Mhat, lay.mask_words * 8)) ||
         (rc = ar.alloc((void**)&pl.sB, lay.out_spectra_words * 4)) || (rc = ar.alloc((void**)&pl.ct, lay.ct_in_words * 8)) ||
         (rc = ar.alloc((void**)&pl.ct_out, lay.ct_out_words * 8)))
@@ -830,7 +832,12 @@ extern "C" int fdsc_server_add_type(fdsc_server* S, const fdsc_params* P, const 
     if (t.L.g_c == 0) default_pack(P->info, t.L, &t.L.g_c, &t.L.g_b);
     int rc = fdsc_make_layer(P->info, &t.L, &t.D1, &t.lay1);
     if (rc) return rc;
-    if (!fused_ok(t.D1)) return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "served layers need H W <= S and 8 <= H, W <= 512");
+    if (!fused_ok(t.D1) || t.D1.beta != 1)
+        return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "served layers need H W <= S and 8 <= H, W <= 512");
+    // a batch packs one request per image group; with d > 1 slot sets the d
+    // images of a group would share one ciphertext, and so one client key
+    if (P->info.d != 1)
+        return fdsc_set_error(FDSC_ERR_UNSUPPORTED, "served layers need one slot set per ciphertext (d = 1)");
     if (t.D1.T > P->max_T) return fdsc_set_error(FDSC_ERR_NOISE, "T = %u exceeds the params' max_T", t.D1.T);
     if (fh == 0 || fw == 0 || fh > t.D1.H || fw > t.D1.W) return fdsc_set_error(FDSC_ERR_ARG, "filter does not fit");
     t.keys = keys;
@@ -846,7 +853,7 @@ extern "C" int fdsc_server_add_type(fdsc_server* S, const fdsc_params* P, const 
     const bool tensor = S->cfg.max_batch >= kServerTensorMinImages &&
                         fdsc_make_layer(P->info, &Lmax, &Dmax, nullptr) == FDSC_OK &&
                         homconv_tc_supported(P->info.n, Dmax);
-    if (tensor && (rc = S->arena.alloc((void**)&t.Ptc, filter_tc_words(P->info.n, t.D1) * 8))) return rc;
+    if (tensor && (rc = S->arena.alloc((void**)&t.Ptc, filter_tc_words(P->info.n, P->info.d, t.D1) * 8))) return rc;
     cudaError_t e = launch_filter_prepare(P->dev, t.D1, w, fh, fw, t.Phat, 0);
     if (e == cudaSuccess && tensor) e = launch_filter_tc(P->dev, t.D1, t.Phat, t.Ptc, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -39,7 +39,12 @@ def gpu_round_trip(P, L, xA, xB, w, ks, es, ss, homrec=True):
     out["yA"] = F.intt2d(P, SA.view(L.B, L.Co, H, W))
     out["yB"] = F.intt2d(P, sB.view(L.B, L.Co, H, W))
     torch.cuda.synchronize()
-    return {k: (u64(v) if v.dtype == torch.int64 else u32(v)) for k, v in out.items()}
+    res = {k: (u64(v) if v.dtype == torch.int64 else u32(v)) for k, v in out.items()}
+    # filter plaintexts are stored once per group of d evaluation indices
+    # (w_0(x^d) takes one value on each group): expand to the oracle's layout
+    d = P.info.d
+    res["Phat"] = np.repeat(res["Phat"].reshape(-1, P.n // d), d, axis=1).reshape(-1)
+    return res
 
 
 def compare_all(got, ref, keys=None):

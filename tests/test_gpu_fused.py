@@ -38,6 +38,10 @@ CASES = [
     dict(n=1024, p=65537, B=1, Ci=2, Co=2, H=8, W=128, fh=3, fw=5),                # wide plane
     dict(n=2048, p=147457, B=1, Ci=64, Co=64, H=32, W=32, fh=3),                   # Table 2 "Medium" prime
     dict(n=1024, p=786433, B=3, Ci=6, Co=3, H=16, W=16, fh=3, g_c=2, g_b=2),       # p = 3 2^18 + 1, near 2^20
+    # spectra spanning several ciphertexts (H W > S)
+    dict(n=4096, p=12289, B=3, Ci=3, Co=2, H=64, W=64, fh=3, g_c=1),              # d = 2, beta = 2, ragged B
+    dict(n=1024, p=65537, B=1, Ci=2, Co=2, H=64, W=64, fh=3, g_c=1),              # d = 1, beta = 4
+    dict(n=2048, p=65537, B=2, Ci=3, Co=2, H=32, W=128, fh=3, fw=5, g_c=1),        # beta = 2, wide plane
 ]
 
 
@@ -96,12 +100,7 @@ def test_fused_path_bit_exact(F, args):
 
 def test_fused_path_rejects_unsupported_shapes(F):
     P = F.Params(1024, 65537)
-    L = F.LayerSpec(1, 2, 2, 64, 64, 1, 1)  # H W = 4096 > S = 1024: spectra span several ciphertexts
-    x = torch.zeros(2 * 64 * 64, dtype=torch.int32, device="cuda")
-    with pytest.raises(F.FdscError) as e:
-        F.encode_share(P, L, x)
-    assert e.value.code == -5
-    L2 = F.LayerSpec(1, 2, 2, 4, 64, 1, 1)  # H = 4 < 8
+    L2 = F.LayerSpec(1, 2, 2, 4, 64, 1, 1)  # H = 4 < 8: no radix-8 column passes
     with pytest.raises(F.FdscError) as e:
         F.encode_share(P, L2, torch.zeros(2 * 4 * 64, dtype=torch.int32, device="cuda"))
     assert e.value.code == -5
@@ -145,4 +144,37 @@ def test_multi_client_batch_equals_single_requests(F):
         assert np.array_equal(yB_n[i], ref["yB"][0]), i
         y = O.conv_plain(p, (xA[i:i + 1].astype(np.int64) + xB[i:i + 1]) % p, w)[0]
         assert np.array_equal((yA_n[i].astype(np.int64) + yB_n[i]) % p, y)
+    P.close()
+
+
+def test_binarized_layer_full_size_fused_path(F):
+    """The binarized 64x64x128 layer at batch 8 (n = 4096, p = 12289: two
+    slot sets per ciphertext, each spectrum over two ciphertexts) through the
+    fused kernels at full size, HomConv on the tensor cores and on the CUDA
+    cores: both give the same words, and s_A + s_B is the convolution of
+    x_A + x_B with the filters on sampled planes."""
+    ls = FI.CONFIGS["cfg4"].layers[0]
+    cid = FI.CONFIGS["cfg4"].cid
+    P = F.Params(ls.n, ls.p, max_T=ls.Ci)
+    L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, 1, 1)
+    xA, xB = FI.shares(ls, cid)
+    w = FI.weights(ls, cid)
+    ks, es, ss = FI.seeds(cid)
+    t_hat = F.keygen(P, ks)
+    Phat = F.filter_prepare(P, L, dev(w, np.int8))
+    Mhat, sB = F.mask_prepare(P, L, ss)
+    ct, A, R = F.online_produce(P, L, t_hat, es, dev(xA, np.int32), dev(xB, np.int32), P_hat=Phat, M_hat=Mhat)
+    out = F.homconv_tc(P, L, ct, A, R, F.filter_tc(P, L, Phat), Mhat)
+    assert torch.equal(out, F.homconv_sum(P, L, ct, A, R, Phat, Mhat))
+    yA = F.decrypt_share(P, L, t_hat, out)
+    yB = F.intt2d(P, sB.view(ls.B, ls.Co, ls.H, ls.W))
+    torch.cuda.synchronize()
+    assert F.homconv_tc_status() == 0
+    y = (u32(yA).reshape(ls.B, ls.Co, ls.H, ls.W).astype(np.int64) +
+         u32(yB).reshape(ls.B, ls.Co, ls.H, ls.W)) % ls.p
+    x = (xA.astype(np.int64) + xB) % ls.p
+    rng = np.random.default_rng(cid)
+    for _ in range(4):
+        b, co = int(rng.integers(ls.B)), int(rng.integers(ls.Co))
+        assert np.array_equal(y[b, co], O.conv_plain(ls.p, x[b:b + 1], w[co:co + 1])[0, 0]), (b, co)
     P.close()

@@ -469,7 +469,9 @@ def test_homconv_tc_full_size_binarized_layer(F):
     gen = torch.Generator(device="cuda").manual_seed(44)
     q = OP.q
     ct = torch.randint(0, q, (OL.n_in * 2 * ls.n,), dtype=torch.int64, device="cuda", generator=gen)
-    Ph = torch.randint(0, q, (ls.Co * OL.T * OL.beta * ls.n,), dtype=torch.int64, device="cuda", generator=gen)
+    dd = OP.d  # one filter word per group of d evaluation indices
+    assert F.layout(P, L).filter_words == ls.Co * OL.T * OL.beta * ls.n // dd
+    Ph = torch.randint(0, q, (ls.Co * OL.T * OL.beta * ls.n // dd,), dtype=torch.int64, device="cuda", generator=gen)
     Mh = torch.randint(0, q, (OL.n_out * ls.n,), dtype=torch.int64, device="cuda", generator=gen)
     a = F.homconv_tc(P, L, ct, None, None, F.filter_tc(P, L, Ph), Mh)
     b = F.homconv_sum(P, L, ct, None, None, Ph, Mh)
@@ -478,13 +480,13 @@ def test_homconv_tc_full_size_binarized_layer(F):
     assert torch.equal(a, b)
     ctn, Phn, Mhn, outn = (u64(t) for t in (ct, Ph, Mh, a))
     ctn = ctn.reshape(OL.GB, OL.T, OL.beta, 2, ls.n)
-    Phn = Phn.reshape(ls.Co, OL.T, OL.beta, ls.n)
+    Phn = Phn.reshape(ls.Co, OL.T, OL.beta, ls.n // dd)
     outn = outn.reshape(OL.GB, ls.Co, OL.beta, 2, ls.n)
     Mhn = Mhn.reshape(OL.GB, ls.Co, OL.beta, ls.n)
     rng = np.random.default_rng(4)
     for _ in range(64):
         bb, co, h, c, j = (int(rng.integers(m)) for m in (OL.GB, ls.Co, OL.beta, 2, ls.n))
-        s = sum(int(ctn[bb, k, h, c, j]) * int(Phn[co, k, h, j]) for k in range(OL.T)) % q
+        s = sum(int(ctn[bb, k, h, c, j]) * int(Phn[co, k, h, j // dd]) for k in range(OL.T)) % q
         if c == 1:
             s = (s - int(Mhn[bb, co, h, j])) % q
         assert int(outn[bb, co, h, c, j]) == s, (bb, co, h, c, j)

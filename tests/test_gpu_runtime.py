@@ -31,8 +31,9 @@ LAYERS = [  # (n, p, B, Ci, Co, H, W, fh)
     (2048, 65537, 2, 64, 16, 32, 32, 3),
     (2048, 65537, 2, 128, 8, 16, 16, 3),
     (4096, 65537, 2, 256, 4, 8, 8, 3),
-    (4096, 12289, 2, 3, 2, 64, 64, 3),   # spectra span two ciphertexts: step-by-step path
+    (4096, 12289, 2, 3, 2, 64, 64, 3),   # spectra span two ciphertexts (fused)
     (1024, 65537, 3, 4, 4, 16, 16, 5),
+    (512, 65537, 2, 3, 2, 4, 16, 3),     # H = 4 < 8: step-by-step path
 ]
 
 
@@ -71,9 +72,9 @@ def test_plan_of_uneven_layers_matches_oracle(F, tune, tensor):
             assert np.array_equal(u32(d["yA"]).reshape(ref["yA"].shape), ref["yA"]), (i, rep)
             assert np.array_equal(u32(d["yB"]).reshape(ref["yB"].shape), ref["yB"]), (i, rep)
     infos = [plan.info(i) for i in range(len(LAYERS))]
-    assert [x.fused for x in infos] == [1, 1, 1, 0, 1]
+    assert [x.fused for x in infos] == [1, 1, 1, 1, 1, 0]
     if tune:
-        assert all(x.candidates > 0 for x, f in zip(infos, [1, 1, 1, 0, 1]) if f)
+        assert all(x.candidates > 0 for x, f in zip(infos, [1, 1, 1, 1, 1, 0]) if f)
     if tensor:
         assert [x.homconv_variant for x in infos] == [7] * len(LAYERS)
         assert F.homconv_tc_status() == 0

@@ -71,10 +71,12 @@ def test_params_query_rejects(F):
 def test_layout_matches_oracle(F, n, p, shape):
     B, Ci, Co, H, W, g_c, g_b = shape
     lay = F.layout_query(n, p, F.LayerSpec(B, Ci, Co, H, W, g_c, g_b))
-    ref = O.layer(O.params(n, p), B, Ci, Co, H, W, g_c, g_b)
+    OP = O.params(n, p)
+    ref = O.layer(OP, B, Ci, Co, H, W, g_c, g_b)
     for k in ("HW", "T", "GB", "beta", "n_in", "n_out"):
         assert getattr(lay, k) == getattr(ref, k), k
-    assert lay.ct_in_words == ref.n_in * 2 * n and lay.filter_words == Co * ref.T * ref.beta * n
+    # one filter word per group of d evaluation indices (w_0(x^d) plaintexts)
+    assert lay.ct_in_words == ref.n_in * 2 * n and lay.filter_words == Co * ref.T * ref.beta * n // OP.d
 
 
 def test_layout_rejects_bad_packing(F):
@@ -107,14 +109,16 @@ def test_flood_bits_max_matches_oracle_bound(F, n, p, T):
     (256, 65537, (5, 34, 130, 8, 8, 1, 1)),
 ])
 def test_filter_tc_words(F, n, p, shape):
-    """Size of the tensor-core filter layout: per evaluation index and block of
-    16 input ciphertexts, 8 fp16 digit planes of 16 values for every row, the
-    rows of the last 128-channel tile rounded up to a multiple of 8."""
+    """Size of the tensor-core filter layout: per group of d evaluation
+    indices (one filter value each) and block of 16 input ciphertexts, 8 fp16
+    digit planes of 16 values for every row, the rows of the last
+    128-channel tile rounded up to a multiple of 8."""
     B, Ci, Co, H, W, g_c, g_b = shape
     L = F.LayerSpec(B, Ci, Co, H, W, g_c, g_b)
-    ref = O.layer(O.params(n, p), B, Ci, Co, H, W, g_c, g_b)
+    OP = O.params(n, p)
+    ref = O.layer(OP, B, Ci, Co, H, W, g_c, g_b)
     co_pad = 128 * ((Co - 1) // 128) + -(-(Co - 128 * ((Co - 1) // 128)) // 8) * 8
-    assert F.filter_tc_words(n, p, L) * 8 == ref.beta * n * (-(-ref.T // 16)) * co_pad * 8 * 16 * 2
+    assert F.filter_tc_words(n, p, L) * 8 == ref.beta * (n // OP.d) * (-(-ref.T // 16)) * co_pad * 8 * 16 * 2
 
 
 def test_filter_tc_rejects_large_T(F):

@@ -287,3 +287,28 @@ def test_flood_error_is_uniform_on_its_interval():
     assert e.min() >= -(1 << f) and e.max() < (1 << f)
     assert e.min() < -(1 << (f - 1)) and e.max() > (1 << (f - 1))
     assert abs(np.mean(e >= 0) - 0.5) < 0.02
+
+
+@pytest.mark.parametrize("n,p,B,Ci,Co,H,W,g_c,g_b", [(4096, 12289, 2, 3, 2, 64, 64, 1, 1),
+                                                    (4096, 12289, 4, 5, 3, 16, 16, 2, 2),
+                                                    (1024, 7681, 2, 3, 2, 16, 16, 1, 1)])
+def test_filter_plaintexts_take_one_value_per_group_of_d_indices(n, p, B, Ci, Co, H, W, g_c, g_b):
+    """With d = n/S slot sets the filter plaintexts are w_0(x^d) (Sec. 3.1's
+    SIMDScMult over several slot sets): in the bit-reversed NTT_q order the d
+    consecutive evaluation indices of a group are the points x times the d-th
+    roots of unity, where x^d -- and so the filter -- takes one value.  This
+    is what lets the filter be stored once per group.  Checked on the
+    oracle's plaintexts, and the group's points checked directly."""
+    P = O.params(n, p)
+    assert P.d > 1
+    L = O.layer(P, B, Ci, Co, H, W, g_c, g_b)
+    w = np.random.default_rng(n + p).integers(-8, 8, (Co, Ci, 3, 3)).astype(np.int8)
+    Ph = O.filter_prepare(P, L, w).reshape(-1, n)
+    for r in range(1, P.d):
+        assert np.array_equal(Ph[:, r::P.d], Ph[:, 0::P.d])
+    # the points: psi^(2 brv(j) + 1) for the j of a group, raised to d, agree
+    q, psi, logn = P.q, P.psi_q, n.bit_length() - 1
+    brv = lambda j: int(format(j, "0%db" % logn)[::-1], 2)
+    for g0 in range(0, n, P.d * 37):
+        pts = {pow(pow(psi, 2 * brv(j) + 1, q), P.d, q) for j in range(g0, g0 + P.d)}
+        assert len(pts) == 1
