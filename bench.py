@@ -705,18 +705,18 @@ def run_chain(F, flush, sleep_cycles, args):
             "path": "one chained plan (FDSC_PLAN_CHAIN), one graph launch per inference"}
 
 
-def run_serving(F, args):
-    """The served mix: Poisson arrivals (mean 2000 requests/s) of single-image
-    requests drawn uniformly from three layer types, each from one of a pool
-    of client keys; continuous batching inside the library's server under a
-    120 GB HBM budget; latency from submit to completion."""
+def run_serving(F, args, rate=None, n_req=None):
+    """The served mix: Poisson arrivals (mean 2000 requests/s, or `rate`) of
+    single-image requests drawn uniformly from three layer types, each from
+    one of a pool of client keys; continuous batching inside the library's
+    server under a 120 GB HBM budget; latency from submit to completion."""
     import threading
 
     import torch
 
     c = FI.CONFIGS["cfg3"]
-    rate = c.extra["rate_per_s"]
-    n_req = args.serve_requests
+    rate = rate or c.extra["rate_per_s"]
+    n_req = n_req or args.serve_requests
     P = F.Params(2048, 65537, max_T=64)
     t0 = time.perf_counter()
     keys = torch.stack([F.keygen(P, 5000 + k) for k in range(args.serve_keys)]).reshape(-1)
@@ -772,7 +772,9 @@ def run_serving(F, args):
     st = S.stats()
     S.close()
     P.close()
-    return {"workload": "cfg3", "requests": n_req, "rate_per_s": rate, "completed": int(st.completed),
+    return {"workload": "cfg3" if rate == c.extra["rate_per_s"] else "cfg3 mix at %g requests/s" % rate,
+            "requests": n_req, "rate_per_s": rate, "completed": int(st.completed),
+            "lanes": int(st.lanes), "lane_capacity": int(st.lane_capacity), "reserved_bytes": int(st.reserved_bytes),
             "throughput_req_per_s": st.completed / wall, "p50_us": st.p50_us, "p99_us": st.p99_us,
             "mean_us": st.mean_us, "max_us": st.max_us, "mean_batch": st.mean_batch, "batches": int(st.batches),
             "peak_inflight_bytes": int(st.peak_inflight_bytes), "client_keys": args.serve_keys,
@@ -1210,6 +1212,8 @@ def run_gpu(args, rank, local_rank, world):
     chain = None if args.skip_batched else run_chain(F, flush, sleep_cycles, args)
     binarized = None if args.skip_batched else run_binarized(F, sleep_cycles, args)
     serving = None if args.skip_serving else run_serving(F, args)
+    # the same mix at a load where batches form (arrivals faster than one-request batches retire)
+    serving_high = None if args.skip_serving else run_serving(F, args, rate=args.serve_high_rate)
 
     local_sec = total_ms / 1e3
     tot_sec, tot_units = aggregate(local_sec, float(args.steps * ls.B), world)
@@ -1304,6 +1308,7 @@ def run_gpu(args, rank, local_rank, world):
         "chain": chain,
         "binarized": binarized,
         "serving": serving,
+        "serving_high_load": serving_high,
         "ntt2d_sweep": sweep,
         "primitive_rates": {k: {"ops_per_s": v[0], "ops_per_clk_per_sm": v[1]} for k, v in calib.items()},
         "gpu_launches": LAUNCHES_PER_STEP * (args.steps + len(step_ms)) + 6 * n_4s * R + 8 * n_unfused
@@ -1328,7 +1333,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--homconv-variant", type=int, default=0)
     ap.add_argument("--e2e-requests", type=int, default=2000)
-    ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-high-rate", type=float, default=50000.0)
     ap.add_argument("--serve-keys", type=int, default=64)
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")

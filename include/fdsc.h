@@ -402,9 +402,14 @@ int fdsc_plan_destroy(fdsc_plan* plan);
 /* Not in the paper.  A host thread inside the library admits requests (one
  * image of one registered layer type, from one client) into batches while
  * earlier batches are still on the GPU: each lane is a stream with its own
- * buffers, a batch holds up to max_batch requests of one type, and a batch is
- * launched only when the bytes of all requests in flight stay within
- * hbm_budget_bytes.  Every request carries its own key and seeds and is
+ * buffers, a batch holds up to lane_capacity requests of one type, and a
+ * batch is launched only when the bytes of all requests in flight stay within
+ * hbm_budget_bytes.  The budget also sizes the lanes' device buffers (the
+ * memory requests in flight occupy): fdsc_server_start gives every lane room
+ * for min(max_batch, budget / (lanes x the largest request)) requests, with
+ * fewer lanes when not one request per lane fits, so the lanes never hold
+ * more device memory than the budget.  Filter plaintexts (per type) and the
+ * callers' key pools are resident state outside it.  Every request carries its own key and seeds and is
  * computed with the multi-client kernels, so its shares are bit-identical
  * whether it runs alone or batched with others. */
 typedef struct {
@@ -431,6 +436,13 @@ typedef struct {
     uint64_t tensor_batches;    /* batches whose HomConv ran on the tensor cores
                                    (batches of 4 or more requests, when the
                                    layer admits fdsc_homconv_tc)               */
+    uint64_t reserved_bytes;    /* device bytes of the lanes' request buffers
+                                   (at most hbm_budget_bytes)                  */
+    uint32_t lanes;             /* lanes made (fewer than asked when the budget
+                                   holds less than one request per lane)       */
+    uint32_t lane_capacity;     /* requests one lane's buffers hold: at most
+                                   max_batch, and budget / (lanes x the largest
+                                   request's bytes)                            */
 } fdsc_server_stats;
 
 typedef struct fdsc_server fdsc_server;
@@ -444,12 +456,15 @@ int fdsc_server_create(const fdsc_server_config* cfg, fdsc_server** out);
  * a pointer to its key pool (device [nkeys][n]). */
 int fdsc_server_add_type(fdsc_server* s, const fdsc_params* P, const fdsc_layer* L, const int8_t* w, uint32_t fh,
                          uint32_t fw, const uint64_t* keys, uint32_t nkeys, uint32_t* type_id);
-/* Allocates the lanes' buffers, records every lane's batch of every type and
- * size (1 .. max_batch) as a CUDA graph (after one run per type on zero
- * inputs), and starts the scheduling thread.  Types must all be added
- * before; FDSC_ERR_CUDA if a recording fails. */
+/* Allocates the lanes' buffers within the budget (see above), records every
+ * lane's batch of every type and size (1 .. lane_capacity) as a CUDA graph
+ * (after one run per type on zero inputs), and starts the scheduling thread.
+ * Types must all be added before; FDSC_ERR_BUDGET if the budget holds no
+ * request, FDSC_ERR_CUDA if a recording fails. */
 int fdsc_server_start(fdsc_server* s);
-/* Queues a request (thread-safe); FDSC_ERR_BUDGET if it can never fit. */
+/* Queues a request (thread-safe); FDSC_ERR_BUDGET if it can never fit.  The
+ * latency statistics are kept in a fixed histogram (0.45 % bins between 1 us
+ * and 100 s): the server's memory does not grow with the requests served. */
 int fdsc_server_submit(fdsc_server* s, const fdsc_request* r, uint64_t* ticket);
 /* Waits at most timeout_ms for a ticket; FDSC_ERR_TIMEOUT if not done. */
 int fdsc_server_wait(fdsc_server* s, uint64_t ticket, uint32_t timeout_ms, double* latency_us);

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -13,6 +14,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "fdsc_internal.h"
@@ -508,6 +510,36 @@ struct Req {
     Clock::time_point t_submit;
 };
 
+// Request latencies in a fixed histogram: 4096 bins spaced evenly in log
+// between 1 us and 100 s (each bin 0.45 % wide), so the server's memory does
+// not grow with the number of requests and a percentile costs one pass over
+// the bins.  A percentile reports its bin's geometric centre.
+struct LatencyHist {
+    static constexpr int kBins = 4096;
+    static constexpr double kLo = 1.0, kHi = 1e8;
+    uint64_t count[kBins] = {};
+    uint64_t n = 0;
+    double sum = 0, max = 0;
+    void add(double us) {
+        const double t = std::log(std::max(us, kLo) / kLo) / std::log(kHi / kLo);
+        const int b = std::min(kBins - 1, std::max(0, (int)(t * kBins)));
+        count[b]++;
+        n++;
+        sum += us;
+        max = std::max(max, us);
+    }
+    double pct(double q) const {
+        if (!n) return 0.0;
+        const uint64_t rank = std::min<uint64_t>(n - 1, (uint64_t)(q * (double)(n - 1) + 0.5));
+        uint64_t seen = 0;
+        for (int b = 0; b < kBins; b++) {
+            seen += count[b];
+            if (seen > rank) return kLo * std::pow(kHi / kLo, (b + 0.5) / kBins);
+        }
+        return max;
+    }
+};
+
 struct Lane {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -543,7 +575,9 @@ struct fdsc_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Req> pending;
     std::map<uint64_t, double> done;  // ticket -> latency (us); -1 = failed
-    std::vector<double> latencies;
+    LatencyHist latencies;
+    uint32_t lane_cap = 0;            // requests a lane's buffers hold (<= max_batch, from the budget)
+    uint64_t reserved = 0;            // device bytes of the lanes' request buffers
     uint64_t next_ticket = 1, submitted = 0, completed = 0, batches = 0, batched_requests = 0;
     std::atomic<uint64_t> tensor_batches{0};  // batches whose HomConv ran on the tensor cores
     uint64_t inflight = 0, peak_inflight = 0;
@@ -632,7 +666,7 @@ int record_batch(const fdsc_server* S, Lane& ln, uint32_t type, uint32_t G, bool
 // direct run per type at the smallest and largest batch (zero inputs) so
 // that every kernel's attributes are set outside the capture.
 int record_lane_graphs(fdsc_server* S, Lane& ln) {
-    const uint32_t B = S->cfg.max_batch;
+    const uint32_t B = S->lane_cap;
     memset(ln.h_xA, 0, B * S->max_in * 4);
     memset(ln.h_xB, 0, B * S->max_in * 4);
     memset(ln.h_seeds, 0, 3 * (size_t)B * 8);
@@ -681,7 +715,7 @@ int launch_batch(fdsc_server* S, Lane& ln) {
         ln.h_seeds[2 * G + b] = r.key;
     }
     S->copies->run(jobs);
-    const size_t k = (size_t)ln.type * S->cfg.max_batch + (G - 1);
+    const size_t k = (size_t)ln.type * S->lane_cap + (G - 1);
     RT_TRY(cudaGraphLaunch(ln.graphs[k], ln.stream));
     RT_TRY(cudaEventRecord(ln.done, ln.stream));
     if (ln.graph_tensor[k]) S->tensor_batches++;
@@ -705,7 +739,7 @@ void finish_batch(fdsc_server* S, Lane& ln, bool ok) {
     for (auto& q : ln.batch) {
         const double us = std::chrono::duration<double, std::micro>(now - q.t_submit).count();
         S->done[q.ticket] = ok ? us : -1.0;
-        if (ok) S->latencies.push_back(us);
+        if (ok) S->latencies.add(us);
         S->completed++;
     }
     S->inflight -= ln.bytes;
@@ -756,7 +790,7 @@ void worker_loop(fdsc_server* S) {
             const uint64_t per = S->types[type].bytes_per_request;
             std::vector<Req> batch;
             uint64_t bytes = 0;
-            for (auto it = S->pending.begin(); it != S->pending.end() && batch.size() < S->cfg.max_batch;) {
+            for (auto it = S->pending.begin(); it != S->pending.end() && batch.size() < S->lane_cap;) {
                 if (it->r.type != type) {
                     ++it;
                     continue;
@@ -807,6 +841,15 @@ void worker_loop(fdsc_server* S) {
 }
 
 }  // namespace
+
+// Device bytes of a lane's request buffers for B requests of the largest type
+// (each buffer 256-byte aligned inside the lane's block).
+static uint64_t lane_bytes(const fdsc_server* S, uint64_t B) {
+    auto al = [](uint64_t b) { return (b + 255) & ~(uint64_t)255; };
+    return 2 * al(B * S->max_in * 4) + 3 * al(B * S->max_out * 4) + al(B * S->max_ct_in * 8) +
+           2 * al(B * S->max_add * 8) + al(B * S->max_ct_out * 8) + al(B * S->max_mask * 8) + al(B * S->max_n * 8) +
+           al(3 * B * 8);
+}
 
 extern "C" int fdsc_server_create(const fdsc_server_config* cfg, fdsc_server** out) {
     if (!cfg || !out || cfg->max_batch == 0 || cfg->lanes == 0)
@@ -874,18 +917,46 @@ extern "C" int fdsc_server_add_type(fdsc_server* S, const fdsc_params* P, const 
 extern "C" int fdsc_server_start(fdsc_server* S) {
     if (!S || S->types.empty()) return fdsc_set_error(FDSC_ERR_ARG, "server needs at least one type");
     if (S->started) return FDSC_OK;
-    const uint64_t B = S->cfg.max_batch;
-    S->lanes.resize(S->cfg.lanes);
+    // The lanes' request buffers are what requests in flight occupy, so the
+    // budget sizes them: every lane holds the same number of requests of the
+    // largest type, as many as max_batch and the budget's share allow; when
+    // not even one fits per lane, fewer lanes are made (FDSC_ERR_BUDGET if
+    // not one request fits at all).  One device block per lane.
+    const uint64_t per = lane_bytes(S, 1);
+    uint64_t nl = S->cfg.lanes, cap = std::min<uint64_t>(S->cfg.max_batch, S->cfg.hbm_budget_bytes / (nl * per));
+    if (cap == 0) {
+        nl = std::min<uint64_t>(nl, S->cfg.hbm_budget_bytes / per);
+        cap = 1;
+    }
+    if (nl == 0)
+        return fdsc_set_error(FDSC_ERR_BUDGET, "the budget of %llu bytes holds no request (%llu bytes each)",
+                              (unsigned long long)S->cfg.hbm_budget_bytes, (unsigned long long)per);
+    S->lane_cap = (uint32_t)cap;
+    const uint64_t B = cap;
+    S->lanes.resize(nl);
     for (auto& ln : S->lanes) {
         int rc;
-        if ((rc = S->arena.alloc((void**)&ln.xA, B * S->max_in * 4)) || (rc = S->arena.alloc((void**)&ln.xB, B * S->max_in * 4)) ||
-            (rc = S->arena.alloc((void**)&ln.yA, B * S->max_out * 4)) || (rc = S->arena.alloc((void**)&ln.yB, B * S->max_out * 4)) ||
-            (rc = S->arena.alloc((void**)&ln.sB, B * S->max_out * 4)) || (rc = S->arena.alloc((void**)&ln.ct, B * S->max_ct_in * 8)) ||
-            (rc = S->arena.alloc((void**)&ln.A, B * S->max_add * 8)) || (rc = S->arena.alloc((void**)&ln.R, B * S->max_add * 8)) ||
-            (rc = S->arena.alloc((void**)&ln.ct_out, B * S->max_ct_out * 8)) ||
-            (rc = S->arena.alloc((void**)&ln.M, B * S->max_mask * 8)) || (rc = S->arena.alloc((void**)&ln.keys, B * S->max_n * 8)) ||
-            (rc = S->arena.alloc((void**)&ln.seeds, 3 * B * 8)))
-            return rc;
+        unsigned char* blk = nullptr;
+        const uint64_t bytes = lane_bytes(S, B);
+        if ((rc = S->arena.alloc((void**)&blk, bytes))) return rc;
+        S->reserved += bytes;
+        uint64_t off = 0;
+        auto carve = [&](auto** p, uint64_t b) {
+            *p = reinterpret_cast<std::remove_reference_t<decltype(**p)>*>(blk + off);
+            off += (b + 255) & ~(uint64_t)255;
+        };
+        carve(&ln.xA, B * S->max_in * 4);
+        carve(&ln.xB, B * S->max_in * 4);
+        carve(&ln.yA, B * S->max_out * 4);
+        carve(&ln.yB, B * S->max_out * 4);
+        carve(&ln.sB, B * S->max_out * 4);
+        carve(&ln.ct, B * S->max_ct_in * 8);
+        carve(&ln.A, B * S->max_add * 8);
+        carve(&ln.R, B * S->max_add * 8);
+        carve(&ln.ct_out, B * S->max_ct_out * 8);
+        carve(&ln.M, B * S->max_mask * 8);
+        carve(&ln.keys, B * S->max_n * 8);
+        carve(&ln.seeds, 3 * B * 8);
         if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&ln.side[0], cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&ln.side[1], cudaStreamNonBlocking) != cudaSuccess ||
@@ -954,21 +1025,20 @@ extern "C" int fdsc_server_wait(fdsc_server* S, uint64_t ticket, uint32_t timeou
 extern "C" int fdsc_server_stats_get(fdsc_server* S, fdsc_server_stats* out) {
     if (!S || !out) return fdsc_set_error(FDSC_ERR_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(S->mu);
-    std::vector<double> v = S->latencies;
-    std::sort(v.begin(), v.end());
-    auto pct = [&](double q) { return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5))]; };
+    const LatencyHist& h = S->latencies;
     out->submitted = S->submitted;
     out->completed = S->completed;
     out->batches = S->batches;
     out->tensor_batches = S->tensor_batches.load();
     out->peak_inflight_bytes = S->peak_inflight;
     out->mean_batch = S->batches ? (double)S->batched_requests / S->batches : 0.0;
-    out->p50_us = pct(0.50);
-    out->p99_us = pct(0.99);
-    double sum = 0;
-    for (double x : v) sum += x;
-    out->mean_us = v.empty() ? 0.0 : sum / v.size();
-    out->max_us = v.empty() ? 0.0 : v.back();
+    out->p50_us = h.pct(0.50);
+    out->p99_us = h.pct(0.99);
+    out->mean_us = h.n ? h.sum / (double)h.n : 0.0;
+    out->max_us = h.max;
+    out->lanes = (uint32_t)S->lanes.size();
+    out->lane_capacity = S->lane_cap;
+    out->reserved_bytes = S->reserved;
     return S->error;
 }
 

@@ -609,7 +609,8 @@ class Request(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [(k, C.c_uint64) for k in ("submitted", "completed", "batches", "peak_inflight_bytes")] + \
                [(k, C.c_double) for k in ("mean_batch", "p50_us", "p99_us", "mean_us", "max_us")] + \
-               [("tensor_batches", C.c_uint64)]
+               [("tensor_batches", C.c_uint64), ("reserved_bytes", C.c_uint64), ("lanes", C.c_uint32),
+                ("lane_capacity", C.c_uint32)]
 
 
 class Server:

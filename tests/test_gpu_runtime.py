@@ -233,19 +233,98 @@ def test_server_budget_and_timeouts(F):
     keys = F.keygen(P, 1)
     w = dev(np.ones((8, 64, 3, 3), np.int8), np.int8)
     S = F.Server(hbm_budget_bytes=1 << 20, max_batch=4, lanes=2)  # 1 MiB: less than one request needs
+    S.add_type(P, F.LayerSpec(1, 64, 8, 32, 32, 0, 1), w, keys)
+    with pytest.raises(F.FdscError) as e:
+        S.start()
+    assert e.value.code == -7
+    S.close()
+    S = F.Server(hbm_budget_bytes=1 << 30, max_batch=4, lanes=2)
     tid = S.add_type(P, F.LayerSpec(1, 64, 8, 32, 32, 0, 1), w, keys)
     S.start()
     x = np.zeros((64, 32, 32), np.uint32)
     y = np.zeros((8, 32, 32), np.uint32)
-    with pytest.raises(F.FdscError) as e:
-        S.submit(tid, 0, 1, 2, x, x, y, y)
-    assert e.value.code == -7
     with pytest.raises(F.FdscError) as e:
         S.wait(12345, timeout_ms=20)  # a ticket nobody submitted
     assert e.value.code == -6
     with pytest.raises(F.FdscError) as e:
         S.submit(tid, 5, 1, 2, x, x, y, y)  # key outside the pool
     assert e.value.code == -1
+    S.close()
+    P.close()
+
+
+def test_server_budget_bounds_device_memory(F):
+    """The budget sizes the lanes' device buffers: with room for 2.5
+    requests and 4 lanes asked, two lanes of one request each are made and
+    the device memory fdsc_server_start takes stays within the budget (plus
+    the recorded graphs); a large budget gives lanes x max_batch requests'
+    worth.  Requests under the small budget give the same shares."""
+    P = F.Params(2048, 65537, max_T=64)
+    keys = torch.stack([F.keygen(P, k) for k in (3, 4)]).reshape(-1)
+    g = np.random.default_rng(9)
+    w = g.integers(-8, 8, (16, 64, 3, 3)).astype(np.int8)
+    L = F.LayerSpec(1, 64, 16, 32, 32, 0, 1)
+
+    def started(budget, lanes, max_batch):
+        S = F.Server(hbm_budget_bytes=budget, max_batch=max_batch, lanes=lanes)
+        tid = S.add_type(P, L, dev(w, np.int8), keys)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        S.start()
+        torch.cuda.synchronize()
+        return S, tid, free0 - torch.cuda.mem_get_info()[0]
+
+    big, tid_b, drop_big = started(8 << 30, 4, 16)
+    stb = big.stats()
+    assert (stb.lanes, stb.lane_capacity) == (4, 16)
+    assert drop_big >= stb.reserved_bytes > 0
+    per = stb.reserved_bytes / 64  # one request slot of one lane
+    budget = int(2.5 * per)
+    small, tid_s, drop_small = started(budget, 4, 16)
+    st = small.stats()
+    assert (st.lanes, st.lane_capacity) == (2, 1) and st.reserved_bytes <= budget
+    assert drop_small <= budget + (32 << 20) < drop_big
+    outs = {}
+    for name, S, tid in (("big", big, tid_b), ("small", small, tid_s)):
+        rng = np.random.default_rng(21)
+        res = []
+        tickets = []
+        for i in range(6):
+            xa = rng.integers(0, 65537, (64, 32, 32)).astype(np.uint32)
+            xb = rng.integers(0, 65537, (64, 32, 32)).astype(np.uint32)
+            ya, yb = np.zeros((16, 32, 32), np.uint32), np.zeros((16, 32, 32), np.uint32)
+            res.append((xa, xb, ya, yb))
+            tickets.append(S.submit(tid, i % 2, 40 + i, 50 + i, xa, xb, ya, yb))
+        for tk in tickets:
+            S.wait(tk)
+        outs[name] = [(ya.copy(), yb.copy()) for _, _, ya, yb in res]
+        assert S.stats().completed == 6
+        S.close()
+    for (a1, b1), (a2, b2) in zip(outs["big"], outs["small"]):
+        assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+    P.close()
+
+
+def test_server_latency_histogram_percentiles(F):
+    """The latency record is a fixed histogram: its percentiles lie within a
+    bin (0.45 %) of the sorted latencies the waiters saw."""
+    P = F.Params(2048, 65537, max_T=64)
+    keys = F.keygen(P, 2)
+    w = dev(np.ones((4, 4, 3, 3), np.int8), np.int8)
+    S = F.Server(hbm_budget_bytes=1 << 30, max_batch=4, lanes=2)
+    tid = S.add_type(P, F.LayerSpec(1, 4, 4, 16, 16, 0, 1), w, keys)
+    S.start()
+    x = np.ones((4, 16, 16), np.uint32)
+    lat = []
+    for i in range(200):
+        y1, y2 = np.zeros((4, 16, 16), np.uint32), np.zeros((4, 16, 16), np.uint32)
+        lat.append(S.wait(S.submit(tid, 0, i, i, x, x, y1, y2)))
+    st = S.stats()
+    v = np.sort(lat)
+    for q, got in ((0.50, st.p50_us), (0.99, st.p99_us)):
+        ref = v[min(len(v) - 1, int(q * (len(v) - 1) + 0.5))]
+        assert abs(got - ref) <= 0.005 * ref, (q, got, ref)
+    assert abs(st.max_us - v[-1]) < 1e-6 * v[-1] and abs(st.mean_us - v.mean()) < 1e-6 * v.mean()
     S.close()
     P.close()
 
