@@ -87,12 +87,13 @@ def layer_counts(ls, T, beta, GB, n, addends=2):
 
 # the HomConv kernel behind each variant number (fdsc_set_homconv_variant)
 HOMCONV_KERNELS = {3: "homconv_kernel<1,false,2>", 4: "homconv3_kernel<0>", 10: "homconv5_kernel<8>",
-                   11: "homconv6_kernel<16>", 12: "homconv6_kernel<8>"}
+                   11: "homconv6_kernel<16,1>", 12: "homconv6_kernel<8,1>", 13: "homconv6_kernel<8,2>",
+                   14: "homconv6_kernel<8,4>"}
 
 
 def variant_used(T, requested):
     """The variant the library runs for T input ciphertexts (0 = its default)."""
-    if requested in (11, 12) and T <= 64:
+    if requested in (11, 12, 13, 14) and T <= 64:
         return requested
     if requested == 10 and T <= 128 and T % 4 == 0:
         return 10
@@ -838,8 +839,10 @@ def run_kernel_only(args):
     images, the first layer of the 16-image stack), `homconv_tc` (the tensor-core HomConv of
     the 16x16x128->128 layer at 16 images), `ntt2d` (forward NTT2D of
     --planes 32x32 planes), `step` (the fused online step of that layer,
-    eager) or `plan` (the 16-image stack as one autotuned plan; under a
-    profiler the tuner's timings, and so its choices, can differ)."""
+    eager), `binarized` (the binarized 64x64x128 layer at batch 8 through
+    the fused path, HomConv on the tensor cores) or `plan` (the 16-image
+    stack as one autotuned plan; under a profiler the tuner's timings, and
+    so its choices, can differ)."""
     import torch
 
     torch.cuda.set_device(0)
@@ -886,6 +889,30 @@ def run_kernel_only(args):
             P2.close()
         print("ran %d x plan" % args.steps)
         return
+    if args.kernel_only == "binarized":
+        # the binarized 64x64x128 layer at batch 8 through the fused path
+        P.close()
+        c4 = FI.CONFIGS["cfg4"]
+        ls4 = c4.layers[0]
+        P = F.Params(ls4.n, ls4.p, max_T=ls4.Ci)
+        L4 = F.LayerSpec(ls4.B, ls4.Ci, ls4.Co, ls4.H, ls4.W, 1, 1)
+        dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
+        xA_h, xB_h = FI.shares(ls4, c4.cid)
+        ks, es, ss = FI.seeds(c4.cid)
+        t_hat = F.keygen(P, ks)
+        Phat = F.filter_prepare(P, L4, dev(FI.weights(ls4, c4.cid), np.int8))
+        Ptc = F.filter_tc(P, L4, Phat)
+        Mhat, sB = F.mask_prepare(P, L4, ss)
+        xA, xB = dev(xA_h, np.int32), dev(xB_h, np.int32)
+        for _ in range(args.steps):
+            ct, A, R = F.online_produce(P, L4, t_hat, es, xA, xB)
+            F.intt2d(P, sB.view(ls4.B, ls4.Co, ls4.H, ls4.W))
+            F.decrypt_share(P, L4, t_hat, F.homconv_tc(P, L4, ct, A, R, Ptc, Mhat))
+        torch.cuda.synchronize()
+        assert F.homconv_tc_status() == 0
+        print("ran %d x binarized" % args.steps)
+        P.close()
+        return
     if args.kernel_only == "homconv_tc":
         # the tensor-core HomConv on the 16x16x128->128 layer of the 16-image stack
         ls = FI.CONFIGS["cfg2"].layers[1]
@@ -928,8 +955,7 @@ def run_kernel_only(args):
         Mhat, sB = F.mask_prepare(P, L, ss)
         xA, xB = dev(xA_h, np.int32), dev(xB_h, np.int32)
         for _ in range(args.steps):
-            ct = F.encrypt_constants(P, L, t_hat, es)
-            A, R = F.encode_share(P, L, xA), F.encode_share(P, L, xB)
+            ct, A, R = F.online_produce(P, L, t_hat, es, xA, xB)
             F.intt2d(P, sB.view(ls.B, ls.Co, ls.H, ls.W))
             F.decrypt_share(P, L, t_hat, F.homconv_sum(P, L, ct, A, R, Phat, Mhat))
     torch.cuda.synchronize()
@@ -1339,7 +1365,8 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--clocks-dir", default="", help="where the raw nvidia-smi clock samples go (default: a temp dir)")
-    ap.add_argument("--kernel-only", choices=["homconv", "homconv_b16", "homconv_tc", "ntt2d", "step", "plan"],
+    ap.add_argument("--kernel-only", choices=["homconv", "homconv_b16", "homconv_tc", "ntt2d", "step", "plan",
+                                              "binarized"],
                     help="only run --steps launches of one part of the path (for profiler captures)")
     ap.add_argument("--planes", type=int, default=65536, help="planes for --kernel-only ntt2d")
     args = ap.parse_args()

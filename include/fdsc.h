@@ -537,6 +537,16 @@ int fdsc_set_homconv_variant(int variant);
  * launches issued after the call, process-wide. */
 int fdsc_set_launch_overlap(int on);
 
+/* The fused decryption of a layer whose output ciphertexts fill less than half
+ * the SMs (one image) splits every ciphertext over a cluster of two CTAs, one
+ * coefficient parity each (on = 1, the default): a lower latency for that
+ * image, for about 45 % more instructions in all.  Off (0): one CTA per
+ * ciphertext, the better choice when consecutive layers overlap on the GPU
+ * and the SMs, not one layer's latency, are the bound.  The words are the same
+ * either way.  Returns the previous setting; process-wide, for launches issued
+ * after the call. */
+int fdsc_set_decrypt_pair(int on);
+
 /* Measured throughput of the exact arithmetic primitives on the current
  * device (the ALU side of the roofline): which = 0, the 60 x 60 -> 128-bit
  * multiply-accumulate of HomConv; 1, the 64-bit Shoup multiplication mod q

@@ -71,6 +71,9 @@ int fdsc_check_fused(const fdsc_params* P, const DevLayer& D, size_t smem, const
 // Whether online kernels are launched with programmatic stream serialisation
 // (fdsc_set_launch_overlap; off by default).
 bool fdsc_launch_overlap();
+// Whether one image's decryption may split each ciphertext over a CTA pair
+// (fdsc_set_decrypt_pair; on by default).
+bool fdsc_decrypt_pair_allowed();
 
 #ifdef __CUDACC__
 // Launches an online kernel (one that calls griddep_wait() before touching

@@ -56,6 +56,15 @@ __device__ __forceinline__ void acc_mac(Acc128& acc, u64 a, u64 b) {
 __device__ __forceinline__ u64 acc_reduce(const Acc128& a, const DevParams& P) {
     return reduce128(((u64)a.w[3] << 32) | a.w[2], ((u64)a.w[1] << 32) | a.w[0], P);
 }
+// a += b (128-bit, carry-chained)
+__device__ __forceinline__ void acc_add(Acc128& a, const Acc128& b) {
+    asm("add.cc.u32  %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, %5;\n\t"
+        "addc.cc.u32 %2, %2, %6;\n\t"
+        "addc.u32    %3, %3, %7;"
+        : "+r"(a.w[0]), "+r"(a.w[1]), "+r"(a.w[2]), "+r"(a.w[3])
+        : "r"(b.w[0]), "r"(b.w[1]), "r"(b.w[2]), "r"(b.w[3]));
+}
 __device__ __forceinline__ void acc_set(Acc128& a, u64 r) {
     a.w[0] = (u32)r;
     a.w[1] = (u32)(r >> 32);
@@ -711,7 +720,11 @@ __device__ __forceinline__ void cp_async_w(void* smem, const void* g, bool share
         cp_async16(smem, g);
 }
 
-template <int kD>
+// kS: independent partial sums per output word (term k goes to sum k mod kS),
+// so that each thread has 4 kS carry chains in flight instead of 4: the
+// chains' dependent latency, not the multiply pipe, bounds the kernel at one
+// image, where a scheduler has only about four warps.
+template <int kD, int kS, bool kEarly>
 __global__ void __launch_bounds__(kThreads5, 2)
     homconv6_kernel(DevParams P, DevLayer L, const u64* __restrict__ ct_in, const u64* __restrict__ A1,
                     const u64* __restrict__ A2, const u64* __restrict__ Phat, const u64* __restrict__ Mhat,
@@ -735,47 +748,59 @@ __global__ void __launch_bounds__(kThreads5, 2)
     const u64 w_step = beta * nd;
     const bool shared_w = P.d > 1;  // both indices use one filter word (copied as 8 bytes)
     griddep_release();
-    griddep_wait();
+    // the first kD filter terms: before the grid-dependency wait when the
+    // caller guarantees the kernel before this one does not write P_hat
+    if (!kEarly) griddep_wait();
 #pragma unroll
     for (int u = 0; u < kD; u++) {
         if (active && (u32)u < T) cp_async_w(ring + u * kThreads5, wp + (u64)u * w_step, shared_w);
         cp_commit();
     }
+    if (kEarly) griddep_wait();
     ulonglong2 m = make_ulonglong2(0, 0);
     if (active && Mhat) m = ldg2(Mhat + (((u64)bb * L.Co + co) * beta + h) * n + j);
-    for (u32 e = threadIdx.x; e < T * kPairs; e += kThreads5) {
-        const u32 k = e / kPairs, jp = e % kPairs, Jx = jt * kJ5 + 2 * jp;
-        ulonglong2 x0 = make_ulonglong2(0, 0), x1 = make_ulonglong2(0, 0);
-        if (Jx < nJ) {
-            const u32 hx = Jx >> P.logn, jx = Jx & (P.n - 1);
-            const u64 u = ((u64)bb * T + k) * beta + hx;
-            x0 = ldg2(ct_in + u * 2 * n + jx);
-            x1 = ldg2(ct_in + u * 2 * n + n + jx);
-            if (A1) {
-                const ulonglong2 a = ldg2(A1 + u * n + jx);
-                x1.x = addmod_q(x1.x, a.x, P.q);
-                x1.y = addmod_q(x1.y, a.y, P.q);
-            }
-            if (A2) {
-                const ulonglong2 a = ldg2(A2 + u * n + jx);
-                x1.x = addmod_q(x1.x, a.x, P.q);
-                x1.y = addmod_q(x1.y, a.y, P.q);
+    // the input tile: every thread's loads (kSU pairs at a time) are issued
+    // before any is used, so the tile costs one memory latency, not kSU
+    constexpr u32 kSU = 4;
+    for (u32 e0 = threadIdx.x; e0 < T * kPairs; e0 += kSU * kThreads5) {
+        ulonglong2 x0[kSU], x1[kSU], a1[kSU], a2[kSU];
+#pragma unroll
+        for (u32 i = 0; i < kSU; i++) {
+            const u32 e = e0 + i * kThreads5, k = e / kPairs, jp = e % kPairs, Jx = jt * kJ5 + 2 * jp;
+            x0[i] = x1[i] = a1[i] = a2[i] = make_ulonglong2(0, 0);
+            if (e < T * kPairs && Jx < nJ) {
+                const u32 hx = Jx >> P.logn, jx = Jx & (P.n - 1);
+                const u64 u = ((u64)bb * T + k) * beta + hx;
+                x0[i] = ldg2(ct_in + u * 2 * n + jx);
+                x1[i] = ldg2(ct_in + u * 2 * n + n + jx);
+                if (A1) a1[i] = ldg2(A1 + u * n + jx);
+                if (A2) a2[i] = ldg2(A2 + u * n + jx);
             }
         }
-        xs[(k * 2 + 0) * kPairs + jp] = x0;
-        xs[(k * 2 + 1) * kPairs + jp] = x1;
+#pragma unroll
+        for (u32 i = 0; i < kSU; i++) {
+            const u32 e = e0 + i * kThreads5, k = e / kPairs, jp = e % kPairs;
+            if (e >= T * kPairs) break;
+            ulonglong2 c1 = x1[i];
+            c1.x = addmod_q(addmod_q(c1.x, a1[i].x, P.q), a2[i].x, P.q);
+            c1.y = addmod_q(addmod_q(c1.y, a1[i].y, P.q), a2[i].y, P.q);
+            xs[(k * 2 + 0) * kPairs + jp] = x0[i];
+            xs[(k * 2 + 1) * kPairs + jp] = c1;
+        }
     }
     __syncthreads();
     if (!active) {
         asm volatile("cp.async.wait_all;" ::: "memory");
         return;
     }
-    Acc128 acc[2][2];  // [index J + e][component]
+    Acc128 acc[kS][2][2];  // [partial sum][index J + e][component]
 #pragma unroll
-    for (int e = 0; e < 2; e++) {
-        acc_zero(acc[e][0]);
-        acc_zero(acc[e][1]);
-    }
+    for (int s = 0; s < kS; s++)
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            acc_zero(acc[s][e][0]);
+            acc_zero(acc[s][e][1]);
+        }
     for (u32 k0 = 0; k0 < T; k0 += kD) {
 #pragma unroll
         for (int u = 0; u < kD; u++) {
@@ -785,22 +810,30 @@ __global__ void __launch_bounds__(kThreads5, 2)
                 ulonglong2 w = ring[u * kThreads5];
                 if (shared_w) w.y = w.x;
                 const ulonglong2 xa = xs[(k * 2 + 0) * kPairs + lane], xb = xs[(k * 2 + 1) * kPairs + lane];
-                acc_mac(acc[0][0], xa.x, w.x);
-                acc_mac(acc[1][0], xa.y, w.y);
-                acc_mac(acc[0][1], xb.x, w.x);
-                acc_mac(acc[1][1], xb.y, w.y);
+                Acc128(&a)[2][2] = acc[u % kS];  // kD is a multiple of kS: term k -> sum k mod kS
+                acc_mac(a[0][0], xa.x, w.x);
+                acc_mac(a[1][0], xa.y, w.y);
+                acc_mac(a[0][1], xb.x, w.x);
+                acc_mac(a[1][1], xb.y, w.y);
                 // the slot is refilled only after its words were used
                 if (k + kD < T) cp_async_w(ring + u * kThreads5, wp + (u64)(k + kD) * w_step, shared_w);
                 cp_commit();
             }
         }
     }
+#pragma unroll
+    for (int s = 1; s < kS; s++)  // T <= 64 products in all: the sums stay below 2^128
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            acc_add(acc[0][e][0], acc[s][e][0]);
+            acc_add(acc[0][e][1], acc[s][e][1]);
+        }
     const u64 v = ((u64)bb * L.Co + co) * beta + h;
     ulonglong2 r0, r1;
-    r0.x = acc_reduce(acc[0][0], P);
-    r0.y = acc_reduce(acc[1][0], P);
-    r1.x = acc_reduce(acc[0][1], P);
-    r1.y = acc_reduce(acc[1][1], P);
+    r0.x = acc_reduce(acc[0][0][0], P);
+    r0.y = acc_reduce(acc[0][1][0], P);
+    r1.x = acc_reduce(acc[0][0][1], P);
+    r1.y = acc_reduce(acc[0][1][1], P);
     if (Mhat) {
         r1.x = submod_q(r1.x, m.x, P.q);
         r1.y = submod_q(r1.y, m.y, P.q);
@@ -811,7 +844,7 @@ __global__ void __launch_bounds__(kThreads5, 2)
 
 bool v6_supported(const DevLayer& L) { return L.T <= kMaxT6; }
 
-template <int kD>
+template <int kD, int kS, bool kEarly = false>
 cudaError_t launch_v6(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
                       const u64* Phat, const u64* Mhat, u64* ct_out, cudaStream_t s) {
     const u32 nJ = L.beta * P.n;
@@ -821,10 +854,10 @@ cudaError_t launch_v6(const DevParams& P, const DevLayer& L, const u64* ct_in, c
     if (grid > 0x7FFFFFFFull || !v6_supported(L)) return cudaErrorInvalidConfiguration;
     if (smem + 1024 > 48 * 1024) {
         cudaError_t e =
-            cudaFuncSetAttribute(homconv6_kernel<kD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(homconv6_kernel<kD, kS, kEarly>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    return launch_online(homconv6_kernel<kD>, (u32)grid, kThreads5, smem, s, P, L, ct_in, A1, A2, Phat, Mhat, ct_out,
+    return launch_online(homconv6_kernel<kD, kS, kEarly>, (u32)grid, kThreads5, smem, s, P, L, ct_in, A1, A2, Phat, Mhat, ct_out,
                          jtiles, ctiles);
 }
 
@@ -874,10 +907,11 @@ cudaError_t launch_v4(const DevParams& P, const DevLayer& L, const u64* ct_in, c
 // 8 / 9 = staged tile with Karatsuba limb columns and 1 / 2 image groups per
 // CTA, 10 = lean staged tile with two indices per lane (T a multiple of 4,
 // at most 128; 4 otherwise), 11 / 12 = the same with the filter streamed
-// through a shared-memory ring of 16 / 8 terms (T <= 64; 10 otherwise).  7 is
-// the tensor-core kernel, a plan-only choice.
+// through a shared-memory ring of 16 / 8 terms (T <= 64; 10 otherwise), 13 /
+// 14 = 12 with 2 / 4 independent partial sums per output word.  7 is the
+// tensor-core kernel, a plan-only choice.
 static int g_homconv_variant = 0;
-bool homconv_variant_valid(int v) { return v >= 0 && v <= 12 && v != 7; }
+bool homconv_variant_valid(int v) { return v >= 0 && v <= 15 && v != 7; }
 extern "C" int fdsc_set_homconv_variant(int v) {
     if (!homconv_variant_valid(v)) return FDSC_ERR_ARG;
     g_homconv_variant = v;
@@ -904,8 +938,8 @@ int homconv_default_variant(const DevLayer& L) { return L.T <= kMaxT6 ? 12 : (L.
 
 // The variant launch_homconv_v runs when asked for v (the fallbacks below).
 int homconv_effective_variant(const DevLayer& L, int v) {
-    if (v <= 0 || v > 12 || v == 7) v = homconv_default_variant(L);
-    if ((v == 11 || v == 12) && !v6_supported(L)) v = 10;
+    if (v <= 0 || v > 15 || v == 7) v = homconv_default_variant(L);
+    if (v >= 11 && v <= 15 && !v6_supported(L)) v = 10;
     if (v == 10 && !v5_supported(L)) v = L.T <= 256 ? 4 : 3;
     if (v >= 8 && v <= 9 && (u64)L.T * 2 * kJ4 * 8 > kMaxStage4) v = 3;
     if (v >= 4 && v <= 6 && L.T > 256) v = 3;
@@ -914,11 +948,15 @@ int homconv_effective_variant(const DevLayer& L, int v) {
 
 cudaError_t launch_homconv_v(const DevParams& P, const DevLayer& L, const u64* ct_in, const u64* A1, const u64* A2,
                              const u64* Phat, const u64* Mhat, u64* ct_out, int v, cudaStream_t s) {
-    if (v <= 0 || v > 12 || v == 7) v = homconv_default_variant(L);
-    if (v == 11 || v == 12) {
-        if (v6_supported(L))
-            return v == 11 ? launch_v6<16>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s)
-                           : launch_v6<8>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+    if (v <= 0 || v > 15 || v == 7) v = homconv_default_variant(L);
+    if (v >= 11 && v <= 15) {
+        if (v6_supported(L)) switch (v) {
+                case 11: return launch_v6<16, 1>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+                case 12: return launch_v6<8, 1>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+                case 13: return launch_v6<8, 2>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+                case 14: return launch_v6<8, 4>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+                default: return launch_v6<8, 1, true>(P, L, ct_in, A1, A2, Phat, Mhat, ct_out, s);
+            }
         v = 10;
     }
     if (v == 10) {

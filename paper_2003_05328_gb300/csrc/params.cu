@@ -31,6 +31,10 @@ static std::atomic<int> g_launch_overlap{0};
 bool fdsc_launch_overlap() { return g_launch_overlap.load(std::memory_order_relaxed) != 0; }
 extern "C" int fdsc_set_launch_overlap(int on) { return g_launch_overlap.exchange(on ? 1 : 0); }
 
+static std::atomic<int> g_decrypt_pair{1};
+bool fdsc_decrypt_pair_allowed() { return g_decrypt_pair.load(std::memory_order_relaxed) != 0; }
+extern "C" int fdsc_set_decrypt_pair(int on) { return g_decrypt_pair.exchange(on ? 1 : 0); }
+
 // ---------------------------------------------------------------- number theory
 static u64 mul_mod(u64 a, u64 b, u64 m) { return (u64)((u128)a * b % m); }
 

@@ -585,7 +585,7 @@ cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u6
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    if (P.d == 1 && L.beta == 1 && P.n >= 32 && 2ull * L.n_out <= (u64)sms) {
+    if (fdsc_decrypt_pair_allowed() && P.d == 1 && L.beta == 1 && P.n >= 32 && 2ull * L.n_out <= (u64)sms) {
         // one slot set and fewer output ciphertexts than half the SMs (a single
         // image): the two CTAs of a cluster take one parity of the coefficients
         // each, on SMs that would otherwise idle; batched work keeps one CTA per

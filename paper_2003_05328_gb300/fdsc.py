@@ -74,6 +74,7 @@ _SIGS = {
     "fdsc_decrypt": (C.c_int, [_vp, _PL, _vp, _vp, _vp, _vp]),
     "fdsc_set_homconv_variant": (C.c_int, [C.c_int]),
     "fdsc_set_launch_overlap": (C.c_int, [C.c_int]),
+    "fdsc_set_decrypt_pair": (C.c_int, [C.c_int]),
     "fdsc_calibrate": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "fdsc_encrypt_constants": (C.c_int, [_vp, _PL, _vp, C.c_uint64, _vp, _vp]),
     "fdsc_encode_share": (C.c_int, [_vp, _PL, _vp, _vp, _vp]),
@@ -316,6 +317,12 @@ def set_launch_overlap(on: bool) -> bool:
     """Programmatic dependent launch of the online kernels (default off);
     returns the previous setting."""
     return bool(lib().fdsc_set_launch_overlap(1 if on else 0))
+
+
+def set_decrypt_pair(on: bool) -> bool:
+    """One image's decryption on CTA pairs (default on; off: one CTA per
+    ciphertext, fewer instructions); returns the previous setting."""
+    return bool(lib().fdsc_set_decrypt_pair(1 if on else 0))
 
 
 # ---------------------------------------------------------------- online

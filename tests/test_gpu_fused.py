@@ -178,3 +178,25 @@ def test_binarized_layer_full_size_fused_path(F):
         b, co = int(rng.integers(ls.B)), int(rng.integers(ls.Co))
         assert np.array_equal(y[b, co], O.conv_plain(ls.p, x[b:b + 1], w[co:co + 1])[0, 0]), (b, co)
     P.close()
+
+
+def test_decrypt_pair_switch_gives_the_same_words(F):
+    """One image's decryption on CTA pairs (the default) and on one CTA per
+    ciphertext (fdsc_set_decrypt_pair(0)) write the same shares."""
+    n, p, Ci, Co, H, W = 2048, 65537, 64, 64, 32, 32
+    P = F.Params(n, p, max_T=64)
+    L = F.LayerSpec(1, Ci, Co, H, W, 2, 1)
+    lay = F.layout(P, L)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    q = P.info.q
+    ct = torch.randint(0, q, (lay.ct_out_words,), dtype=torch.int64, device="cuda", generator=g)
+    t_hat = F.keygen(P, 5)
+    a = F.decrypt_share(P, L, t_hat, ct)
+    old = F.set_decrypt_pair(False)
+    try:
+        b = F.decrypt_share(P, L, t_hat, ct)
+    finally:
+        F.set_decrypt_pair(old)
+    torch.cuda.synchronize()
+    assert old and torch.equal(a, b)
+    P.close()

@@ -330,7 +330,7 @@ def test_homconv_variants_identical(F, shape):
     ref = O.homconv(OP, OL, summed.astype(np.uint64), Ph, Mh)
     d = lambda a: dev(a.view(np.int64), np.int64)
     try:
-        for v in (1, 2, 3, 4, 5, 6, 8, 9, 10, 11, 12):
+        for v in (1, 2, 3, 4, 5, 6, 8, 9, 10, 11, 12, 13, 14, 15):
             F.set_homconv_variant(v)
             out = F.homconv_sum(P, L, d(ct), d(A1), d(A2), d(Ph), d(Mh))
             assert np.array_equal(u64(out).reshape(ref.shape), ref), v
