@@ -27,6 +27,13 @@ constexpr u32 kMaxThreads = 512;
 
 inline u32 threads_for(u32 n) { return n / 8 < 32 ? 32 : n / 8; }
 
+// The NTT_q twiddle pairs (16 n bytes) are staged in shared memory up to
+// n = 2048; at n = 4096 the kernels are instantiated with kGTw = true and read
+// them from global memory (L1-resident after the first pass), so that two
+// CTAs fit on an SM.
+inline bool global_qtw(u32 n) { return n > 2048; }
+inline u32 qtw_entries(u32 n) { return global_qtw(n) ? 0u : n; }
+
 // ---------------------------------------------------------------- L2 prefetch of a later kernel's operands
 // Up to two device ranges (16-byte aligned, whole multiples of 16 bytes)
 // split evenly over `slices` CTAs; the CTA `slice` asks the L2 cache for its
@@ -59,17 +66,19 @@ struct L2Prefetch {
 // recomputable from the seed).
 // The work of ciphertext u (one CTA); sm: constants_smem_bytes of dynamic
 // shared memory.
+template <bool kGTw>
 __device__ __forceinline__ void constants_body(unsigned char* sm, const DevParams& P, const u64* __restrict__ t_hat,
                                                u64 key_stride, u32 per_group, u64 seed,
                                                const u64* __restrict__ seeds, u64* __restrict__ ct, int c1_only,
                                                u32 u, const L2Prefetch* pf = nullptr) {
     const u32 n = P.n;
-    ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^brv, companion)
-    u64* c = reinterpret_cast<u64*>(tq + n);             // padded [n]
+    ulonglong2* tq_s = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^brv, companion), unless kGTw
+    u64* c = reinterpret_cast<u64*>(tq_s + (kGTw ? 0 : n));  // padded [n]
     u64* key = c + padded_len(n);                        // [n], the key's NTT_q words
+    const ulonglong2* tq = kGTw ? P.qfw2 : tq_s;
     __shared__ u64 cdt[19];
     const u32 grp = u / per_group;
-    stage_async(tq, P.qfw2, n * 16);
+    stage_async(tq_s, P.qfw2, kGTw ? 0 : n * 16);
     if (threadIdx.x < 19) cdt[threadIdx.x] = P.cdt[threadIdx.x];
     __syncthreads();
     const u32 ur = seeds ? u - grp * per_group : u;  // ciphertext number for the randomness
@@ -112,30 +121,34 @@ __device__ __forceinline__ void constants_body(unsigned char* sm, const DevParam
     }
 }
 
+template <bool kGTw>
 __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, const u64* __restrict__ t_hat, u64 key_stride,
                                                                 u32 per_group, u64 seed, const u64* __restrict__ seeds,
                                                                 u64* __restrict__ ct, int c1_only) {
     extern __shared__ __align__(16) unsigned char sm[];
     griddep_release();
-    constants_body(sm, P, t_hat, key_stride, per_group, seed, seeds, ct, c1_only, blockIdx.x);
+    constants_body<kGTw>(sm, P, t_hat, key_stride, per_group, seed, seeds, ct, c1_only, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- share encoding
 // One CTA per input ciphertext u = (bb, k) (beta = 1).  kMode 0: write
 // A[u] = NTT_q(Delta m); kMode 1: add it to ct[u].c1.
-template <int kMode>
+template <int kMode, bool kGTw>
 __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P, const DevLayer& L,
                                            const u32* __restrict__ x, u64* __restrict__ out, u32 u,
                                            const L2Prefetch* pf = nullptr) {
     const u32 n = P.n, S = P.S;
     const u32 np = padded_len(n);                        // padded length (even)
-    ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^brv, companion)
-    uint2* tp = reinterpret_cast<uint2*>(tq + n);        // [S] (psi_p^-brv, companion)
+    ulonglong2* tq_s = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^brv, companion), unless kGTw
+    uint2* tp = reinterpret_cast<uint2*>(tq_s + (kGTw ? 0 : n));  // [S] (psi_p^-brv, companion)
     uint2* tw_row = tp + S;                              // [W/2]
     uint2* tw_col = tw_row + (L.W >> 1);                 // [H/2]
     u64* c = reinterpret_cast<u64*>(tw_col + (L.H >> 1));  // padded [n]
     u32* slots = reinterpret_cast<u32*>(c + np);         // padded [n] = d slot sets
-    u32* planes = slots + np;                            // beta > 1: padded [d][HW], the d images' planes
+    // beta > 1: padded [d][HW], the d images' planes -- in c's room when they
+    // fit there (beta <= 2: c is written only after the planes are read)
+    u32* planes = L.beta <= 2 ? reinterpret_cast<u32*>(c) : slots + np;
+    const ulonglong2* tq = kGTw ? P.qfw2 : tq_s;
     const u32 h = u % L.beta, k = (u / L.beta) % L.T, bb = u / (L.beta * L.T);
     const u32 HW = L.HW, logHW = L.logH + L.logW, blocks = L.g_c * L.g_b;
     if (L.beta > 1) {
@@ -150,7 +163,7 @@ __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P
         stage_pairs_for_length(tw_row, L.logW, false, P);  // group 3
         stage_pairs_for_length(tw_col, L.logH, false, P);  // group 2
         stage_async(tp, P.pinv2, S * 8);                    // group 1
-        stage_async(tq, P.qfw2, n * 16);                    // group 0
+        stage_async(tq_s, P.qfw2, kGTw ? 0 : n * 16);  // group 0
         if (pf) pf->issue();
         stage_wait_groups<2>();
         for (u32 r = 0; r < P.d; r++) {  // one plane per pass: H W / 8 <= blockDim threads
@@ -191,7 +204,7 @@ __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P
     stage_pairs_for_length(tw_row, L.logW, false, P);  // group 3
     stage_pairs_for_length(tw_col, L.logH, false, P);  // group 2
     stage_async(tp, P.pinv2, S * 8);                    // group 1
-    stage_async(tq, P.qfw2, n * 16);                    // group 0
+    stage_async(tq_s, P.qfw2, kGTw ? 0 : n * 16);  // group 0
     store8(0, v);
     for (u32 e0 = 8 * blockDim.x; e0 < n; e0 += 8 * blockDim.x) {
         load8(e0, v);
@@ -220,13 +233,13 @@ __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P
     }
 }
 
-template <int kMode>
+template <int kMode, bool kGTw>
 __global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLayer L, const u32* __restrict__ x,
                                                             u64* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char sm[];
     griddep_release();
     griddep_wait();
-    share_body<kMode>(sm, P, L, x, out, blockIdx.x);
+    share_body<kMode, kGTw>(sm, P, L, x, out, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- the three producers in one launch
@@ -238,6 +251,7 @@ __global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLaye
 // issued, asks the L2 cache for its slice of two device ranges (the next
 // kernel's input-independent operands: filter plaintexts and masks), so
 // that those bytes stream from HBM while the transforms run.
+template <bool kGTw>
 __global__ void __launch_bounds__(kMaxThreads) produce_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
                                                               u64 seed, const u32* __restrict__ xA,
                                                               const u32* __restrict__ xB, u64* __restrict__ ct,
@@ -248,8 +262,8 @@ __global__ void __launch_bounds__(kMaxThreads) produce_kernel(DevParams P, DevLa
     const u32 role = blockIdx.x / L.n_in, u = blockIdx.x - role * L.n_in;
     pf.slice = blockIdx.x;
     pf.slices = gridDim.x;
-    if (role == 0) constants_body(sm, P, t_hat, 0, L.n_in, seed, nullptr, ct, 0, u, &pf);
-    else share_body<0>(sm, P, L, role == 1 ? xA : xB, role == 1 ? A : R, u, &pf);
+    if (role == 0) constants_body<kGTw>(sm, P, t_hat, 0, L.n_in, seed, nullptr, ct, 0, u, &pf);
+    else share_body<0, kGTw>(sm, P, L, role == 1 ? xA : xB, role == 1 ? A : R, u, &pf);
 }
 
 // ---------------------------------------------------------------- decrypt + fold + INTT2D
@@ -264,15 +278,15 @@ __device__ __forceinline__ u32 round_pq2(u64 v, const DevParams& P) {
 }
 
 // kMulti: a spectrum spans L.beta > 1 ciphertexts (H W > S); otherwise one.
-template <bool kMulti>
+template <bool kMulti, bool kGTw>
 __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
                                                                     u64 key_stride, const u64* __restrict__ ct,
                                                                     u32* __restrict__ y, u32 scale, u32 scale_s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const u32 n = P.n, S = P.S;
     const u32 np = padded_len(n);
-    ulonglong2* tq = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^-brv, companion)
-    uint2* tp = reinterpret_cast<uint2*>(tq + n);        // [S] (psi_p^brv, companion)
+    ulonglong2* tq_s = reinterpret_cast<ulonglong2*>(sm);  // [n] (psi^-brv, companion), unless kGTw
+    uint2* tp = reinterpret_cast<uint2*>(tq_s + (kGTw ? 0 : n));  // [S] (psi_p^brv, companion)
     uint2* tw_row = tp + S;                              // [W/2]
     uint2* tw_col = tw_row + (L.W >> 1);                 // [H/2]
     u64* c = reinterpret_cast<u64*>(tw_col + (L.H >> 1));  // padded [n]
@@ -280,6 +294,7 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
     const u32 HW = L.HW, logHW = L.logH + L.logW;
     const u32 nplanes = P.d * L.g_b;
     u32* planes = slots + np;                            // padded [d g_b HW]
+    const ulonglong2* tq = kGTw ? P.qinv2 : tq_s;
     griddep_release();
     griddep_wait();
 
@@ -307,7 +322,7 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
             }
         }
         if (h == 0) {
-            stage_async(tq, P.qinv2, n * 16);                  // group 3
+            stage_async(tq_s, P.qinv2, kGTw ? 0 : n * 16);    // group 3
             stage_async(tp, P.pfw2, S * 8);                    // group 2
             stage_pairs_for_length(tw_row, L.logW, true, P);  // group 1
             stage_pairs_for_length(tw_col, L.logH, true, P);  // group 0
@@ -525,12 +540,12 @@ cudaError_t opt_in(K kernel, size_t bytes) {
 }  // namespace
 
 size_t share_smem_bytes(const DevParams& P, const DevLayer& L) {
-    const size_t np = padded_len(P.n), npl = L.beta > 1 ? padded_len(P.d * L.HW) : 0;
-    return (size_t)P.n * 16 + np * 8 + (size_t)P.S * 8 + np * 4 + npl * 4 + (size_t)4 * (L.W + L.H);
+    const size_t np = padded_len(P.n), npl = L.beta > 2 ? padded_len(P.d * L.HW) : 0;
+    return (size_t)qtw_entries(P.n) * 16 + np * 8 + (size_t)P.S * 8 + np * 4 + npl * 4 + (size_t)4 * (L.W + L.H);
 }
 size_t decrypt_share_smem_bytes(const DevParams& P, const DevLayer& L) {
     const size_t np = padded_len(P.n), npl = padded_len(P.d * L.g_b * L.HW);
-    return (size_t)P.n * 16 + np * 8 + (size_t)P.S * 8 + np * 4 + npl * 4 + (size_t)4 * (L.W + L.H);
+    return (size_t)qtw_entries(P.n) * 16 + np * 8 + (size_t)P.S * 8 + np * 4 + npl * 4 + (size_t)4 * (L.W + L.H);
 }
 // Threads of the fused kernels: n / 8 for the length-n passes, and at least
 // H W / 8 for the line passes of one plane (more than n / 8 only when a
@@ -539,24 +554,29 @@ u32 fused_threads(const DevParams& P, const DevLayer& L) {
     const u32 t = threads_for(P.n), tl = L.HW / 8;
     return t > tl ? t : tl;
 }
-size_t constants_smem_bytes(const DevParams& P) { return (size_t)P.n * 24 + (size_t)padded_len(P.n) * 8; }
+size_t constants_smem_bytes(const DevParams& P) {
+    return (size_t)qtw_entries(P.n) * 16 + (size_t)P.n * 8 + (size_t)padded_len(P.n) * 8;
+}
 
 cudaError_t launch_constants(const DevParams& P, const DevLayer& L, const u64* t_hat, u64 key_stride, u64 seed,
                              const u64* seeds, u64* ct, cudaStream_t s, bool c1_only) {
     const size_t sm = constants_smem_bytes(P);
-    cudaError_t e = opt_in(constants_kernel, sm);
+    auto kern = global_qtw(P.n) ? constants_kernel<true> : constants_kernel<false>;
+    cudaError_t e = opt_in(kern, sm);
     if (e != cudaSuccess) return e;
-    return launch_online(constants_kernel, L.n_in, threads_for(P.n), sm, s, P, t_hat, key_stride, L.T * L.beta, seed,
+    return launch_online(kern, L.n_in, threads_for(P.n), sm, s, P, t_hat, key_stride, L.T * L.beta, seed,
                          seeds, ct, c1_only ? 1 : 0);
 }
 
 cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u64* out, bool add_to_ct,
                          cudaStream_t s) {
     const size_t sm = share_smem_bytes(P, L);
-    cudaError_t e = add_to_ct ? opt_in(share_kernel<1>, sm) : opt_in(share_kernel<0>, sm);
+    const bool g = global_qtw(P.n);
+    auto kern = add_to_ct ? (g ? share_kernel<1, true> : share_kernel<1, false>)
+                          : (g ? share_kernel<0, true> : share_kernel<0, false>);
+    cudaError_t e = opt_in(kern, sm);
     if (e != cudaSuccess) return e;
-    return launch_online(add_to_ct ? share_kernel<1> : share_kernel<0>, L.n_in, fused_threads(P, L), sm, s, P, L, x,
-                         out);
+    return launch_online(kern, L.n_in, fused_threads(P, L), sm, s, P, L, x, out);
 }
 
 size_t produce_smem_bytes(const DevParams& P, const DevLayer& L) {
@@ -568,10 +588,11 @@ cudaError_t launch_produce(const DevParams& P, const DevLayer& L, const u64* t_h
                            const u32* xB, u64* ct, u64* A, u64* R, const void* pf0, u64 pf0_bytes, const void* pf1,
                            u64 pf1_bytes, cudaStream_t s) {
     const size_t sm = produce_smem_bytes(P, L);
-    cudaError_t e = opt_in(produce_kernel, sm);
+    auto kern = global_qtw(P.n) ? produce_kernel<true> : produce_kernel<false>;
+    cudaError_t e = opt_in(kern, sm);
     if (e != cudaSuccess) return e;
     L2Prefetch pf = {{pf0, pf1}, {pf0_bytes, pf1_bytes}, 0, 0};
-    return launch_online(produce_kernel, 3 * L.n_in, fused_threads(P, L), sm, s, P, L, t_hat, seed, xA, xB, ct, A,
+    return launch_online(kern, 3 * L.n_in, fused_threads(P, L), sm, s, P, L, t_hat, seed, xA, xB, ct, A,
                          R, pf);
 }
 
@@ -590,12 +611,15 @@ cudaError_t launch_decrypt_share(const DevParams& P, const DevLayer& L, const u6
         // image): the two CTAs of a cluster take one parity of the coefficients
         // each, on SMs that would otherwise idle; batched work keeps one CTA per
         // ciphertext (the pair repeats the loads and the first products)
-        cudaError_t e = opt_in(decrypt_share_pair_kernel, sm);
+        const size_t sm2 = sm + (size_t)(P.n - qtw_entries(P.n)) * 16;  // the pair stages the NTT_q twiddles at any n
+        cudaError_t e = opt_in(decrypt_share_pair_kernel, sm2);
         if (e != cudaSuccess) return e;
-        return launch_online(decrypt_share_pair_kernel, 2 * L.n_out, threads_for(P.n), sm, s, P, L, t_hat, key_stride,
+        return launch_online(decrypt_share_pair_kernel, 2 * L.n_out, threads_for(P.n), sm2, s, P, L, t_hat, key_stride,
                              ct, y, scale, fdsc_shoup32(scale, P.p));
     }
-    auto kern = L.beta > 1 ? decrypt_share_kernel<true> : decrypt_share_kernel<false>;
+    const bool g = global_qtw(P.n);
+    auto kern = L.beta > 1 ? (g ? decrypt_share_kernel<true, true> : decrypt_share_kernel<true, false>)
+                           : (g ? decrypt_share_kernel<false, true> : decrypt_share_kernel<false, false>);
     cudaError_t e = opt_in(kern, sm);
     if (e != cudaSuccess) return e;
     return launch_online(kern, L.n_out / L.beta, fused_threads(P, L), sm, s, P, L, t_hat, key_stride, ct, y, scale,
