@@ -488,9 +488,14 @@ def run_tensor_homconv(F, flush, args):
         same = bool(torch.equal(o1, o2))
         status = F.homconv_tc_status()
         macs = 2 * ls.Co * lay.T * lay.beta * ls.n * lay.GB
-        gbt = 8 if lay.GB >= 8 else (4 if lay.GB >= 4 else (2 if lay.GB >= 2 else 1))
-        nb = 2 * gbt
-        items = lay.beta * ls.n * (-(-ls.Co // 128)) * (-(-lay.GB // gbt))
+        # the kernel's items: the d indices sharing a filter word (d <= 8) and
+        # up to 8 / d image groups, B columns nb = 2 x groups x d
+        dj = info.d if info.d <= 8 else 1
+        gbt = 1
+        while 2 * gbt <= 8 // dj and 2 * gbt <= lay.GB:
+            gbt *= 2
+        nb = 2 * gbt * dj
+        items = lay.beta * (ls.n // dj) * (-(-ls.Co // 128)) * (-(-lay.GB // gbt))
         mmas = items * (8 * (-(-lay.T // 16)) + 1)
         flops = mmas * 2 * 128 * 8 * nb * 16
         byts = 8 * (Ptc.numel() + lay.ct_in_words + 2 * lay.n_in * ls.n + lay.ct_out_words + lay.mask_words)

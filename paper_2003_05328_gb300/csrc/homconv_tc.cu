@@ -38,8 +38,10 @@
 // phases ahead of the mbarrier it polls (a parity wait cannot tell phase k
 // from phase k - 2).
 // A unit is (item, 16 input ciphertexts); an item is (J, 128 output channels,
-// up to 8 image groups).  Up to 8 TMEM accumulators let the MMAs of later
-// items run while the epilogue drains earlier ones.  Every wait is bounded: on
+// up to 8 image groups; with d slot sets per ciphertext, the d evaluation
+// indices sharing a filter word and up to 8 / d image groups).  Up to 8 TMEM
+// accumulators let the MMAs of later items run while the epilogue drains
+// earlier ones.  Every wait is bounded: on
 // a timeout the CTA records an error, stops, lets its copies and MMAs finish,
 // frees its TMEM and returns.
 #include <cuda_fp16.h>
@@ -61,7 +63,9 @@ constexpr u64 kDigitBias = 0x8080808080808080ull;
 constexpr u64 kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 
 struct TcGeom {
-    u32 NB;       // B columns (bb, c) per item: 2 x image groups per pass
+    u32 NB;       // B columns (r, bb, c) per item: 2 x image groups per pass x evaluation indices per item
+    u32 dj;       // evaluation indices per item: d (the group sharing one filter word) or 1
+    u32 lgbt;     // log2 gbt
     u32 KB;       // 16-ciphertext blocks: ceil(T / 16)
     u32 n_ct;     // 128-channel tiles
     u32 n_gbg;    // image-group passes
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     volatile u32* abort = reinterpret_cast<volatile u32*>(sm + 408);
     unsigned char* zero_blk = sm + 1024;
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const u32 nJ = L.beta * P.n;
+    const u32 nJ = L.beta * P.n / G.dj;  // items per (channel tile, image-group pass): groups of dj indices
     const u32 my_items = blockIdx.x < G.n_items ? (G.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const u32 total_units = my_items * G.KB;
 
@@ -299,7 +303,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 mbar_expect_tx(bar, bytes);
                 // indices J of one group of d share their filter unit (w_0(x^d) plaintexts)
                 bulk_g2s(smem_u32(sm + G.off_slot + s * G.ssz),
-                         Ptc + ((u64)((it.J / P.d) * G.KB + it.kb) * G.co_pad + it.ct * 128) * 256, bytes, bar);
+                         Ptc + ((u64)((it.J * G.dj / P.d) * G.KB + it.kb) * G.co_pad + it.ct * 128) * 256, bytes,
+                         bar);
             }
             if (u < total_units) {
                 *abort = 1;
@@ -316,24 +321,27 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             // input words of a unit, staged by this warp's lanes with cp.async:
             // [16][NB] ciphertext words, then [16][NB/2] A1 and [16][NB/2] A2 words of
             // the c1 columns; double-buffered so the next unit's copies fly while
-            // this one is converted
+            // this one is converted.  Column col = 2 (r gbt + bbi) + c: index
+            // r of the item's dj evaluation indices, image group bbi of the pass,
+            // ciphertext part c.
             u64* xbuf = reinterpret_cast<u64*>(sm + G.off_slot + s * G.ssz + G.az + 256 * NB);
             auto stage_x = [&](const UnitIter& t, u64* xr) {
-                const u32 h = t.J >> P.logn, j = t.J & (P.n - 1), bb0 = t.gbg * G.gbt;
+                const u32 Jb = t.J * G.dj, h = Jb >> P.logn, j = Jb & (P.n - 1), bb0 = t.gbg * G.gbt;
 #pragma unroll 2
                 for (u32 e = lane; e < 32 * NB; e += 32) {
                     u32 plane, kk, col;
                     if (e < 16 * NB) {
                         plane = 0, kk = e / NB, col = e % NB;
                     } else {
-                        const u32 r = (e - 16 * NB) % (8 * NB);
-                        plane = 1 + (e - 16 * NB) / (8 * NB), kk = r / NBH, col = 2 * (r % NBH) + 1;
+                        const u32 ra = (e - 16 * NB) % (8 * NB);
+                        plane = 1 + (e - 16 * NB) / (8 * NB), kk = ra / NBH, col = 2 * (ra % NBH) + 1;
                     }
-                    const u32 c = col & 1, k = t.kb * 16 + kk, bb = bb0 + (col >> 1);
+                    const u32 c = col & 1, k = t.kb * 16 + kk, hc2 = col >> 1;
+                    const u32 r = hc2 >> G.lgbt, bb = bb0 + (hc2 & (G.gbt - 1));
                     const u64* base = plane == 0 ? ct_in : (plane == 1 ? A1 : A2);
                     if (k < L.T && bb < L.GB && base) {
                         const u64 uin = ((u64)bb * L.T + k) * L.beta + h;
-                        cp_async8(smem_u32(xr + e), base + (plane == 0 ? uin * 2 + c : uin) * P.n + j);
+                        cp_async8(smem_u32(xr + e), base + (plane == 0 ? uin * 2 + c : uin) * P.n + j + r);
                     } else {
                         xr[e] = 0;
                     }
@@ -448,7 +456,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         UnitIter it(blockIdx.x, gridDim.x, nJ, G.n_ct, G.KB, 0);
         for (u32 li = 0; li < my_items; li++, it.next(G.KB)) {
             const u32 b = li % NBUF;
-            const u32 h = it.J >> P.logn, j = it.J & (P.n - 1);
+            const u32 Jb = it.J * G.dj, h = Jb >> P.logn, j = Jb & (P.n - 1);
             const u32 co = it.ct * 128 + r, bb0 = it.gbg * G.gbt;
             const u64 vbase = ((u64)bb0 * L.Co + co) * L.beta + h;
             const u64 obase = vbase * 2 * P.n + j, mbase = vbase * P.n + j;
@@ -456,9 +464,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             u64 mk[NBH];
 #pragma unroll
             for (int i = 0; i < NBH; i++) {
-                const u32 col = col0 + i, bb = bb0 + (col >> 1);
+                const u32 col = col0 + i, hc2 = col >> 1, bbi = hc2 & (G.gbt - 1), ri = hc2 >> G.lgbt;
                 mk[i] = 0;
-                if ((col & 1) && Mhat && co < L.Co && bb < L.GB) mk[i] = __ldg(Mhat + mbase + (u64)(col >> 1) * msk_bb);
+                if ((col & 1) && Mhat && co < L.Co && bb0 + bbi < L.GB)
+                    mk[i] = __ldg(Mhat + mbase + (u64)bbi * msk_bb + ri);
             }
             if (!__all_sync(0xffffffffu, mbar_wait(b_tfull + 8 * b, (li / NBUF) & 1, abort))) {
                 *abort = 1;
@@ -509,12 +518,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             if (co < L.Co) {
 #pragma unroll
                 for (int i = 0; i < NBH; i++) {
-                    const u32 col = col0 + i, c = col & 1;
-                    if (bb0 + (col >> 1) >= L.GB) continue;
+                    const u32 col = col0 + i, c = col & 1, hc2 = col >> 1, bbi = hc2 & (G.gbt - 1);
+                    if (bb0 + bbi >= L.GB) continue;
                     const unsigned __int128 v = V[i] - bias;  // the exact sum, in [0, 2^127)
                     u64 res = reduce128((u64)(v >> 64), (u64)v, P);
                     if (c == 1) res = submod_q(res, mk[i], P.q);
-                    ct_out[obase + (u64)(col >> 1) * out_bb + c * P.n] = res;
+                    ct_out[obase + (u64)bbi * out_bb + c * P.n + (hc2 >> G.lgbt)] = res;
                 }
             }
         }
@@ -566,18 +575,26 @@ __device__ u32 g_tc_err;  // nonzero after a CTA gave up waiting (1 loader, 2 MM
 
 }  // namespace
 
-// Geometry of the tensor-core path for a layer of ring degree n; false if
-// it does not apply (T > 128 would let a diagonal reach 2^24).
-static bool tc_geom(u32 n, const DevLayer& L, TcGeom& G, size_t& smem) {
-    if (L.T == 0 || L.T > 128 || L.GB == 0 || L.Co == 0) return false;
-    const u32 gbt = L.GB >= 8 ? 8 : (L.GB >= 4 ? 4 : (L.GB >= 2 ? 2 : 1));
+// Geometry of the tensor-core path for a layer of ring degree n with d slot
+// sets; false if it does not apply (T > 128 would let a diagonal reach 2^24).
+// An item covers the d evaluation indices that share one filter word (d <= 8)
+// and up to 8 / d image groups, so that one filter unit in shared memory
+// serves B columns N = 8 NB <= 128 (the MMA costs the same per instruction up
+// to N = 128).
+static bool tc_geom(u32 n, u32 d, const DevLayer& L, TcGeom& G, size_t& smem) {
+    if (L.T == 0 || L.T > 128 || L.GB == 0 || L.Co == 0 || d == 0 || n % d) return false;
+    const u32 dj = d <= 8 ? d : 1, gmax = 8 / dj;
+    u32 gbt = 1, lg = 0;
+    while (2 * gbt <= gmax && 2 * gbt <= L.GB) gbt *= 2, lg++;
+    G.dj = dj;
     G.gbt = gbt;
-    G.NB = 2 * gbt;
+    G.lgbt = lg;
+    G.NB = 2 * gbt * dj;
     G.KB = (L.T + 15) / 16;
     G.n_ct = (L.Co + 127) / 128;
     G.n_gbg = (L.GB + gbt - 1) / gbt;
     G.co_pad = 128 * (G.n_ct - 1) + tile_rows8(L.Co, G.n_ct - 1);
-    const u64 items = (u64)L.beta * n * G.n_ct * G.n_gbg;
+    const u64 items = (u64)L.beta * (n / dj) * G.n_ct * G.n_gbg;
     if (items > 0x7FFFFFFFull) return false;
     G.n_items = (u32)items;
     const u32 rp = tile_rows8(L.Co, 0);  // the widest tile
@@ -596,7 +613,7 @@ static bool tc_geom(u32 n, const DevLayer& L, TcGeom& G, size_t& smem) {
 bool homconv_tc_supported(u32 n, const DevLayer& L) {
     TcGeom G;
     size_t smem;
-    return tc_geom(n, L, G, smem);
+    return tc_geom(n, 1, L, G, smem);  // the shared-memory need depends on NB <= 16 alone
 }
 
 // Words (u64) of the tensor-core filter layout: 256 bytes per row per
@@ -649,8 +666,8 @@ cudaError_t launch_homconv_tc(const DevParams& P, const DevLayer& L, const u64* 
                               const u64* Ptc, const u64* Mhat, u64* ct_out, cudaStream_t s) {
     TcGeom G;
     size_t smem;
-    if (!tc_geom(P.n, L, G, smem)) return cudaErrorInvalidValue;
-    switch (G.gbt) {
+    if (!tc_geom(P.n, P.d, L, G, smem)) return cudaErrorInvalidValue;
+    switch (G.NB / 2) {
         case 1: return launch_tc<1>(P, L, G, smem, ct_in, A1, A2, Ptc, Mhat, ct_out, s);
         case 2: return launch_tc<2>(P, L, G, smem, ct_in, A1, A2, Ptc, Mhat, ct_out, s);
         case 4: return launch_tc<4>(P, L, G, smem, ct_in, A1, A2, Ptc, Mhat, ct_out, s);

@@ -392,37 +392,44 @@ def _worst_digit_word(q):
     (2048, 16, 50, 8, 32, 32, 2, 1),    # 16 image groups: two passes of 8; T = 25
     (256, 5, 34, 130, 8, 8, 1, 1),      # Co = 130: a full and a 2-channel tile; T = 34: 3 blocks; 5 groups: 4 + 1
     (1024, 1, 128, 128, 32, 32, 1, 1),  # T = 128, the largest the fp32 bound admits
+    # d > 1: an item holds the d evaluation indices that share a filter word
+    (4096, 3, 5, 9, 32, 32, 2, 1, 12289),     # d = 2, two image groups (the second half empty)
+    (4096, 8, 16, 130, 64, 64, 1, 1, 12289),  # d = 2, beta = 2, four image groups, two channel tiles
+    (1024, 9, 20, 12, 16, 16, 1, 1, 7681),    # d = 4: two groups per pass, the second pass ragged; T = 20
 ])
 def test_homconv_tc_matches_oracle(F, shape):
     """The tensor-core HomConv (digit planes in fp16, exact fp32 sums of the
     15 weight classes) gives the oracle's words, with and without the fused
     c1 addends and the HomShare mask."""
-    n, B, Ci, Co, H, W, g_c, g_b = shape
-    OP = O.params(n, 65537)
+    n, B, Ci, Co, H, W, g_c, g_b = shape[:8]
+    p = shape[8] if len(shape) > 8 else 65537
+    OP = O.params(n, p)
     OL = O.layer(OP, B, Ci, Co, H, W, g_c, g_b)
-    P = F.Params(n, 65537, max_T=max(OL.T, 1))
+    P = F.Params(n, p, max_T=max(OL.T, 1))
     L = F.LayerSpec(B, Ci, Co, H, W, g_c, g_b)
     g = np.random.default_rng(n + Ci + Co)
     ct = np.array(g.integers(0, OP.q, (OL.n_in, 2, n), dtype=np.uint64))
     A1 = np.array(g.integers(0, OP.q, (OL.n_in, n), dtype=np.uint64))
     A2 = np.array(g.integers(0, OP.q, (OL.n_in, n), dtype=np.uint64))
-    Ph = np.array(g.integers(0, OP.q, (Co * OL.T * OL.beta, n), dtype=np.uint64))
+    dd = OP.d  # the library stores one filter word per group of d indices; the oracle takes all n
+    Ph = np.array(g.integers(0, OP.q, (Co * OL.T * OL.beta, n // dd), dtype=np.uint64))
     Mh = np.array(g.integers(0, OP.q, (OL.n_out, n), dtype=np.uint64))
     ct[:, :, :4] = OP.q - 1
     Ph[:, :4] = OP.q - 1
     ct[:, :, 4:8] = 0
+    Ph_full = np.repeat(Ph, dd, axis=1)
     summed = ct.astype(object)
     summed[:, 1] = (summed[:, 1] + A1.astype(object) + A2.astype(object)) % OP.q
-    ref = O.homconv(OP, OL, summed.astype(np.uint64), Ph, Mh)
+    ref = O.homconv(OP, OL, summed.astype(np.uint64), Ph_full, Mh)
     d = lambda a: dev(a.view(np.int64), np.int64)
     Ptc = F.filter_tc(P, L, d(Ph))
-    assert Ptc.numel() == F.filter_tc_words(n, 65537, L)
+    assert Ptc.numel() == F.filter_tc_words(n, p, L)
     out = F.homconv_tc(P, L, d(ct), d(A1), d(A2), Ptc, d(Mh))
     torch.cuda.synchronize()
     assert F.homconv_tc_status() == 0
     assert np.array_equal(u64(out).reshape(ref.shape), ref)
     out = F.homconv_tc(P, L, d(ct), None, None, Ptc, None)
-    assert np.array_equal(u64(out).reshape(ref.shape), O.homconv(OP, OL, ct, Ph, None))
+    assert np.array_equal(u64(out).reshape(ref.shape), O.homconv(OP, OL, ct, Ph_full, None))
     # identical to the CUDA-core kernel on the same inputs
     assert torch.equal(F.homconv_tc(P, L, d(ct), d(A1), d(A2), Ptc, d(Mh)),
                        F.homconv_sum(P, L, d(ct), d(A1), d(A2), d(Ph), d(Mh)))
