@@ -1152,6 +1152,11 @@ def run_gpu(args, rank, local_rank, world):
     g_hc = capture(lambda: [homconv_only(d) for d in insts])
     g_hc_warm = capture(lambda: [homconv_only(insts[0]) for _ in insts])
     g_hc_seeded = capture(lambda: [homconv_seeded_only(d) for d in insts])
+    # a reference point of the memory system, not part of the path: one
+    # library reduction (torch.sum) over each instance's filter words, the
+    # same rotation and graph layout as the HomConv launches
+    read_sink = torch.empty((), dtype=torch.int64, device="cuda")
+    g_read = capture(lambda: [torch.sum(d["Phat"].view(-1), 0, out=read_sink) for d in insts])
     for _ in range(args.warmup):
         g_main.replay()
         g_hc.replay()
@@ -1223,6 +1228,9 @@ def run_gpu(args, rank, local_rank, world):
     torch.cuda.synchronize()
     ev_s = back_to_back([g_hc_seeded], hc_reps)
     torch.cuda.synchronize()
+    ev_r = back_to_back([g_read], hc_reps)
+    torch.cuda.synchronize()
+    read_ms = ev_r[0].elapsed_time(ev_r[-1]) / (hc_reps * R)
     hc_avg = ev_h[0].elapsed_time(ev_h[-1]) / (hc_reps * R)
     hc_warm_ms = ev_w[0].elapsed_time(ev_w[-1]) / (hc_reps * R)
     hc_seeded_ms = ev_s[0].elapsed_time(ev_s[-1]) / (hc_reps * R)
@@ -1283,6 +1291,12 @@ def run_gpu(args, rank, local_rank, world):
                 "macs_per_launch": macs, "launch_us": hc_avg * 1e3,
                 "timing": "%d launches back to back over the %d instances (cold), CUDA events" % (hc_reps * R, R),
                 "hbm": hbm_side, "alu": alu_side,
+                "plain_read_reference": {
+                    "us": read_ms * 1e3, "bytes": 8 * insts[0]["Phat"].numel(),
+                    "frac_of_hbm": 8 * insts[0]["Phat"].numel() / (read_ms * 1e-3) / 1e9 / peak,
+                    "what": "torch.sum over one instance's filter words (33.5 MB) per launch, instances rotated "
+                            "(cold), R launches per graph replay: what one cold launch of that size reads on "
+                            "this part, for comparison with the HomConv launch"},
                 "after_producers": {
                     "us": pj_us, "achieved_GB_per_s": alg_bytes / (pj_us * 1e-6) / 1e9,
                     "frac_of_hbm": alg_bytes / (pj_us * 1e-6) / 1e9 / peak,
