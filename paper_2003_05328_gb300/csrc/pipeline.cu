@@ -131,8 +131,10 @@ __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, con
 }
 
 // ---------------------------------------------------------------- share encoding
-// One CTA per input ciphertext u = (bb, k) (beta = 1).  kMode 0: write
-// A[u] = NTT_q(Delta m); kMode 1: add it to ct[u].c1.
+// beta = 1: one CTA per input ciphertext u = (bb, k).  beta > 1: one CTA per
+// spectrum u = (bb, k), writing its beta ciphertexts (bb, k, h) from one
+// transform of the planes.  kMode 0: write A = NTT_q(Delta m); kMode 1: add
+// it to the ciphertexts' c1.
 template <int kMode, bool kGTw>
 __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P, const DevLayer& L,
                                            const u32* __restrict__ x, u64* __restrict__ out, u32 u,
@@ -145,16 +147,15 @@ __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P
     uint2* tw_col = tw_row + (L.W >> 1);                 // [H/2]
     u64* c = reinterpret_cast<u64*>(tw_col + (L.H >> 1));  // padded [n]
     u32* slots = reinterpret_cast<u32*>(c + np);         // padded [n] = d slot sets
-    // beta > 1: padded [d][HW], the d images' planes -- in c's room when they
-    // fit there (beta <= 2: c is written only after the planes are read)
-    u32* planes = L.beta <= 2 ? reinterpret_cast<u32*>(c) : slots + np;
+    u32* planes = slots + np;                            // beta > 1: padded [d][HW], the d images' planes
     const ulonglong2* tq = kGTw ? P.qfw2 : tq_s;
-    const u32 h = u % L.beta, k = (u / L.beta) % L.T, bb = u / (L.beta * L.T);
     const u32 HW = L.HW, logHW = L.logH + L.logW, blocks = L.g_c * L.g_b;
     if (L.beta > 1) {
         // a spectrum spans beta ciphertexts (H W > S, g_c = g_b = 1): slot set r
-        // of this ciphertext holds half h of the spectrum of channel k of image
-        // bb d + r, so the CTA transforms the d whole planes and keeps half h
+        // of ciphertext (bb, k, h) holds part h of the spectrum of channel k of
+        // image bb d + r, so the CTA transforms the d whole planes once and
+        // encodes the beta parts one after the other
+        const u32 k = u % L.T, bb = u / L.T;
         for (u32 e = threadIdx.x; e < P.d * HW; e += blockDim.x) {
             const u32 r = e >> logHW, f = e & (HW - 1), b = bb * P.d + r;
             const u32 pos = (r << logHW) + (brv_bits(f >> L.logW, L.logH) << L.logW) + brv_bits(f & (L.W - 1), L.logW);
@@ -170,12 +171,35 @@ __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P
             lines_r8p<false>(planes + padx(r * HW), 1, true, L.logH, L.logW, tw_row, P.p);
             lines_r8p<false>(planes + padx(r * HW), 1, false, L.logH, L.logW, tw_col, P.p);
         }
-        for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
-            const u32 r = e >> P.logS, s = e & (S - 1);
-            slots[padx(e)] = planes[padx((r << logHW) + h * S + s)];
+        stage_wait_groups<0>();  // every table in place
+#pragma unroll 1
+        for (u32 h = 0; h < L.beta; h++) {
+            for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
+                const u32 r = e >> P.logS, s = e & (S - 1);
+                slots[padx(e)] = planes[padx((r << logHW) + h * S + s)];
+            }
+            __syncthreads();
+            ntt_r8p<false, u32>(slots, P.logS, P.d, tp, P.Sinv, P.Sinv_s, P);  // slot encode
+            for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
+                const u32 r = e >> P.logS, i = e & (S - 1);
+                c[padx(r + P.d * i)] = P.delta * slots[padx(e)];
+            }
+            __syncthreads();
+            ntt_r8p<true, u64>(c, P.logn, 1, tq, 0, 0, P);
+            const u64 uh = (u64)u * L.beta + h;  // ciphertext (bb, k, h)
+            if (kMode == 0) {
+                u64* A = out + uh * n;
+                for (u32 j = threadIdx.x; j < n; j += blockDim.x) A[j] = c[padx(j)];
+            } else {
+                u64* c1 = out + uh * 2 * n + n;
+                for (u32 j = threadIdx.x; j < n; j += blockDim.x) c1[j] = addmod_q(c1[j], c[padx(j)], P.q);
+            }
+            // the next part's slot copy writes slots only: c is rewritten after
+            // the slot transform's barriers
         }
-        __syncthreads();
+        return;
     } else {
+    const u32 k = u % L.T, bb = u / L.T;
     // every load is issued before anything waits: the share's words (eight
     // per thread), then the twiddle tables in the order they are needed
     auto load8 = [&](u32 e0, u32 (&v)[8]) {
@@ -259,7 +283,15 @@ __global__ void __launch_bounds__(kMaxThreads) produce_kernel(DevParams P, DevLa
     extern __shared__ __align__(16) unsigned char sm[];
     griddep_release();
     griddep_wait();
-    const u32 role = blockIdx.x / L.n_in, u = blockIdx.x - role * L.n_in;
+    // CTAs [0, n_in): constants of ciphertext u; then n_in / beta CTAs per
+    // share encoding, one per spectrum
+    const u32 nsh = L.n_in / L.beta;
+    u32 role = 0, u = blockIdx.x;
+    if (blockIdx.x >= L.n_in) {
+        const u32 b = blockIdx.x - L.n_in;
+        role = 1 + b / nsh;
+        u = b % nsh;
+    }
     pf.slice = blockIdx.x;
     pf.slices = gridDim.x;
     if (role == 0) constants_body<kGTw>(sm, P, t_hat, 0, L.n_in, seed, nullptr, ct, 0, u, &pf);
@@ -540,7 +572,7 @@ cudaError_t opt_in(K kernel, size_t bytes) {
 }  // namespace
 
 size_t share_smem_bytes(const DevParams& P, const DevLayer& L) {
-    const size_t np = padded_len(P.n), npl = L.beta > 2 ? padded_len(P.d * L.HW) : 0;
+    const size_t np = padded_len(P.n), npl = L.beta > 1 ? padded_len(P.d * L.HW) : 0;
     return (size_t)qtw_entries(P.n) * 16 + np * 8 + (size_t)P.S * 8 + np * 4 + npl * 4 + (size_t)4 * (L.W + L.H);
 }
 size_t decrypt_share_smem_bytes(const DevParams& P, const DevLayer& L) {
@@ -576,7 +608,7 @@ cudaError_t launch_share(const DevParams& P, const DevLayer& L, const u32* x, u6
                           : (g ? share_kernel<0, true> : share_kernel<0, false>);
     cudaError_t e = opt_in(kern, sm);
     if (e != cudaSuccess) return e;
-    return launch_online(kern, L.n_in, fused_threads(P, L), sm, s, P, L, x, out);
+    return launch_online(kern, L.n_in / L.beta, fused_threads(P, L), sm, s, P, L, x, out);
 }
 
 size_t produce_smem_bytes(const DevParams& P, const DevLayer& L) {
@@ -592,7 +624,7 @@ cudaError_t launch_produce(const DevParams& P, const DevLayer& L, const u64* t_h
     cudaError_t e = opt_in(kern, sm);
     if (e != cudaSuccess) return e;
     L2Prefetch pf = {{pf0, pf1}, {pf0_bytes, pf1_bytes}, 0, 0};
-    return launch_online(kern, 3 * L.n_in, fused_threads(P, L), sm, s, P, L, t_hat, seed, xA, xB, ct, A,
+    return launch_online(kern, L.n_in + 2 * (L.n_in / L.beta), fused_threads(P, L), sm, s, P, L, t_hat, seed, xA, xB, ct, A,
                          R, pf);
 }
 
