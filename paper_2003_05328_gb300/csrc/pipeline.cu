@@ -311,7 +311,7 @@ __device__ __forceinline__ u32 round_pq2(u64 v, const DevParams& P) {
 
 // kMulti: a spectrum spans L.beta > 1 ciphertexts (H W > S); otherwise one.
 template <bool kMulti, bool kGTw>
-__global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
+__global__ void __launch_bounds__(kMaxThreads, kMulti ? 2 : 0) decrypt_share_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
                                                                     u64 key_stride, const u64* __restrict__ ct,
                                                                     u32* __restrict__ y, u32 scale, u32 scale_s) {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -342,27 +342,55 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_share_kernel(DevParams P,
         const u64* c1 = c0 + n;
         // v = c0 t + c1: all of a thread's words (n / blockDim <= 8 of each) are
         // requested at once, before the twiddle tables, which are copied in the
-        // order they are needed
-        u64 a[8], t[8], b[8];
+        // order they are needed; with several ciphertexts per spectrum, four at
+        // a time (fewer registers: two CTAs share an SM)
+        if constexpr (kMulti) {
 #pragma unroll
-        for (int r = 0; r < 8; r++) {
-            const u32 j = threadIdx.x + (u32)r * blockDim.x;
-            if (j < n) {
-                a[r] = __ldg(c0 + j);
-                t[r] = __ldg(t_hat + j);
-                b[r] = __ldg(c1 + j);
+            for (int r0 = 0; r0 < 8; r0 += 4) {
+                u64 a[4], t[4], b[4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const u32 j = threadIdx.x + (u32)(r0 + r) * blockDim.x;
+                    if (j < n) {
+                        a[r] = __ldg(c0 + j);
+                        t[r] = __ldg(t_hat + j);
+                        b[r] = __ldg(c1 + j);
+                    }
+                }
+                if (h == 0 && r0 == 0) {
+                    stage_async(tq_s, P.qinv2, kGTw ? 0 : n * 16);    // group 3
+                    stage_async(tp, P.pfw2, S * 8);                    // group 2
+                    stage_pairs_for_length(tw_row, L.logW, true, P);  // group 1
+                    stage_pairs_for_length(tw_col, L.logH, true, P);  // group 0
+                }
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const u32 j = threadIdx.x + (u32)(r0 + r) * blockDim.x;
+                    if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
+                }
             }
-        }
-        if (h == 0) {
-            stage_async(tq_s, P.qinv2, kGTw ? 0 : n * 16);    // group 3
-            stage_async(tp, P.pfw2, S * 8);                    // group 2
-            stage_pairs_for_length(tw_row, L.logW, true, P);  // group 1
-            stage_pairs_for_length(tw_col, L.logH, true, P);  // group 0
-        }
+        } else {
+            u64 a[8], t[8], b[8];
 #pragma unroll
-        for (int r = 0; r < 8; r++) {
-            const u32 j = threadIdx.x + (u32)r * blockDim.x;
-            if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
+            for (int r = 0; r < 8; r++) {
+                const u32 j = threadIdx.x + (u32)r * blockDim.x;
+                if (j < n) {
+                    a[r] = __ldg(c0 + j);
+                    t[r] = __ldg(t_hat + j);
+                    b[r] = __ldg(c1 + j);
+                }
+            }
+            if (h == 0) {
+                stage_async(tq_s, P.qinv2, kGTw ? 0 : n * 16);    // group 3
+                stage_async(tp, P.pfw2, S * 8);                    // group 2
+                stage_pairs_for_length(tw_row, L.logW, true, P);  // group 1
+                stage_pairs_for_length(tw_col, L.logH, true, P);  // group 0
+            }
+#pragma unroll
+            for (int r = 0; r < 8; r++) {
+                const u32 j = threadIdx.x + (u32)r * blockDim.x;
+                if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
+            }
         }
         stage_wait_groups<3>();
         ntt_r8p<false, u64>(c, P.logn, 1, tq, P.ninv, P.ninv_s, P);
