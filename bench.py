@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 import fdsc_inputs as FI  # noqa: E402
 
 METRIC = "HomConv layers/s & mod-q MAC/s at 32×32×64; p50/p99 served latency"
-PIPE_DEPTH = 2      # steps in flight in the pipelined schedule
+STAGES = 3         # streams of the pipelined schedule: producers, HomConv, decryption
 GRAPH_STEPS = 220   # steps recorded in one graph of the timed loop (20 rotations of the instances)
 WORKLOAD = "cfg1"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -1014,8 +1014,7 @@ def run_gpu(args, rank, local_rank, world):
         insts.append(d)
     LAUNCHES_PER_STEP = 4  # producers, HomConv, decryption, Bob's INTT2D
     side = [torch.cuda.Stream() for _ in range(3)]
-    lanes = [torch.cuda.Stream() for _ in range(PIPE_DEPTH)]
-    lane_side = [torch.cuda.Stream() for _ in range(PIPE_DEPTH)]
+    s_prod, s_hc, s_dec, s_bob = (torch.cuda.Stream() for _ in range(STAGES + 1))
 
     def step(d):
         """One online layer on the current stream: Alice's encryption
@@ -1036,31 +1035,35 @@ def run_gpu(args, rank, local_rank, world):
         return produced
 
     def steps_pipelined(seq):
-        """Consecutive steps (independent layers) software-pipelined over
-        PIPE_DEPTH streams: step i runs on lane i mod PIPE_DEPTH, and its
-        producers start once step i-1's producers are done, so they overlap
-        step i-1's HomConv and decryption; a lane's next step waits for its
-        previous one (at most PIPE_DEPTH steps in flight).  Every step is the
-        whole layer, in the paper's order."""
+        """Consecutive steps (independent layers) software-pipelined by stage:
+        every step's producers run on one stream, its HomConv on a second once
+        they are done, its decryption on a third once that is done (and Bob's
+        INTT2D on a fourth), so the producers of later steps, one step's
+        HomConv and an earlier step's decryption run at once.  Every step is
+        the whole layer, in the paper's order.  seq holds (instance, buffers)
+        pairs: a step reads its instance's inputs (rotated over the R
+        instances) and writes only its own buffers (a set per step of the
+        graph), so no stream can overwrite what another still reads, however
+        far the producers run ahead."""
         main = torch.cuda.current_stream()
-        for st in lanes + lane_side:
+        for st in (s_prod, s_hc, s_dec, s_bob):
             st.wait_stream(main)
-        prev = None
-        for i, d in enumerate(seq):
-            st, sd = lanes[i % PIPE_DEPTH], lane_side[i % PIPE_DEPTH]
-            with torch.cuda.stream(st):
-                if prev is not None:
-                    st.wait_event(prev)
-                sd.wait_stream(st)
-                with torch.cuda.stream(sd):
-                    F.intt2d(P, d["sB4"], out=d["yB"])
-                F.online_produce(P, L, d["t_hat"], d["es"], d["xA"], d["xB"], d["ct"], d["A_msg"], d["A_rec"])
-                prev = torch.cuda.Event()
-                prev.record(st)
-                F.homconv_sum(P, L, d["ct"], d["A_msg"], d["A_rec"], d["Phat"], d["Mhat"], out=d["ct_out"])
-                F.decrypt_share(P, L, d["t_hat"], d["ct_out"], out=d["yA"])
-                st.wait_stream(sd)
-        for st in lanes:
+        for d, o in seq:
+            with torch.cuda.stream(s_prod):
+                F.online_produce(P, L, d["t_hat"], d["es"], d["xA"], d["xB"], o["ct"], o["A_msg"], o["A_rec"])
+                produced = torch.cuda.Event()
+                produced.record(s_prod)
+            with torch.cuda.stream(s_bob):
+                F.intt2d(P, d["sB4"], out=o["yB"])
+            with torch.cuda.stream(s_hc):
+                s_hc.wait_event(produced)
+                F.homconv_sum(P, L, o["ct"], o["A_msg"], o["A_rec"], d["Phat"], d["Mhat"], out=o["ct_out"])
+                convolved = torch.cuda.Event()
+                convolved.record(s_hc)
+            with torch.cuda.stream(s_dec):
+                s_dec.wait_event(convolved)
+                F.decrypt_share(P, L, d["t_hat"], o["ct_out"], out=o["yA"])
+        for st in (s_prod, s_hc, s_dec, s_bob):
             main.wait_stream(st)
 
     def step_4streams(d):
@@ -1106,14 +1109,23 @@ def run_gpu(args, rank, local_rank, world):
             step(d)
             step_unfused(d)
     torch.cuda.synchronize()
-    # the pipelined schedule gives every step's words exactly (checked on two instances)
-    ref = [(d["yA"].clone(), d["yB"].clone()) for d in insts[:2]]
-    for d in insts[:2]:
-        d["yA"].zero_()
-        d["yB"].zero_()
-    steps_pipelined(insts)
+    # the pipelined graphs: G = min(K, GRAPH_STEPS) steps, each writing its own
+    # buffer set (ciphertexts, HomConv output, both output shares)
+    G = max(1, min(args.steps, GRAPH_STEPS))
+    bufs = [dict(ct=torch.empty_like(insts[0]["ct"]), A_msg=torch.empty_like(insts[0]["A_msg"]),
+                 A_rec=torch.empty_like(insts[0]["A_rec"]), ct_out=torch.empty_like(insts[0]["ct_out"]),
+                 yA=torch.empty_like(insts[0]["yA"]), yB=torch.empty_like(insts[0]["yB"])) for _ in range(G)]
+    pipe_seq = lambda k: [(insts[i % R], bufs[i]) for i in range(k)]
+    # the pipelined schedule gives every step's words exactly (checked on the first 2 R steps of a graph)
+    ref = [(d["yA"].clone(), d["yB"].clone()) for d in insts]
+    n_chk = min(G, 2 * R)
+    for o in bufs[:n_chk]:
+        o["yA"].zero_()
+        o["yB"].zero_()
+    steps_pipelined(pipe_seq(n_chk))
     torch.cuda.synchronize()
-    pipelined_ok = all(torch.equal(d["yA"], a) and torch.equal(d["yB"], b) for d, (a, b) in zip(insts, ref))
+    pipelined_ok = all(torch.equal(bufs[i]["yA"], ref[i % R][0]) and torch.equal(bufs[i]["yB"], ref[i % R][1])
+                       for i in range(n_chk))
     if not pipelined_ok:
         raise RuntimeError("pipelined steps differ from single steps")
     s = torch.cuda.Stream()
@@ -1129,13 +1141,12 @@ def run_gpu(args, rank, local_rank, world):
         torch.cuda.current_stream().wait_stream(s)
         return gr
 
-    # exactly K steps: G = min(K, GRAPH_STEPS) consecutive steps (cycling over the
-    # R instances) recorded in one pipelined graph, replayed K // G times, then a
-    # graph of the remaining K mod G steps
-    G = max(1, min(args.steps, GRAPH_STEPS))
-    g_main = capture(lambda: steps_pipelined([insts[i % R] for i in range(G)]))
+    # exactly K steps: G consecutive steps (cycling over the R instances)
+    # recorded in one pipelined graph, replayed K // G times, then a graph of
+    # the remaining K mod G steps
+    g_main = capture(lambda: steps_pipelined(pipe_seq(G)))
     rem = args.steps % G
-    g_rem = capture(lambda: steps_pipelined([insts[i % R] for i in range(rem)])) if rem else None
+    g_rem = capture(lambda: steps_pipelined(pipe_seq(rem))) if rem else None
     g_step_pdl = [capture(lambda d=d: step(d)) for d in insts]
     # each instance's producers alone, and followed by its HomConv (one graph
     # each): the difference is the time HomConv adds after the producers' join
@@ -1342,10 +1353,11 @@ def run_gpu(args, rank, local_rank, world):
                    "step": "online_produce (encryption constants | encode_share(x_A) | encode_share(x_B), one "
                            "launch) -> homconv_sum (HomRec + HomConv + HomShare) -> decrypt_share, intt2d(s_B) on a "
                            "side stream, programmatic dependent launch; consecutive steps (independent layers) "
-                           "pipelined over %d streams (step i's producers after step i-1's, overlapping its HomConv "
-                           "and decryption); K steps timed back to back as %d-step graphs (K // %d of them, then one "
-                           "of K mod %d); per-step p50/p99 from one step alone per graph with an event at every "
-                           "boundary" % (PIPE_DEPTH, G, G, G),
+                           "pipelined by stage over %d streams (producers, HomConv, decryption; each step of a graph "
+                           "writes its own ciphertext and output buffers, its inputs rotate over the instances); K "
+                           "steps timed back to back as %d-step graphs (K // %d of them, then one of K mod %d); "
+                           "per-step p50/p99 from one step alone per graph with an event at every boundary"
+                           % (STAGES, G, G, G),
                    "homconv_variant": variant_used(lay.T, args.homconv_variant)},
         "mac_per_s": value * 2 * ls.Co * ls.Ci * ls.H * ls.W,
         "homconv_layers_per_s": ls.B / (hc_avg * 1e-3),
