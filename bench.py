@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 import fdsc_inputs as FI  # noqa: E402
 
 METRIC = "HomConv layers/s & mod-q MAC/s at 32×32×64; p50/p99 served latency"
-STAGES = 3         # streams of the pipelined schedule: producers, HomConv, decryption
+STAGE_STREAMS = (1, 2, 2)  # streams per stage of the pipelined schedule: producers, HomConv, decryption
 GRAPH_STEPS = 220   # steps recorded in one graph of the timed loop (20 rotations of the instances)
 WORKLOAD = "cfg1"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -1014,7 +1014,11 @@ def run_gpu(args, rank, local_rank, world):
         insts.append(d)
     LAUNCHES_PER_STEP = 4  # producers, HomConv, decryption, Bob's INTT2D
     side = [torch.cuda.Stream() for _ in range(3)]
-    s_prod, s_hc, s_dec, s_bob = (torch.cuda.Stream() for _ in range(STAGES + 1))
+    s_prod = [torch.cuda.Stream() for _ in range(STAGE_STREAMS[0])]
+    s_hc = [torch.cuda.Stream() for _ in range(STAGE_STREAMS[1])]
+    s_dec = [torch.cuda.Stream() for _ in range(STAGE_STREAMS[2])]
+    s_bob = torch.cuda.Stream()
+    stage_streams = s_prod + s_hc + s_dec + [s_bob]
 
     def step(d):
         """One online layer on the current stream: Alice's encryption
@@ -1036,34 +1040,37 @@ def run_gpu(args, rank, local_rank, world):
 
     def steps_pipelined(seq):
         """Consecutive steps (independent layers) software-pipelined by stage:
-        every step's producers run on one stream, its HomConv on a second once
-        they are done, its decryption on a third once that is done (and Bob's
-        INTT2D on a fourth), so the producers of later steps, one step's
-        HomConv and an earlier step's decryption run at once.  Every step is
-        the whole layer, in the paper's order.  seq holds (instance, buffers)
-        pairs: a step reads its instance's inputs (rotated over the R
-        instances) and writes only its own buffers (a set per step of the
-        graph), so no stream can overwrite what another still reads, however
-        far the producers run ahead."""
+        every step's producers run on a producer stream, its HomConv on a
+        HomConv stream once they are done, its decryption on a decryption
+        stream once that is done (and Bob's INTT2D on a stream of its own);
+        step i takes stream i mod k of a stage with k streams (STAGE_STREAMS:
+        two HomConvs and two decryptions of consecutive steps overlap), so
+        producers of later steps, HomConvs and decryptions of earlier ones run
+        at once.  Every step is the whole layer, in the paper's order.  seq
+        holds (instance, buffers) pairs: a step reads its instance's inputs
+        (rotated over the R instances) and writes only its own buffers (a set
+        per step of the graph), so no stream can overwrite what another still
+        reads, however far the producers run ahead."""
         main = torch.cuda.current_stream()
-        for st in (s_prod, s_hc, s_dec, s_bob):
+        for st in stage_streams:
             st.wait_stream(main)
-        for d, o in seq:
-            with torch.cuda.stream(s_prod):
+        for i, (d, o) in enumerate(seq):
+            sp, sh, sd = s_prod[i % len(s_prod)], s_hc[i % len(s_hc)], s_dec[i % len(s_dec)]
+            with torch.cuda.stream(sp):
                 F.online_produce(P, L, d["t_hat"], d["es"], d["xA"], d["xB"], o["ct"], o["A_msg"], o["A_rec"])
                 produced = torch.cuda.Event()
-                produced.record(s_prod)
+                produced.record(sp)
             with torch.cuda.stream(s_bob):
                 F.intt2d(P, d["sB4"], out=o["yB"])
-            with torch.cuda.stream(s_hc):
-                s_hc.wait_event(produced)
+            with torch.cuda.stream(sh):
+                sh.wait_event(produced)
                 F.homconv_sum(P, L, o["ct"], o["A_msg"], o["A_rec"], d["Phat"], d["Mhat"], out=o["ct_out"])
                 convolved = torch.cuda.Event()
-                convolved.record(s_hc)
-            with torch.cuda.stream(s_dec):
-                s_dec.wait_event(convolved)
+                convolved.record(sh)
+            with torch.cuda.stream(sd):
+                sd.wait_event(convolved)
                 F.decrypt_share(P, L, d["t_hat"], o["ct_out"], out=o["yA"])
-        for st in (s_prod, s_hc, s_dec, s_bob):
+        for st in stage_streams:
             main.wait_stream(st)
 
     def step_4streams(d):
@@ -1353,11 +1360,11 @@ def run_gpu(args, rank, local_rank, world):
                    "step": "online_produce (encryption constants | encode_share(x_A) | encode_share(x_B), one "
                            "launch) -> homconv_sum (HomRec + HomConv + HomShare) -> decrypt_share, intt2d(s_B) on a "
                            "side stream, programmatic dependent launch; consecutive steps (independent layers) "
-                           "pipelined by stage over %d streams (producers, HomConv, decryption; each step of a graph "
-                           "writes its own ciphertext and output buffers, its inputs rotate over the instances); K "
-                           "steps timed back to back as %d-step graphs (K // %d of them, then one of K mod %d); "
-                           "per-step p50/p99 from one step alone per graph with an event at every boundary"
-                           % (STAGES, G, G, G),
+                           "pipelined by stage (%d / %d / %d streams for producers / HomConv / decryption; each "
+                           "step of a graph writes its own ciphertext and output buffers, its inputs rotate over "
+                           "the instances); K steps timed back to back as %d-step graphs (K // %d of them, then one "
+                           "of K mod %d); per-step p50/p99 from one step alone per graph with an event at every "
+                           "boundary" % (STAGE_STREAMS + (G, G, G)),
                    "homconv_variant": variant_used(lay.T, args.homconv_variant)},
         "mac_per_s": value * 2 * ls.Co * ls.Ci * ls.H * ls.W,
         "homconv_layers_per_s": ls.B / (hc_avg * 1e-3),
