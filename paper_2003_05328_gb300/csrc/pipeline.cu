@@ -202,14 +202,22 @@ __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P
     const u32 k = u % L.T, bb = u / L.T;
     // every load is issued before anything waits: the share's words (eight
     // per thread), then the twiddle tables in the order they are needed
+    // (the block's image and channel are divided out only when the block
+    // changes: a warp's words share one block, since H W >= 64)
     auto load8 = [&](u32 e0, u32 (&v)[8]) {
+        u32 last = ~0u, bq = 0, br = 0;
 #pragma unroll
         for (int t = 0; t < 8; t++) {
             const u32 e = e0 + threadIdx.x + (u32)t * blockDim.x;
             const u32 r = e >> P.logS, s = e & (S - 1), blk = s >> logHW, f = s & (HW - 1);
             v[t] = 0;
             if (e < n && blk < blocks) {
-                const u32 b = (bb * P.d + r) * L.g_b + blk / L.g_c, ci = k * L.g_c + blk % L.g_c;
+                if (blk != last) {
+                    last = blk;
+                    bq = blk / L.g_c;
+                    br = blk - bq * L.g_c;
+                }
+                const u32 b = (bb * P.d + r) * L.g_b + bq, ci = k * L.g_c + br;
                 if (b < L.B && ci < L.Ci) v[t] = __ldg(x + ((u64)b * L.Ci + ci) * HW + f);
             }
         }
