@@ -87,10 +87,29 @@ __device__ __forceinline__ void constants_body(unsigned char* sm, const DevParam
         seed = seeds[grp];
     }
     // NTT_q(e) needs the seed alone: it runs while the previous kernel finishes
+    // The same discrete Gaussian as gauss_sample (sign bit 63, magnitude = the
+    // table entries the low 63 bits reach), eight coefficients at a time, so
+    // that each table entry is read from shared memory once per eight draws
     const u64 keyE = stream_key(seed, DOM_E);
-    for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
-        const int e = gauss_sample(stream_at(keyE, (u64)ur * n + i), cdt);
-        c[padx(i)] = e >= 0 ? (u64)e : P.q - (u64)(-e);
+    for (u32 i0 = 0; i0 < n; i0 += 8 * blockDim.x) {
+        u64 r[8];
+        int a[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            r[t] = stream_at(keyE, (u64)ur * n + i0 + threadIdx.x + (u32)t * blockDim.x);
+            a[t] = 0;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 19; kk++) {
+            const u64 ck = cdt[kk];
+#pragma unroll
+            for (int t = 0; t < 8; t++) a[t] += ((r[t] & 0x7FFFFFFFFFFFFFFFull) >= ck);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            const u32 i = i0 + threadIdx.x + (u32)t * blockDim.x;
+            if (i < n) c[padx(i)] = (r[t] >> 63) ? (a[t] ? P.q - (u64)a[t] : 0) : (u64)a[t];
+        }
     }
     stage_wait();
     if (pf) pf->issue();
@@ -284,7 +303,7 @@ __global__ void __launch_bounds__(kMaxThreads) share_kernel(DevParams P, DevLaye
 // kernel's input-independent operands: filter plaintexts and masks), so
 // that those bytes stream from HBM while the transforms run.
 template <bool kGTw>
-__global__ void __launch_bounds__(kMaxThreads) produce_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
+__global__ void __launch_bounds__(kMaxThreads, kGTw ? 2 : 0) produce_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
                                                               u64 seed, const u32* __restrict__ xA,
                                                               const u32* __restrict__ xB, u64* __restrict__ ct,
                                                               u64* __restrict__ A, u64* __restrict__ R, L2Prefetch pf) {
