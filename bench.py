@@ -1129,6 +1129,10 @@ def run_gpu(args, rank, local_rank, world):
     for o in bufs[:n_chk]:
         o["yA"].zero_()
         o["yB"].zero_()
+    # the pipelined schedule decrypts each ciphertext with one CTA: the pair form
+    # (two CTAs per ciphertext in a cluster) is faster alone but slower while
+    # producers and HomConvs share the GPU (20.8 against 18.4 us per step)
+    pair_prev = F.set_decrypt_pair(False)
     steps_pipelined(pipe_seq(n_chk))
     torch.cuda.synchronize()
     pipelined_ok = all(torch.equal(bufs[i]["yA"], ref[i % R][0]) and torch.equal(bufs[i]["yB"], ref[i % R][1])
@@ -1154,6 +1158,7 @@ def run_gpu(args, rank, local_rank, world):
     g_main = capture(lambda: steps_pipelined(pipe_seq(G)))
     rem = args.steps % G
     g_rem = capture(lambda: steps_pipelined(pipe_seq(rem))) if rem else None
+    F.set_decrypt_pair(pair_prev)
     g_step_pdl = [capture(lambda d=d: step(d)) for d in insts]
     # each instance's producers alone, and followed by its HomConv (one graph
     # each): the difference is the time HomConv adds after the producers' join
@@ -1360,9 +1365,9 @@ def run_gpu(args, rank, local_rank, world):
                    "step": "online_produce (encryption constants | encode_share(x_A) | encode_share(x_B), one "
                            "launch) -> homconv_sum (HomRec + HomConv + HomShare) -> decrypt_share, intt2d(s_B) on a "
                            "side stream, programmatic dependent launch; consecutive steps (independent layers) "
-                           "pipelined by stage (%d / %d / %d streams for producers / HomConv / decryption; each "
-                           "step of a graph writes its own ciphertext and output buffers, its inputs rotate over "
-                           "the instances); K steps timed back to back as %d-step graphs (K // %d of them, then one "
+                           "pipelined by stage (%d / %d / %d streams for producers / HomConv / decryption, one "
+                           "CTA per decrypted ciphertext; each step of a graph writes its own ciphertext and output "
+                           "buffers, its inputs rotate over the instances); K steps timed back to back as %d-step graphs (K // %d of them, then one "
                            "of K mod %d); per-step p50/p99 from one step alone per graph with an event at every "
                            "boundary" % (STAGE_STREAMS + (G, G, G)),
                    "homconv_variant": variant_used(lay.T, args.homconv_variant)},
