@@ -49,7 +49,7 @@ enum {
     FDSC_ERR_NOISE = -2,       /* the decryption noise bound fails (q too small)  */
     FDSC_ERR_OOM = -3,         /* device or host allocation failed                */
     FDSC_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed     */
-    FDSC_ERR_UNSUPPORTED = -5, /* valid but outside what this build implements    */
+    FDSC_ERR_UNSUPPORTED = -5, /* valid but outside what this library implements  */
     FDSC_ERR_TIMEOUT = -6,     /* a bounded wait ran out                          */
     FDSC_ERR_BUDGET = -7       /* a request can never fit the server's HBM budget */
 };
