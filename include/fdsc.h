@@ -520,8 +520,16 @@ int fdsc_layer_online_noalloc(const fdsc_params* P, const fdsc_layer* L, const u
  * with two image groups per thread, 3 carry-chained 128-bit accumulation,
  * 4 input tile staged in shared memory with carry-chained accumulation,
  * 5 staged tile with limb columns, 6 staged tile with lazy 32-bit-limb
- * columns.  FDSC_ERR_ARG for other values.  Not synchronised with concurrent
- * calls. */
+ * columns, 8 / 9 staged tile with Karatsuba limb columns and one / two image
+ * groups per CTA, 10 staged tile with two evaluation indices per lane
+ * (T a multiple of 4 and at most 128, else 4), 11 / 12 the same with the
+ * filter streamed through a shared-memory ring of 16 / 8 terms (T <= 64,
+ * else 10), 13 / 14 variant 12 with 2 / 4 partial sums per output word,
+ * 15 variant 12 reading its first filter terms before it waits for the
+ * kernel before it: with launch overlap on (fdsc_set_launch_overlap) that
+ * kernel must not write P_hat.  A variant that does not fit a layer falls
+ * back as stated.  7 and values outside 0-15: FDSC_ERR_ARG (the tensor-core
+ * kernel is fdsc_homconv_tc).  Not synchronised with concurrent calls. */
 int fdsc_set_homconv_variant(int variant);
 
 /* Launch overlap for the online kernels (on = 1; off = 0, the default):
