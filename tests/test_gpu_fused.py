@@ -200,3 +200,110 @@ def test_decrypt_pair_switch_gives_the_same_words(F):
     torch.cuda.synchronize()
     assert old and torch.equal(a, b)
     P.close()
+
+
+_PIPELINE_REFS = {}
+
+
+@pytest.mark.parametrize("pair", [False, True])
+def test_stage_pipelined_steps_match_the_oracle(F, pair):
+    """The timed schedule of the one-image 32x32x64 layer: consecutive steps
+    (three instances with their own weights, keys, seeds and shares, cycled
+    over seven steps) pipelined by stage -- every step's producers in one
+    launch on a producer stream, its HomConv on one of two HomConv streams,
+    its decryption on one of two decryption streams, Bob's INTT2D on a
+    stream of its own -- with programmatic dependent launch, run eagerly and
+    as one CUDA graph replayed twice: every step's two output shares are the
+    oracle's words for its instance (pair: decryption on CTA pairs)."""
+    c = FI.CONFIGS["cfg1"]
+    ls = c.layers[0]
+    OP = O.params(ls.n, ls.p)
+    info = F.params_query(ls.n, ls.p)
+    g_c, g_b = FI.default_pack(ls, info.S)
+    OL = O.layer(OP, ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
+    P = F.Params(ls.n, ls.p, max_T=OL.T)
+    L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
+    lay = F.layout(P, L)
+    R, G = 3, 7
+    insts, refs = [], []
+    for r in range(R):
+        xA, xB = FI.shares(ls, c.cid, r)
+        w = FI.weights(ls, c.cid, r)
+        ks, es, ss = FI.seeds(c.cid, r)
+        if r not in _PIPELINE_REFS:  # the oracle takes a few seconds per instance
+            _PIPELINE_REFS[r] = O.round_trip(OP, OL, xA, xB, w, ks, es, ss)
+        refs.append(_PIPELINE_REFS[r])
+        d = dict(es=es, t_hat=F.keygen(P, ks), Phat=F.filter_prepare(P, L, dev(w, np.int8)),
+                 xA=dev(xA, np.int32), xB=dev(xB, np.int32))
+        d["Mhat"], sB = F.mask_prepare(P, L, ss)
+        d["sB4"] = sB.view(ls.B, ls.Co, ls.H, ls.W)
+        insts.append(d)
+
+    def buffers():
+        return dict(ct=torch.empty(lay.ct_in_words, dtype=torch.int64, device="cuda"),
+                    A=torch.empty(lay.n_in * ls.n, dtype=torch.int64, device="cuda"),
+                    R=torch.empty(lay.n_in * ls.n, dtype=torch.int64, device="cuda"),
+                    out=torch.empty(lay.ct_out_words, dtype=torch.int64, device="cuda"),
+                    yA=torch.zeros((ls.B, ls.Co, ls.H, ls.W), dtype=torch.int32, device="cuda"),
+                    yB=torch.zeros((ls.B, ls.Co, ls.H, ls.W), dtype=torch.int32, device="cuda"))
+
+    bufs = [buffers() for _ in range(G)]
+    s_prod = torch.cuda.Stream()
+    s_hc = [torch.cuda.Stream(), torch.cuda.Stream()]
+    s_dec = [torch.cuda.Stream(), torch.cuda.Stream()]
+    s_bob = torch.cuda.Stream()
+    streams = [s_prod, s_bob] + s_hc + s_dec
+
+    def steps():
+        main = torch.cuda.current_stream()
+        for st in streams:
+            st.wait_stream(main)
+        for i, o in enumerate(bufs):
+            d = insts[i % R]
+            with torch.cuda.stream(s_prod):
+                F.online_produce(P, L, d["t_hat"], d["es"], d["xA"], d["xB"], o["ct"], o["A"], o["R"])
+                produced = torch.cuda.Event()
+                produced.record(s_prod)
+            with torch.cuda.stream(s_bob):
+                F.intt2d(P, d["sB4"], out=o["yB"])
+            sh, sd = s_hc[i % 2], s_dec[i % 2]
+            with torch.cuda.stream(sh):
+                sh.wait_event(produced)
+                F.homconv_sum(P, L, o["ct"], o["A"], o["R"], d["Phat"], d["Mhat"], out=o["out"])
+                convolved = torch.cuda.Event()
+                convolved.record(sh)
+            with torch.cuda.stream(sd):
+                sd.wait_event(convolved)
+                F.decrypt_share(P, L, d["t_hat"], o["out"], out=o["yA"])
+        for st in streams:
+            main.wait_stream(st)
+
+    def check():
+        torch.cuda.synchronize()
+        for i, o in enumerate(bufs):
+            ref = refs[i % R]
+            assert np.array_equal(u32(o["yA"]).reshape(ref["yA"].shape), ref["yA"]), i
+            assert np.array_equal(u32(o["yB"]).reshape(ref["yB"].shape), ref["yB"]), i
+            o["yA"].zero_()
+            o["yB"].zero_()
+        torch.cuda.synchronize()
+
+    prev_overlap = F.set_launch_overlap(True)
+    prev_pair = F.set_decrypt_pair(pair)
+    try:
+        steps()
+        check()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(graph, stream=s):
+                steps()
+        torch.cuda.current_stream().wait_stream(s)
+        for _ in range(2):
+            graph.replay()
+            check()
+    finally:
+        F.set_launch_overlap(prev_overlap)
+        F.set_decrypt_pair(prev_pair)
+    P.close()
