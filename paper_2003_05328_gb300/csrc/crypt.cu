@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kMaxThreads) encode_kernel(DevParams P, DevLay
             const u64 idx = 2 * ((u64)u * P.n + j);
             const u64 a = uniform_q(stream_at(keyA, idx), stream_at(keyA, idx + 1), P.q);
             c0[j] = a ? P.q - a : 0;
-            c1[j] = addmod_q(mulmod_q(a, t_hat[j], P), c[j], P.q);
+            c1[j] = muladd_q(a, t_hat[j], c[j], P);
         }
     } else {
         for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) c1[j] = addmod_q(c1[j], c[j], P.q);
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kMaxThreads) decrypt_kernel(DevParams P, DevLa
     const u64* c1 = c0 + P.n;
     griddep_release();
     griddep_wait();
-    for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) c[j] = addmod_q(mulmod_q(c0[j], t_hat[j], P), c1[j], P.q);
+    for (u32 j = threadIdx.x; j < P.n; j += blockDim.x) c[j] = muladd_q(c0[j], t_hat[j], c1[j], P);
     __syncthreads();
     ntt_q_inv8(c, P);
     for (u32 coef = threadIdx.x; coef < P.n; coef += blockDim.x) {

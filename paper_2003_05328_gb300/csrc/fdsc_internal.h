@@ -23,6 +23,7 @@ struct DevParams {
     u64 r64, r64_s;        // 2^64 mod q, floor(r64 2^64 / q)
     u64 one_s;             // floor(2^64 / q): Shoup companion of 1
     u64 round_k;           // floor(p 2^64 / q)
+    u64 mu;                // floor(2^122 / q): Barrett constant of muladd_q
     u64 ninv, ninv_s;      // n^-1 mod q and companion
     const u64* qfw;        // psi_q^brv_n(k), k < n
     const u64* qfw_s;

@@ -25,8 +25,18 @@ __device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const DevParams& P) {
     return r >= P.q ? r - P.q : r;
 }
 
-__device__ __forceinline__ u64 mulmod_q(u64 a, u64 b, const DevParams& P) {
-    return reduce128(__umul64hi(a, b), a * b, P);
+// (a b + c) mod q for a, b, c in [0, q), q in (2^59, 2^60): one Barrett
+// reduction (P. Barrett, CRYPTO '86) of the 121-bit x = a b + c.  With
+// x' = floor(x / 2^58) < 2^63 and mu = floor(2^122 / q), the estimate
+// floor(x' mu / 2^64) lies between x/q - 1.75 and x/q, so it is floor(x/q)
+// or one less, and x minus it times q, taken mod 2^64, is in [0, 2q).
+__device__ __forceinline__ u64 muladd_q(u64 a, u64 b, u64 c, const DevParams& P) {
+    u64 lo = a * b, hi = __umul64hi(a, b);
+    lo += c;
+    hi += lo < c;
+    const u64 est = __umul64hi((hi << 6) | (lo >> 58), P.mu);
+    const u64 r = lo - est * P.q;
+    return r >= P.q ? r - P.q : r;
 }
 __device__ __forceinline__ u64 addmod_q(u64 a, u64 b, u64 q) {
     u64 s = a + b;

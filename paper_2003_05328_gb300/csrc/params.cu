@@ -354,6 +354,7 @@ extern "C" int fdsc_params_create(uint32_t n, uint32_t p, uint32_t max_T, fdsc_p
     D.r64_s = shoup64(D.r64, q);
     D.one_s = shoup64(1, q);
     D.round_k = (u64)(((u128)p << 64) / q);
+    D.mu = (u64)(((u128)1 << 122) / q);
     D.ninv = pow_mod(n, q - 2, q);
     D.ninv_s = shoup64(D.ninv, q);
     D.qfw = (const u64*)(dbase + o_qfw); D.qfw_s = (const u64*)(dbase + o_qfw_s);

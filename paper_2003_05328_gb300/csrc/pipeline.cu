@@ -135,7 +135,7 @@ __device__ __forceinline__ void constants_body(unsigned char* sm, const DevParam
 #pragma unroll
         for (int r = 0; r < 8; r++) {
             const u32 j = j0 + threadIdx.x + (u32)r * blockDim.x;
-            if (j < n) c1[j] = addmod_q(mulmod_q(a[r], key[j], P), c[padx(j)], P.q);
+            if (j < n) c1[j] = muladd_q(a[r], key[j], c[padx(j)], P);
         }
     }
 }
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMulti ? 2 : 0) decrypt_share_ker
 #pragma unroll
                 for (int r = 0; r < 4; r++) {
                     const u32 j = threadIdx.x + (u32)(r0 + r) * blockDim.x;
-                    if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
+                    if (j < n) c[padx(j)] = muladd_q(a[r], t[r], b[r], P);
                 }
             }
         } else {
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMulti ? 2 : 0) decrypt_share_ker
 #pragma unroll
             for (int r = 0; r < 8; r++) {
                 const u32 j = threadIdx.x + (u32)r * blockDim.x;
-                if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
+                if (j < n) c[padx(j)] = muladd_q(a[r], t[r], b[r], P);
             }
         }
         stage_wait_groups<3>();
@@ -537,7 +537,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMaxThreads)
 #pragma unroll
     for (int r = 0; r < 8; r++) {
         const u32 j = threadIdx.x + (u32)r * blockDim.x;
-        if (j < n) c[padx(j)] = addmod_q(mulmod_q(a[r], t[r], P), b[r], P.q);
+        if (j < n) c[padx(j)] = muladd_q(a[r], t[r], b[r], P);
     }
     stage_wait_groups<3>();
     // this part's half-length input: h_t = c_{2t} + c_{2t+1}, or psi^-(2k+1) (c_{2t} - c_{2t+1})
