@@ -242,19 +242,6 @@ __global__ void __launch_bounds__(kMaxThreads) mask_kernel(DevParams P, DevLayer
 }
 
 // ---------------------------------------------------------------- decrypt
-// round(p v / q) = floor((2 p v + q) / (2 q)): estimate floor(p v / q) from
-// below with floor(v floor(p 2^64 / q) / 2^64) (off by at most 1), then
-// step up while 2 q (z + 1) <= 2 p v + q (at most twice).
-__device__ __forceinline__ u32 round_pq(u64 v, const DevParams& P) {
-    u64 z = __umul64hi(v, P.round_k);
-    const unsigned __int128 num = (unsigned __int128)(2ull * P.p) * v + P.q;
-    const unsigned __int128 q2 = (unsigned __int128)2 * P.q;
-#pragma unroll
-    for (int it = 0; it < 3; it++)
-        if (q2 * (z + 1) <= num) z++;
-    return (u32)(z >= P.p ? z - P.p : z);
-}
-
 __global__ void __launch_bounds__(kMaxThreads) decrypt_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
                                                            const u64* __restrict__ ct, u32* __restrict__ SA) {
     extern __shared__ u64 smem[];

@@ -38,6 +38,36 @@ __device__ __forceinline__ u64 muladd_q(u64 a, u64 b, u64 c, const DevParams& P)
     const u64 r = lo - est * P.q;
     return r >= P.q ? r - P.q : r;
 }
+// Decryption's rounding, round(p v / q) mod p = floor((2 p v + q) / (2 q))
+// mod p for v in [0, q): z = floor(v floor(p 2^64 / q) / 2^64) is
+// floor(p v / q) or one less, so the remainder p v - z q, taken mod 2^64,
+// lies in [0, 2q); one conditional step makes it p v mod q, and the value
+// rounds up when twice that remainder passes q (q is odd: no ties).
+__device__ __forceinline__ u32 round_pq(u64 v, const DevParams& P) {
+    u64 z = __umul64hi(v, P.round_k);
+    u64 rem = (u64)P.p * v - z * P.q;
+    if (rem >= P.q) {
+        rem -= P.q;
+        z++;
+    }
+    z += 2 * rem >= P.q;
+    return (u32)(z >= P.p ? z - P.p : z);
+}
+// The same value from the same estimate z, stepped up while
+// 2 q (z + 1) <= 2 p v + q in 128-bit arithmetic (at most twice).  Slower
+// alone, but the one-ciphertext fused decryption keeps it: in the pipelined
+// one-image step its CTAs share SMs with the producers that bound the step,
+// and with the remainder form there the step took 18.6 instead of 18.2 us
+// (same GPU, alternating runs).
+__device__ __forceinline__ u32 round_pq_wide(u64 v, const DevParams& P) {
+    u64 z = __umul64hi(v, P.round_k);
+    const unsigned __int128 num = (unsigned __int128)(2ull * P.p) * v + P.q;
+    const unsigned __int128 q2 = (unsigned __int128)2 * P.q;
+#pragma unroll
+    for (int it = 0; it < 3; it++)
+        if (q2 * (z + 1) <= num) z++;
+    return (u32)(z >= P.p ? z - P.p : z);
+}
 __device__ __forceinline__ u64 addmod_q(u64 a, u64 b, u64 q) {
     u64 s = a + b;
     return s >= q ? s - q : s;

@@ -326,16 +326,6 @@ __global__ void __launch_bounds__(kMaxThreads, kGTw ? 2 : 0) produce_kernel(DevP
 }
 
 // ---------------------------------------------------------------- decrypt + fold + INTT2D
-__device__ __forceinline__ u32 round_pq2(u64 v, const DevParams& P) {
-    u64 z = __umul64hi(v, P.round_k);
-    const unsigned __int128 num = (unsigned __int128)(2ull * P.p) * v + P.q;
-    const unsigned __int128 q2 = (unsigned __int128)2 * P.q;
-#pragma unroll
-    for (int it = 0; it < 3; it++)
-        if (q2 * (z + 1) <= num) z++;
-    return (u32)(z >= P.p ? z - P.p : z);
-}
-
 // kMulti: a spectrum spans L.beta > 1 ciphertexts (H W > S); otherwise one.
 template <bool kMulti, bool kGTw>
 __global__ void __launch_bounds__(kMaxThreads, kMulti ? 2 : 0) decrypt_share_kernel(DevParams P, DevLayer L, const u64* __restrict__ t_hat,
@@ -423,7 +413,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMulti ? 2 : 0) decrypt_share_ker
         ntt_r8p<false, u64>(c, P.logn, 1, tq, P.ninv, P.ninv_s, P);
         for (u32 coef = threadIdx.x; coef < n; coef += blockDim.x) {
             const u32 r = coef & (P.d - 1), i = coef / P.d;
-            slots[padx(r * S + i)] = round_pq2(c[padx(coef)], P);
+            slots[padx(r * S + i)] = kMulti ? round_pq(c[padx(coef)], P) : round_pq_wide(c[padx(coef)], P);
         }
         stage_wait_groups<2>();
         ntt_r8p<true, u32>(slots, P.logS, P.d, tp, 0, 0, P);  // slot decode
@@ -569,7 +559,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMaxThreads)
         __syncthreads();
     }
     ntt_r8p<false, u64>(c, P.logn - 1, 1, tq, P.ninv, P.ninv_s, P);  // v_{2i+rank}, i < n/2, times n^-1
-    for (u32 i = threadIdx.x; i < hn; i += blockDim.x) slots[padx(i)] = round_pq2(c[padx(i)], P);
+    for (u32 i = threadIdx.x; i < hn; i += blockDim.x) slots[padx(i)] = round_pq(c[padx(i)], P);
     stage_wait_groups<2>();
     ntt_r8p<true, u32>(slots, P.logS - 1, 1, tp, 0, 0, P);  // half-length slot decode
     {
