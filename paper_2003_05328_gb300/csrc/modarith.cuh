@@ -55,10 +55,11 @@ __device__ __forceinline__ u32 round_pq(u64 v, const DevParams& P) {
 }
 // The same value from the same estimate z, stepped up while
 // 2 q (z + 1) <= 2 p v + q in 128-bit arithmetic (at most twice).  Slower
-// alone, but the one-ciphertext fused decryption keeps it: in the pipelined
-// one-image step its CTAs share SMs with the producers that bound the step,
-// and with the remainder form there the step took 18.6 instead of 18.2 us
-// (same GPU, alternating runs).
+// alone, but the fused decryptions of one ciphertext per CTA or CTA pair
+// keep it: in the pipelined one-image step their CTAs share SMs with the
+// producers that bound the step, and with the remainder form there the step
+// took 18.6 instead of 18.2 us (same GPU, alternating runs); the pair kernel
+// then compiled to 64 registers with spills and took 15.7 instead of 13.7 us.
 __device__ __forceinline__ u32 round_pq_wide(u64 v, const DevParams& P) {
     u64 z = __umul64hi(v, P.round_k);
     const unsigned __int128 num = (unsigned __int128)(2ull * P.p) * v + P.q;

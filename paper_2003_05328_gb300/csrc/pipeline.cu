@@ -559,7 +559,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kMaxThreads)
         __syncthreads();
     }
     ntt_r8p<false, u64>(c, P.logn - 1, 1, tq, P.ninv, P.ninv_s, P);  // v_{2i+rank}, i < n/2, times n^-1
-    for (u32 i = threadIdx.x; i < hn; i += blockDim.x) slots[padx(i)] = round_pq(c[padx(i)], P);
+    for (u32 i = threadIdx.x; i < hn; i += blockDim.x) slots[padx(i)] = round_pq_wide(c[padx(i)], P);
     stage_wait_groups<2>();
     ntt_r8p<true, u32>(slots, P.logS - 1, 1, tp, 0, 0, P);  // half-length slot decode
     {
