@@ -149,6 +149,54 @@ __global__ void __launch_bounds__(kMaxThreads) constants_kernel(DevParams P, con
     constants_body<kGTw>(sm, P, t_hat, key_stride, per_group, seed, seeds, ct, c1_only, blockIdx.x);
 }
 
+// ---------------------------------------------------------------- slot encode fused with the lift
+// The slot encode of the d slot sets in `a` (bit-reversed in, natural out,
+// times S^-1: the radix-8 passes of ntt_r8p) whose last pass, instead of
+// storing the slots, writes coefficient i of slot set r straight into the
+// NTT_q input as c[r + d i] = Delta m (< q).  Every thread of the CTA calls it;
+// it ends synchronised.
+__device__ __forceinline__ void slot_encode_lift(u32* a, u64* c, const uint2* tw, const DevParams& P) {
+    const u32 logL = P.logS, L = 1u << logL, lper = logL - 3;
+    const bool active = threadIdx.x < (P.d << lper);
+    const u32 vec = threadIdx.x >> lper, tl = threadIdx.x & ((1u << lper) - 1u), voff = vec << logL;
+    const int npass = ((int)logL + 2) / 3;
+    for (int ps = 0; ps < npass; ps++) {
+        const int lo = 3 * ps;
+        const int hi = lo + 2 < (int)logL - 1 ? lo + 2 : (int)logL - 1;
+        const u32 wlo = (u32)lo + 3 <= logL ? (u32)lo : logL - 3;
+        if (active) {
+            const u32 hb = (tl >> wlo) << (wlo + 3);
+            const u32 base = hb | (tl & ((1u << wlo) - 1u));
+            u32 x[8];
+#pragma unroll
+            for (int r = 0; r < 8; r++) x[r] = a[padx(voff + base + ((u32)r << wlo))];
+#pragma unroll
+            for (int st = 0; st < 3; st++) {
+                const int b = (int)wlo + st;
+                if (b > hi || b < lo) continue;
+                const u32 tb = (L + hb) >> (b + 1);
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    if (r & (1 << st)) continue;
+                    bfly_pair<false>(x[r], x[r | (1 << st)], tw[tb + (r >> (st + 1))], P);
+                }
+            }
+            if (ps == npass - 1) {
+#pragma unroll
+                for (int r = 0; r < 8; r++) {
+                    u32 y = shoup_mul32(x[r], P.Sinv, P.Sinv_s, P.p);
+                    y = y >= P.p ? y - P.p : y;
+                    c[padx(vec + P.d * (base + ((u32)r << wlo)))] = P.delta * y;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 8; r++) a[padx(voff + base + ((u32)r << wlo))] = x[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- share encoding
 // beta = 1: one CTA per input ciphertext u = (bb, k).  beta > 1: one CTA per
 // spectrum u = (bb, k), writing its beta ciphertexts (bb, k, h) from one
@@ -198,12 +246,7 @@ __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P
                 slots[padx(e)] = planes[padx((r << logHW) + h * S + s)];
             }
             __syncthreads();
-            ntt_r8p<false, u32>(slots, P.logS, P.d, tp, P.Sinv, P.Sinv_s, P);  // slot encode
-            for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
-                const u32 r = e >> P.logS, i = e & (S - 1);
-                c[padx(r + P.d * i)] = P.delta * slots[padx(e)];
-            }
-            __syncthreads();
+            slot_encode_lift(slots, c, tp, P);  // slot encode, then Delta m into c
             ntt_r8p<true, u64>(c, P.logn, 1, tq, 0, 0, P);
             const u64 uh = (u64)u * L.beta + h;  // ciphertext (bb, k, h)
             if (kMode == 0) {
@@ -268,11 +311,7 @@ __device__ __forceinline__ void share_body(unsigned char* sm, const DevParams& P
     lines_r8p<false>(slots, n >> logHW, false, L.logH, L.logW, tw_col, P.p);
     }
     stage_wait_groups<1>();
-    ntt_r8p<false, u32>(slots, P.logS, P.d, tp, P.Sinv, P.Sinv_s, P);  // slot encode
-    for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
-        const u32 r = e >> P.logS, i = e & (S - 1);
-        c[padx(r + P.d * i)] = P.delta * slots[padx(e)];
-    }
+    slot_encode_lift(slots, c, tp, P);  // slot encode, then Delta m into c
     stage_wait_groups<0>();
     ntt_r8p<true, u64>(c, P.logn, 1, tq, 0, 0, P);
     if (kMode == 0) {
