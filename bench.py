@@ -41,7 +41,7 @@ import fdsc_inputs as FI  # noqa: E402
 METRIC = "HomConv layers/s & mod-q MAC/s at 32×32×64; p50/p99 served latency"
 STAGE_STREAMS = (1, 2, 2)  # streams per stage of the pipelined schedule: producers, HomConv, decryption
 GRAPH_STEPS = 220   # steps recorded in one graph of the timed loop (20 rotations of the instances)
-WORKLOAD = "cfg1"
+WORKLOAD = "cifar_32x32x64_b1"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "homconv_traffic.json")
 KERNEL_SOURCES = ["paper_2003_05328_gb300/csrc/homconv.cu", "paper_2003_05328_gb300/csrc/modarith.cuh",
@@ -366,7 +366,7 @@ def run_batched(F, flush, sleep_cycles, args):
     per-layer path: every (layer, image) pair launched on its own."""
     import torch
 
-    c = FI.CONFIGS["cfg2"]
+    c = FI.CONFIGS["stack_16img_32x32x64_16x16x128_8x8x256"]
     params, specs, singles = {}, [], []
     dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
     for li, ls in enumerate(c.layers):
@@ -410,7 +410,7 @@ def run_batched(F, flush, sleep_cycles, args):
     ms_single = timed(lambda: [pp.launch() for pp in per_pair], max(3, reps // 5))
     units = sum(ls.B for ls in c.layers)
     info = [plan.info(i) for i in range(len(c.layers))]
-    out = {"workload": "cfg2", "layers": [f"{ls.H}x{ls.W}x{ls.Ci}->{ls.Co}, n={ls.n}" for ls in c.layers],
+    out = {"workload": "stack_16img_32x32x64_16x16x128_8x8x256", "layers": [f"{ls.H}x{ls.W}x{ls.Ci}->{ls.Co}, n={ls.n}" for ls in c.layers],
            "images": c.layers[0].B, "layers_per_s": units / (np.mean(ms_plan) * 1e-3),
            "ms_per_launch": float(np.mean(ms_plan)), "per_layer_path_layers_per_s": units / (np.mean(ms_single) * 1e-3),
            "per_layer_path_ms": float(np.mean(ms_single)), "speedup_vs_per_layer": float(np.mean(ms_single) / np.mean(ms_plan)),
@@ -428,7 +428,7 @@ def run_batched(F, flush, sleep_cycles, args):
 
 # HomConv shapes where the contraction is a dense product: the 16-image stack's
 # three layers and the binarized 64x64x128 layer at batch 8
-TENSOR_SHAPES = [("cfg2", 0), ("cfg2", 1), ("cfg2", 2), ("cfg4", 0)]
+TENSOR_SHAPES = [("stack_16img_32x32x64_16x16x128_8x8x256", 0), ("stack_16img_32x32x64_16x16x128_8x8x256", 1), ("stack_16img_32x32x64_16x16x128_8x8x256", 2), ("binarized_64x64x128_b8", 0)]
 
 
 def run_tensor_homconv(F, flush, args):
@@ -538,7 +538,7 @@ def run_binarized(F, sleep_cycles, args):
     convolution on sampled planes."""
     import torch
 
-    c = FI.CONFIGS["cfg4"]
+    c = FI.CONFIGS["binarized_64x64x128_b8"]
     ls = c.layers[0]
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm = peaks.get("hbm_gbs") or 6800.0
@@ -627,7 +627,7 @@ def run_binarized(F, sleep_cycles, args):
     alg = filt + per_groups
     moved = 8 * Ptc.numel() + per_groups
     macs = 2 * ls.Co * lay.T * lay.beta * ls.n * lay.GB
-    res = {"workload": "cfg4", "layer": "64x64x128->128 3x3, binarized weights, batch 8", "n": ls.n, "p": ls.p,
+    res = {"workload": "binarized_64x64x128_b8", "layer": "64x64x128->128 3x3, binarized weights, batch 8", "n": ls.n, "p": ls.p,
            "d": d, "beta": lay.beta, "T": lay.T, "image_groups": lay.GB,
            "step_us": step_us, "layers_per_s": ls.B / (step_us * 1e-6),
            "stage_us": {"online_produce": prod_us, "homconv_tc": hc_tc_us, "homconv_cuda_cores": hc_cc_us,
@@ -720,7 +720,7 @@ def run_serving(F, args, rate=None, n_req=None):
 
     import torch
 
-    c = FI.CONFIGS["cfg3"]
+    c = FI.CONFIGS["served_mix_28x28x1_32x32x64_16x16x128"]
     rate = rate or c.extra["rate_per_s"]
     n_req = n_req or args.serve_requests
     P = F.Params(2048, 65537, max_T=64)
@@ -778,7 +778,7 @@ def run_serving(F, args, rate=None, n_req=None):
     st = S.stats()
     S.close()
     P.close()
-    return {"workload": "cfg3" if rate == c.extra["rate_per_s"] else "cfg3 mix at %g requests/s" % rate,
+    return {"workload": "served_mix_28x28x1_32x32x64_16x16x128" if rate == c.extra["rate_per_s"] else "served mix at %g requests/s" % rate,
             "requests": n_req, "rate_per_s": rate, "completed": int(st.completed),
             "lanes": int(st.lanes), "lane_capacity": int(st.lane_capacity), "reserved_bytes": int(st.reserved_bytes),
             "throughput_req_per_s": st.completed / wall, "p50_us": st.p50_us, "p99_us": st.p99_us,
@@ -870,7 +870,7 @@ def run_kernel_only(args):
     if args.kernel_only == "plan":
         # the 16-image uneven stack as one autotuned plan, launched --steps times
         P.close()
-        c2 = FI.CONFIGS["cfg2"]
+        c2 = FI.CONFIGS["stack_16img_32x32x64_16x16x128_8x8x256"]
         params, specs = {}, []
         dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
         for li, ls2 in enumerate(c2.layers):
@@ -897,7 +897,7 @@ def run_kernel_only(args):
     if args.kernel_only == "binarized":
         # the binarized 64x64x128 layer at batch 8 through the fused path
         P.close()
-        c4 = FI.CONFIGS["cfg4"]
+        c4 = FI.CONFIGS["binarized_64x64x128_b8"]
         ls4 = c4.layers[0]
         P = F.Params(ls4.n, ls4.p, max_T=ls4.Ci)
         L4 = F.LayerSpec(ls4.B, ls4.Ci, ls4.Co, ls4.H, ls4.W, 1, 1)
@@ -920,7 +920,7 @@ def run_kernel_only(args):
         return
     if args.kernel_only == "homconv_tc":
         # the tensor-core HomConv on the 16x16x128->128 layer of the 16-image stack
-        ls = FI.CONFIGS["cfg2"].layers[1]
+        ls = FI.CONFIGS["stack_16img_32x32x64_16x16x128_8x8x256"].layers[1]
         info = F.params_query(ls.n, ls.p)
         g_c, g_b = FI.default_pack(ls, info.S)
         L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
@@ -937,7 +937,7 @@ def run_kernel_only(args):
         assert F.homconv_tc_status() == 0
     elif args.kernel_only in ("homconv", "homconv_b16"):
         if args.kernel_only == "homconv_b16":
-            ls = FI.CONFIGS["cfg2"].layers[0]
+            ls = FI.CONFIGS["stack_16img_32x32x64_16x16x128_8x8x256"].layers[0]
             g_c, g_b = FI.default_pack(ls, info.S)
             L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, g_c, g_b)
             lay = F.layout(P, L)

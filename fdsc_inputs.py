@@ -52,20 +52,20 @@ class Config:
 
 
 CONFIGS = {
-    "cfg0": Config("single layer 16x16x4->4, 3x3, n=1024", 0,
+    "layer_16x16x4_b1": Config("single layer 16x16x4->4, 3x3, n=1024", 0,
                    (LayerShape(1, 4, 4, 16, 16, 3, 3, 1024, 65537),)),
-    "cfg1": Config("CIFAR-shaped layer 32x32x64->64, 3x3, batch 1, n=2048", 1,
+    "cifar_32x32x64_b1": Config("CIFAR-shaped layer 32x32x64->64, 3x3, batch 1, n=2048", 1,
                    (LayerShape(1, 64, 64, 32, 32, 3, 3, 2048, 65537),)),
-    "cfg2": Config("batched uneven stack, 16 images: 32x32x64->64, 16x16x128->128, 8x8x256->256", 2,
+    "stack_16img_32x32x64_16x16x128_8x8x256": Config("batched uneven stack, 16 images: 32x32x64->64, 16x16x128->128, 8x8x256->256", 2,
                    (LayerShape(16, 64, 64, 32, 32, 3, 3, 2048, 65537),
                     LayerShape(16, 128, 128, 16, 16, 3, 3, 2048, 65537),
                     LayerShape(16, 256, 256, 8, 8, 3, 3, 4096, 65537))),
-    "cfg3": Config("served mix: 28x28 (pad 32)x1->16 5x5, 32x32x64->64 3x3, 16x16x128->128 3x3", 3,
+    "served_mix_28x28x1_32x32x64_16x16x128": Config("served mix: 28x28 (pad 32)x1->16 5x5, 32x32x64->64 3x3, 16x16x128->128 3x3", 3,
                    (LayerShape(1, 1, 16, 32, 32, 5, 5, 2048, 65537, h=28, w=28),
                     LayerShape(1, 64, 64, 32, 32, 3, 3, 2048, 65537),
                     LayerShape(1, 128, 128, 16, 16, 3, 3, 2048, 65537)),
                    extra={"rate_per_s": 2000.0, "requests": 20000, "hbm_budget_bytes": 120 * 10**9}),
-    "cfg4": Config("binarized layer 64x64x128->128, batch 8, p=12289, n=4096", 4,
+    "binarized_64x64x128_b8": Config("binarized layer 64x64x128->128, batch 8, p=12289, n=4096", 4,
                    (LayerShape(8, 128, 128, 64, 64, 3, 3, 4096, 12289, binary=True),)),
 }
 

@@ -45,7 +45,7 @@ def test_homconv_counts():
     import bench
     import fdsc_inputs as FI
 
-    ls = FI.CONFIGS["cfg1"].layers[0]
+    ls = FI.CONFIGS["cifar_32x32x64_b1"].layers[0]
     byts, macs = bench.layer_counts(ls, 32, 1, 1, 2048, addends=0)
     assert macs == 2 * 64 * 64 * 32 * 32  # equals the useful MACs: g_c H W = S
     assert byts == 8 * 64 * 32 * 2048 + 8 * (2 * 32 * 2048 + 3 * 64 * 2048)

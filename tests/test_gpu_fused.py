@@ -153,8 +153,8 @@ def test_binarized_layer_full_size_fused_path(F):
     fused kernels at full size, HomConv on the tensor cores and on the CUDA
     cores: both give the same words, and s_A + s_B is the convolution of
     x_A + x_B with the filters on sampled planes."""
-    ls = FI.CONFIGS["cfg4"].layers[0]
-    cid = FI.CONFIGS["cfg4"].cid
+    ls = FI.CONFIGS["binarized_64x64x128_b8"].layers[0]
+    cid = FI.CONFIGS["binarized_64x64x128_b8"].cid
     P = F.Params(ls.n, ls.p, max_T=ls.Ci)
     L = F.LayerSpec(ls.B, ls.Ci, ls.Co, ls.H, ls.W, 1, 1)
     xA, xB = FI.shares(ls, cid)
@@ -215,7 +215,7 @@ def test_stage_pipelined_steps_match_the_oracle(F, pair):
     stream of its own -- with programmatic dependent launch, run eagerly and
     as one CUDA graph replayed twice: every step's two output shares are the
     oracle's words for its instance (pair: decryption on CTA pairs)."""
-    c = FI.CONFIGS["cfg1"]
+    c = FI.CONFIGS["cifar_32x32x64_b1"]
     ls = c.layers[0]
     OP = O.params(ls.n, ls.p)
     info = F.params_query(ls.n, ls.p)

@@ -108,7 +108,7 @@ def test_keygen_matches_oracle(F, n, p):
 
 
 # ---------------------------------------------------------------- whole layer, every stage
-@pytest.mark.parametrize("cfg", ["cfg0", "cfg1"])
+@pytest.mark.parametrize("cfg", ["layer_16x16x4_b1", "cifar_32x32x64_b1"])
 def test_config_layer_bit_exact(F, cfg):
     c = FI.CONFIGS[cfg]
     ls = c.layers[0]
@@ -173,14 +173,14 @@ def test_small_layer_sweep_with_edge_values(F, i, case):
 
 @pytest.mark.parametrize("layer", [0, 1, 2])
 def test_batched_stack_layers_reduced_batch_bit_exact(F, layer):
-    ls = FI.CONFIGS["cfg2"].layers[layer]
+    ls = FI.CONFIGS["stack_16img_32x32x64_16x16x128_8x8x256"].layers[layer]
     S = O.params(ls.n, ls.p).S
     g_c, g_b = FI.default_pack(ls, S)
     _check_layer(F, ls.n, ls.p, 2, ls.Ci, ls.Co, ls.H, ls.W, ls.fh, ls.fw, g_c, g_b, seed=20 + layer)
 
 
 def test_binarized_layer_reduced_channels_bit_exact(F):
-    ls = FI.CONFIGS["cfg4"].layers[0]
+    ls = FI.CONFIGS["binarized_64x64x128_b8"].layers[0]
     g = np.random.default_rng(44)
     B, Ci, Co = 2, 8, 8
     xA, xB, _ = _inputs(44, B, Ci, Co, ls.H, ls.W, 3, 3, ls.p)
@@ -260,13 +260,13 @@ def _full_size_property(F, ls, cid, g_c, g_b, sample_planes):
 
 @pytest.mark.parametrize("layer", [0, 1, 2])
 def test_batched_stack_full_batch_property(F, layer):
-    ls = FI.CONFIGS["cfg2"].layers[layer]
+    ls = FI.CONFIGS["stack_16img_32x32x64_16x16x128_8x8x256"].layers[layer]
     g_c, g_b = FI.default_pack(ls, O.params(ls.n, ls.p).S)
     _full_size_property(F, ls, 2, g_c, g_b, 6)
 
 
 def test_binarized_layer_full_size_property(F):
-    ls = FI.CONFIGS["cfg4"].layers[0]
+    ls = FI.CONFIGS["binarized_64x64x128_b8"].layers[0]
     _full_size_property(F, ls, 4, 1, 1, 4)
 
 
@@ -468,7 +468,7 @@ def test_homconv_tc_full_size_binarized_layer(F):
     ciphertexts per spectrum): the tensor-core words equal the CUDA-core
     kernel's at full size, and sampled output words equal the oracle's
     per-word sum."""
-    ls = FI.CONFIGS["cfg4"].layers[0]
+    ls = FI.CONFIGS["binarized_64x64x128_b8"].layers[0]
     OP = O.params(ls.n, ls.p)
     OL = O.layer(OP, ls.B, ls.Ci, ls.Co, ls.H, ls.W, 1, 1)
     P = F.Params(ls.n, ls.p, max_T=OL.T)

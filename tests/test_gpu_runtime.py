@@ -185,7 +185,7 @@ def test_server_large_batches_use_the_tensor_cores(F):
 def _served_mix_refs():
     """The served mix's three layer types at full size, with the requests of
     the full-size server test and the oracle's shares for each alone."""
-    c = FI.CONFIGS["cfg3"]
+    c = FI.CONFIGS["served_mix_28x28x1_32x32x64_16x16x128"]
     OP = O.params(2048, 65537)
     key_seeds = [31, 32, 33]
     types = []

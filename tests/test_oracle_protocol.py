@@ -119,7 +119,7 @@ def _e2e(n, p, B, Ci, Co, H, W, fh, g_c=None, g_b=1, seed=0, homrec=True, suppor
 
 
 @pytest.mark.parametrize("args", [
-    dict(n=1024, p=65537, B=1, Ci=4, Co=4, H=16, W=16, fh=3),                       # cfg0 shape
+    dict(n=1024, p=65537, B=1, Ci=4, Co=4, H=16, W=16, fh=3),                       # the 16x16x4 layer's shape
     dict(n=256, p=65537, B=3, Ci=5, Co=3, H=8, W=8, fh=3, g_c=2, g_b=2),            # ragged Ci, B
     dict(n=256, p=65537, B=2, Ci=3, Co=2, H=32, W=16, fh=3),                       # halves (HW > S)
     dict(n=512, p=12289, B=3, Ci=3, Co=2, H=8, W=8, fh=3, g_c=2, g_b=2),            # p = 12289
@@ -174,7 +174,7 @@ def test_homshare_fold_gives_product_minus_mask():
     assert np.array_equal((out["SA_hat"].astype(object) + out["sB_hat"]) % p, Y)
 
 
-@pytest.mark.parametrize("cfg", ["cfg0", "cfg1"])
+@pytest.mark.parametrize("cfg", ["layer_16x16x4_b1", "cifar_32x32x64_b1"])
 def test_config_round_trip(cfg):
     c = FI.CONFIGS[cfg]
     ls = c.layers[0]
